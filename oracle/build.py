@@ -1,0 +1,30 @@
+"""Compile the C part of the FP64 oracle (test infrastructure only).
+
+The shared object is built next to the source, under ``oracle/_build``.  It is compiled
+with ``-ffp-contract=off`` so that no multiply-add is fused and results are the same on
+x86-64 and AArch64 hosts, and with OpenMP so that the CPU baseline can use every core.
+"""
+import os
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "lbm_oracle.c")
+OUT_DIR = os.path.join(HERE, "_build")
+LIB = os.path.join(OUT_DIR, "liblbm_oracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Build ``liblbm_oracle.so`` if it is missing or older than its source."""
+    os.makedirs(OUT_DIR, exist_ok=True)
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+        return LIB
+    tmp = LIB + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force=True))
