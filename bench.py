@@ -1,0 +1,381 @@
+"""Throughput of the fused D2Q9 improved-MRT pseudopotential step on GB300.
+
+Workload (one GPU): a 4096 x 4096 periodic FP32 field holding 64 non-overlapping
+droplets (radii uniform in [40, 200], seed 5) of the Carnahan-Starling fluid with
+a = 0.25, T = 0.6 T_c, sigma = 0.114, liquid/vapour viscosities 0.05/0.5 with the
+relaxation time linear in rho.  A benchmark step is one time step of the whole field
+(one launch of the fused kernel); every 100th step also runs the diagnostics pass
+(mass, momentum, max |v|, |d rho|_inf).  The state (1.2 GB) is far larger than L2, so no
+flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on the host
+cores instead (each step: one oracle step on a 1024 x 1024 window of the same field).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+NX = NY = 4096
+A, B, R = 0.25, 4.0, 1.0
+TR = 0.6
+SIGMA = 0.114
+NU_L, NU_V = 0.05, 0.5
+RATES = (1.0, 1.1, 1.1, 1.0, 1.1, 1.0, 1.1, 1.0, 1.0)
+DIAG_EVERY = 100
+BYTES_PER_LU = 72  # 9 float populations read + 9 written per lattice update
+WORKLOAD = "droplets64_4096x4096_fp32"
+REF_WINDOW = 1024
+METRIC = "MLUPS (D2Q9 MRT-pseudopotential step, 4096^2, FP32)"
+
+
+def eos_T():
+    from paper_1211_6932_gb300 import workloads as wl
+    return TR * wl.t_crit(A, B, R)
+
+
+def field(rho_l, rho_v):
+    from paper_1211_6932_gb300 import workloads as wl
+    rho, _, _ = wl.multi_droplets(NX, NY, rho_l, rho_v, 4.0, 64, 40.0, 200.0, seed=5)
+    return rho
+
+
+def config(extra=None):
+    c = {"workload": WORKLOAD, "grid": [NX, NY], "droplets": 64, "a": A, "T_over_Tc": TR,
+         "sigma": SIGMA, "nu_l": NU_L, "nu_v": NU_V, "visc_mode": "linear",
+         "diag_every": DIAG_EVERY, "l2": "state 1.21 GB > 129 MB L2, no flush",
+         "parallelism": "replicas"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("lbm_device.cuh",):
+        with open(os.path.join(ROOT, "paper_1211_6932_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(n_nodes):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the kernel."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "sweep_traffic.json")) as fh:
+            t = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if t.get("kernel_hash") != kernel_source_hash():
+        return None
+    return float(t["dram_bytes_per_node"]) * n_nodes
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(steps=None, budget_s=15.0):
+    """The FP64 oracle on a 1024 x 1024 window of the workload, on the host cores."""
+    import numpy as np
+
+    import oracle
+    from oracle import thermo
+    T = eos_T()
+    rl, rv, _ = thermo.maxwell(A, B, R, T)
+    rho = field(rl, rv)[:REF_WINDOW, :REF_WINDOW].copy()
+    p = oracle.Params(nx=REF_WINDOW, ny=REF_WINDOW, a=A, b=B, R=R, T=T, sigma=SIGMA,
+                      s=RATES, visc_mode=oracle.VISC_LINEAR, nu_l=NU_L, nu_v=NU_V,
+                      rho_l=rl, rho_v=rv)
+    f = oracle.equilibrium(rho)
+    f = oracle.run(p, f, 1)  # warm-up
+    if steps is None:
+        t0 = time.perf_counter()
+        f = oracle.run(p, f, 1)
+        one = time.perf_counter() - t0
+        steps = max(1, min(200, int(budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    f = oracle.run(p, f, steps)
+    dt = time.perf_counter() - t0
+    assert np.isfinite(f).all()
+    mlups = REF_WINDOW * REF_WINDOW * steps / dt / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": oracle.threads(), "kind": "oracle",
+            "sample": "%d oracle steps on a %dx%d window of the %dx%d field (%.1f s)" % (
+                steps, REF_WINDOW, REF_WINDOW, NX, NY, dt)}, steps, dt
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from oracle import thermo
+    import numpy as np
+    T = eos_T()
+    rl, rv, _ = thermo.maxwell(A, B, R, T)
+    rho = field(rl, rv)[:REF_WINDOW, :REF_WINDOW].copy()
+    p = oracle.Params(nx=REF_WINDOW, ny=REF_WINDOW, a=A, b=B, R=R, T=T, sigma=SIGMA,
+                      s=RATES, visc_mode=oracle.VISC_LINEAR, nu_l=NU_L, nu_v=NU_V,
+                      rho_l=rl, rho_v=rv)
+    f = oracle.equilibrium(rho)
+    for _ in range(args.warmup):
+        f = oracle.run(p, f, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = oracle.run(p, f, 1)
+    dt = time.perf_counter() - t0
+    assert np.isfinite(f).all()
+    value = REF_WINDOW * REF_WINDOW * args.steps / dt / 1e6
+    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config({"sample_window": [REF_WINDOW, REF_WINDOW]}),
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": oracle.threads(),
+                             "kind": "oracle",
+                             "sample": "each step: one oracle step on a %dx%d window" % (
+                                 REF_WINDOW, REF_WINDOW)},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_1211_6932_gb300 import Eos, Lattice, maxwell
+
+    world, rank, local = dist_setup()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    T = eos_T()
+    eos = Eos(a=A, T=T, b=B, R=R)
+    rl, rv = maxwell(eos)
+    rho = field(rl, rv)
+    stream = torch.cuda.Stream(device=dev)
+    L = Lattice(NX, NY, eos, G=-1.0, sigma=SIGMA, s=RATES, nu_l=NU_L, nu_v=NU_V,
+                precision="fp32", visc_mode="linear", stream=stream,
+                tile_vec=args.tile_vec, tile_rows=args.tile_rows)
+    L.init_fields(rho)
+    n_nodes = NX * NY
+
+    # warm-up (graph capture happens here)
+    for _ in range(args.warmup):
+        L.step(1)
+    L.step(64)
+    L.diagnostics()
+    L.sync()
+
+    K = args.steps
+    chunks = []
+    k = 0
+    while k < K:
+        n = min(DIAG_EVERY, K - k)
+        chunks.append(n)
+        k += n
+    ev_step = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in chunks]
+    ev_diag = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in chunks]
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    launches = 0
+    diag_last = None
+    t_all0.record(stream)
+    for i, n in enumerate(chunks):
+        ev_step[i][0].record(stream)
+        L.step(n)
+        ev_step[i][1].record(stream)
+        launches += n
+        if n == DIAG_EVERY:
+            ev_diag[i][0].record(stream)
+            diag_last = L.diagnostics()
+            ev_diag[i][1].record(stream)
+            launches += 2
+    t_all1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    L.sync()
+    total_ms = t_all0.elapsed_time(t_all1)
+    step_ms = sum(a.elapsed_time(b) for a, b in ev_step)
+    total_ms_max = max_over_ranks(total_ms, world)
+    avg_launch_ms = step_ms / K
+    value = world * n_nodes * K / (total_ms_max * 1e-3) / 1e6
+
+    # End to end through the C ABI with host buffers: upload the initial fields from
+    # pinned memory, 100 steps, read the density back.
+    e2e_steps = max(1, min(5, K // DIAG_EVERY))
+    rho_h = torch.from_numpy(rho).pin_memory()
+    out_h = torch.empty((NY, NX), dtype=torch.float64).pin_memory()
+    rho_np, out_np = rho_h.numpy(), out_h.numpy()
+    L.init_fields(rho_np)
+    L.step(DIAG_EVERY)
+    L.sync()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        L.init_fields(rho_np)
+        L.step(DIAG_EVERY)
+        L.moments(out=out_np)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_value = world * n_nodes * DIAG_EVERY * e2e_steps / e2e_s / 1e6
+
+    peak, peak_kind = load_peak()
+    achieved = BYTES_PER_LU * n_nodes / (avg_launch_ms * 1e-3) / 1e9
+    traffic = load_traffic(n_nodes)
+    vec, rows = L.tiling
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": total_ms_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config({"tile_vec": vec, "tile_rows": rows}),
+            "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": peak_kind,
+                         "kernel": "sweep_kernel<float,%d,STEP>" % vec,
+                         "algorithmic_bytes_per_launch": BYTES_PER_LU * n_nodes,
+                         "avg_launch_ms": avg_launch_ms},
+            "e2e": {"value": e2e_value, "unit": "MLUPS",
+                    "h2d_bytes_per_step": n_nodes * 8, "d2h_bytes_per_step": n_nodes * 4,
+                    "lbm_steps_per_step": DIAG_EVERY},
+            "clocks": clocks,
+            "diagnostics": diag_last,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()[0]
+        print(json.dumps(line), flush=True)
+    L.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--tile-vec", type=int, default=0)
+    ap.add_argument("--tile-rows", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

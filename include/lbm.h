@@ -1,0 +1,258 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) D2Q9 improved-MRT pseudopotential lattice
+ * Boltzmann library, after Li, Luo & Li, "Lattice Boltzmann modeling of multiphase flows
+ * at large density ratio with an improved pseudopotential model" (arXiv:1211.6932).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - Return value: LBM_OK (0) on success, a negative LBM_E* code otherwise.  The message
+ *    of the last failure is available from lbm_last_error(handle) (or
+ *    lbm_last_error(NULL) for failures before a handle exists, kept per thread).
+ *  - Lattice units: c = delta_t = 1, c_s^2 = 1/3.
+ *  - Host field arrays are row-major (ny, nx) doubles: element (y, x) at y*nx + x.
+ *    Host population arrays are (9, ny, nx) doubles: f_q(x, y) at q*nx*ny + y*nx + x, with
+ *    the D2Q9 velocities in this order: e0 = (0,0), e1 = (1,0), e2 = (0,1), e3 = (-1,0),
+ *    e4 = (0,-1), e5 = (1,1), e6 = (-1,1), e7 = (-1,-1), e8 = (1,-1).
+ *    Populations are those at the current time before collision (the f of Eq. 1).
+ *  - The library owns every device buffer of a handle; the caller owns every host buffer
+ *    and every device buffer it passes in.  Pointers are only read during the call.
+ *  - Work is queued on the handle's CUDA stream.  Calls that return data to the host
+ *    synchronise that stream; lbm_step does not.
+ *  - A handle is not thread-safe: one thread at a time.
+ *  - Nothing here falls back to the CPU: without a usable CUDA device lbm_create returns
+ *    LBM_ECUDA.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_EINVAL (-1)    /* an argument is out of range; nothing was changed */
+#define LBM_ENOMEM (-2)    /* a device or host allocation failed */
+#define LBM_ECUDA (-3)     /* a CUDA runtime call failed (message names it) */
+#define LBM_EUNSTABLE (-4) /* a density became non-finite or non-positive */
+#define LBM_ETIMEOUT (-5)  /* a bounded device-side wait ran out */
+#define LBM_ESTATE (-6)    /* call not valid in the handle's current state */
+#define LBM_EIO (-7)       /* file could not be read/written, or failed its checksum */
+
+/* Floating-point format of the stored populations. */
+#define LBM_FP64 0     /* double populations and double arithmetic */
+#define LBM_FP32_DEV 1 /* float deviations f_q - t_q rho_ref, float arithmetic */
+
+/* Viscosity modes (Sec. IV C and Eq. 10: nu = (tau_nu - 1/2) / 3). */
+#define LBM_VISC_CONST 0  /* s[7], s[8] used as given */
+#define LBM_VISC_STEP 1   /* nu = nu_l where rho >= rho_c, nu_v below (Sec. IV C) */
+#define LBM_VISC_LINEAR 2 /* tau_nu linear in rho between rho_v and rho_l, clamped */
+
+/* Boundaries.  x is always periodic. */
+#define LBM_BC_PERIODIC 0 /* periodic in y */
+#define LBM_BC_WALLS_Y 1  /* no-slip walls at y = -1/2 and y = ny - 1/2 (halfway
+                             bounce-back, Sec. IV C); psi at a ghost row equals psi of the
+                             adjacent fluid row */
+
+/* Carnahan-Starling equation of state, Eq. 30:
+ *   p = rho R T (1 + x + x^2 - x^3) / (1 - x)^3 - a rho^2,  x = b rho / 4. */
+typedef struct {
+  double a, b, R, T;
+} lbm_eos;
+
+/* Optional settings for lbm_create.  Fill with lbm_options_default, then override. */
+typedef struct {
+  int precision;  /* LBM_FP32_DEV (default) or LBM_FP64 */
+  int visc_mode;  /* -1 (default): LBM_VISC_STEP if nu_l > 0 and nu_v > 0, else CONST */
+  int bc;         /* LBM_BC_PERIODIC (default) or LBM_BC_WALLS_Y */
+  int psi_fp64;   /* FP32_DEV only: 1 evaluates psi (Eqs. 24, 30) in double precision */
+  double rho_ref; /* FP32_DEV deviation reference; < 0 (default): the Maxwell vapour
+                     density when T < T_c, else 0.  Ignored for LBM_FP64 (always 0). */
+  double rho_c;   /* STEP switch density; <= 0 (default): 0.5218 / b (Sec. IV A) */
+  double rho_l;   /* LINEAR end points; <= 0 (default): Maxwell construction (Eq. 22) */
+  double rho_v;
+  void* stream;   /* cudaStream_t to queue work on; NULL: a stream the handle owns */
+  int device;     /* CUDA device ordinal; -1 (default): the library's current device.
+                     Every call on the handle makes this device current first. */
+  int tile_vec;   /* columns per thread in the step kernel: 1, 2, 4 (4 is FP32 only);
+                     0 (default): 4 for FP32_DEV, 1 for FP64 */
+  int tile_rows;  /* rows per CTA sweep; 0 (default): sized to fill the GPU */
+} lbm_options;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Diagnostics of the current state (Eq. 6 fields), accumulated in double precision. */
+typedef struct {
+  double mass;     /* sum over nodes of rho */
+  double mom_x;    /* sum over nodes of rho v_x  (rho v = sum e f + F/2, Eq. 6) */
+  double mom_y;    /* sum over nodes of rho v_y */
+  double max_u;    /* max over nodes of |v| (the spurious current at equilibrium) */
+  double dinf;     /* max over nodes of |rho - rho at the previous diagnostics call|;
+                      -1 on the first call after create/init/load */
+  long long step;  /* number of steps taken since the last init */
+  long long nonfinite; /* nodes whose rho or v is not finite */
+} lbm_diag;
+
+/* Fill *opt with the defaults described above.  opt must not be NULL. */
+void lbm_options_default(lbm_options* opt);
+
+/*
+ * Create a lattice of nx x ny nodes (Sec. II).
+ *   eos       Carnahan-Starling parameters (Eq. 30); a, b, R, T > 0.
+ *   G         interaction strength of Eq. 7; must make 2 (p_EOS - rho/3) / G >= 0 over the
+ *             initial densities (G = -1 in the paper, Sec. IV A).
+ *   sigma     improved-forcing parameter of Eq. 25 (0 gives Eq. 9, the original scheme).
+ *   s[9]      relaxation rates of Eq. 2, (s_rho, s_e, s_zeta, s_j, s_q, s_j, s_q, s_nu,
+ *             s_nu), each in (0, 2).  s[1] and s[2] are the 1/tau_e and 1/tau_zeta of
+ *             Eq. 25.
+ *   nu_l,nu_v liquid / vapour kinematic viscosities for the STEP and LINEAR modes (> 0);
+ *             they replace s[7] and s[8] there.  Pass 0, 0 for LBM_VISC_CONST.
+ *   opt       NULL for defaults.
+ * nx, ny >= 1 and nx*ny*9 populations must fit in device memory.  The populations start
+ * at zero; call lbm_init_fields or lbm_set_populations before stepping.
+ * On success *out receives the handle (free with lbm_destroy).
+ */
+int lbm_create(lbm_handle** out, int nx, int ny, lbm_eos eos, double G, double sigma,
+               const double s[9], double nu_l, double nu_v, const lbm_options* opt);
+
+/* Release every resource of the handle.  NULL is allowed. */
+void lbm_destroy(lbm_handle* h);
+
+/* Message of the last failure on h (NULL: of the calling thread's last failed create).
+ * Never NULL; "" when there was none.  Valid until the next call on the same handle. */
+const char* lbm_last_error(const lbm_handle* h);
+
+/*
+ * Set every node to the equilibrium of Eq. 3 for host fields rho, ux, uy ((ny, nx)
+ * doubles; ux or uy may be NULL for zero), i.e. f_q = t_q rho [1 + 3 e.v + 9/2 (e.v)^2 -
+ * 3/2 v^2].  Resets the step counter and the dinf reference.  Returns LBM_EINVAL if a
+ * density is not in (0, 4/b) or gives a negative psi^2 (Eq. 24).  Synchronous.
+ */
+int lbm_init_fields(lbm_handle* h, const double* rho, const double* ux, const double* uy);
+
+/* Same as lbm_init_fields with device pointers (double, (ny, nx), caller-owned). */
+int lbm_init_fields_device(lbm_handle* h, const double* rho, const double* ux,
+                           const double* uy);
+
+/* Replace the state with host populations f ((9, ny, nx) doubles, pre-collision, current
+ * time).  Resets the step counter.  Synchronous. */
+int lbm_set_populations(lbm_handle* h, const double* f);
+
+/* Copy the current pre-collision populations to host f ((9, ny, nx) doubles).
+ * Synchronous; returns LBM_EUNSTABLE (after copying) if a step flagged a bad density. */
+int lbm_get_populations(lbm_handle* h, double* f);
+
+/*
+ * Advance n >= 0 time steps (Eqs. 1-7 with the forcing of Eq. 25, Sec. II-III).  Each
+ * step is one launch of the fused kernel; runs of steps are replayed from a CUDA graph.
+ * Asynchronous: returns once the work is queued.  Status is reported by lbm_sync and by
+ * every synchronous call.
+ */
+int lbm_step(lbm_handle* h, int n);
+
+/* Wait for queued work; LBM_EUNSTABLE if any step met a non-finite or non-positive
+ * density since the last init. */
+int lbm_sync(lbm_handle* h);
+
+/* Density and velocity of Eq. 6 (rho v = sum e f + F/2) into host (ny, nx) doubles;
+ * any pointer may be NULL.  Synchronous. */
+int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy);
+
+/* Same into caller-owned device arrays of (ny, nx) elements of the storage type
+ * (double for LBM_FP64, float for LBM_FP32_DEV); any pointer may be NULL.  Queued on the
+ * handle's stream, not synchronised. */
+int lbm_moments_device(lbm_handle* h, void* rho, void* ux, void* uy);
+
+/* Global diagnostics of the current state (see lbm_diag).  Each call also stores rho as
+ * the reference of the next call's dinf.  Synchronous. */
+int lbm_diagnostics(lbm_handle* h, lbm_diag* out);
+
+/* Number of steps since the last init/set/load. */
+long long lbm_step_count(const lbm_handle* h);
+
+/* psi of Eqs. 24 and 30 as the step kernel evaluates it (in the handle's precision and
+ * psi mode), for n host densities; output in host doubles.  Synchronous. */
+int lbm_eval_psi(lbm_handle* h, const double* rho, double* psi, size_t n);
+
+/* Write the state (populations in storage format, parameters, step counter) to path with
+ * a CRC-32; lbm_load restores it into a handle created with the same nx, ny and
+ * precision (LBM_EINVAL otherwise, LBM_EIO on a short read or bad checksum). */
+int lbm_save(lbm_handle* h, const char* path);
+int lbm_load(lbm_handle* h, const char* path);
+
+/* Kernel configuration in use: columns per thread and rows per CTA sweep. */
+int lbm_get_tiling(const lbm_handle* h, int* vec, int* rows);
+/* Change it (same meaning as the lbm_options fields; 0 picks the default). */
+int lbm_set_tiling(lbm_handle* h, int vec, int rows);
+
+/* The CUDA stream the handle queues work on (a cudaStream_t). */
+void* lbm_stream(const lbm_handle* h);
+
+/*
+ * Maxwell equal-area construction (Eq. 22) for the Carnahan-Starling EOS (Eq. 30):
+ * coexistence densities rho_l > rho_v at temperature eos.T.  Host-only; uses the closed
+ * form of int p / rho^2 d rho.  LBM_EINVAL if T is not below the critical temperature or
+ * a parameter is not positive.
+ */
+int lbm_maxwell(lbm_eos eos, double* rho_l, double* rho_v);
+
+/* ---------------------------------------------------------------------------------- */
+/* Batches: many independent lattices (uneven sizes, own EOS and rates) advanced by one
+ * kernel launch per step. */
+
+typedef struct lbm_batch lbm_batch;
+
+/* One instance of a batch; the fields mean what the lbm_create arguments mean. */
+typedef struct {
+  int nx, ny;
+  lbm_eos eos;
+  double G, sigma;
+  double s[9];
+  double nu_l, nu_v;
+  int visc_mode;   /* LBM_VISC_* (no automatic choice here) */
+  int bc;          /* LBM_BC_* */
+  double rho_c;    /* <= 0: 0.5218 / b */
+  double rho_l;    /* <= 0: Maxwell */
+  double rho_v;
+  double rho_ref;  /* < 0: Maxwell vapour density (FP32_DEV only) */
+} lbm_instance;
+
+/* Create a batch of n >= 1 instances in one precision; stream may be NULL; device,
+ * tile_vec and tile_rows as in lbm_options (-1, 0, 0 = defaults). */
+int lbm_batch_create(lbm_batch** out, int n, const lbm_instance* inst, int precision,
+                     void* stream, int device, int tile_vec, int tile_rows);
+void lbm_batch_destroy(lbm_batch* b);
+const char* lbm_batch_last_error(const lbm_batch* b);
+
+/* Equilibrium initialisation of instance i from host fields, as lbm_init_fields. */
+int lbm_batch_init_fields(lbm_batch* b, int i, const double* rho, const double* ux,
+                          const double* uy);
+/* Advance every active instance n steps (one launch per step, CUDA-graph replay). */
+int lbm_batch_step(lbm_batch* b, int n);
+/* Host moments of instance i, as lbm_moments. */
+int lbm_batch_moments(lbm_batch* b, int i, double* rho, double* ux, double* uy);
+/* Host populations of instance i, as lbm_get_populations. */
+int lbm_batch_get_populations(lbm_batch* b, int i, double* f);
+/* Per-instance diagnostics (out has n entries), as lbm_diagnostics. */
+int lbm_batch_diagnostics(lbm_batch* b, lbm_diag* out);
+
+/*
+ * Step until every instance is converged: an instance converges at the first check
+ * where max |rho - rho 'check_every' steps earlier| < tol, after which it stops being
+ * stepped (its state is frozen).  Checks run every check_every steps; at most max_steps
+ * steps are taken.  steps_out (n entries, may be NULL) receives each instance's step
+ * count at convergence, or -1 if it did not converge.  Returns the number of unconverged
+ * instances (>= 0) or a negative error.
+ */
+int lbm_batch_run_to_equilibrium(lbm_batch* b, double tol, int check_every,
+                                 long long max_steps, long long* steps_out);
+
+/* Number of instances still being stepped. */
+int lbm_batch_active(const lbm_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,1028 @@
+// C ABI of the D2Q9 improved-MRT pseudopotential library (declared in include/lbm.h).
+//
+// Every lattice, single or batched, is an instance of one Batch: the populations of all
+// instances live in two slabs (ping-pong), each instance with its own padded planes; one
+// launch of the fused sweep kernel advances every active instance by one step, and runs of
+// steps are replayed from a captured CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using lbm::InstParams;
+using lbm::MomArgs;
+using lbm::WorkItem;
+
+namespace {
+
+constexpr int kGraphSteps = 64;  // even, so a replay returns to the same slab
+thread_local std::string g_thread_err;
+
+struct Batch {
+  bool fp64 = false;
+  size_t esz = 4;
+  int n_inst = 0;
+  std::vector<InstParams> inst;
+  std::vector<int> active;
+  std::vector<long long> steps;
+  std::vector<char> dinf_valid;
+  InstParams* d_inst = nullptr;
+  std::vector<WorkItem> items;  // active instances only
+  WorkItem* d_items = nullptr;
+  int n_items = 0, cap_items = 0;
+  std::vector<WorkItem> all_items;  // every instance, for diagnostics
+  WorkItem* d_all_items = nullptr;
+  int n_all = 0;
+  std::vector<int> item_begin;  // per instance, into all_items
+  int* d_item_begin = nullptr;
+  void* slab[2] = {nullptr, nullptr};
+  size_t slab_elems = 0;
+  int cur = 0;
+  size_t dense_elems = 0;
+  void* rho_prev = nullptr;
+  void* fields[3] = {nullptr, nullptr, nullptr};
+  double* d_part_sum = nullptr;
+  float* d_part_max = nullptr;
+  int* d_part_bad = nullptr;
+  double* d_diag = nullptr;
+  int* d_status = nullptr;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaStream_t cap_stream = nullptr;
+  int vec = 0, rows_req = 0, rows = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  std::string err;
+  int sms = 0;
+  int device = -1;
+};
+
+// Makes the batch's device current for the duration of a public call.
+struct DeviceGuard {
+  explicit DeviceGuard(const Batch* b) {
+    if (b && b->device >= 0) cudaSetDevice(b->device);
+  }
+};
+
+int set_err(std::string& dst, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  dst = buf;
+  return code;
+}
+
+#define CK(b, call)                                                                    \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return set_err((b)->err, e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, \
+                     "%s failed: %s", #call, cudaGetErrorString(e_));                  \
+  } while (0)
+
+size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
+
+template <typename T>
+void free_dev(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+void drop_graphs(Batch* b) {
+  for (auto& g : b->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+void destroy_batch(Batch* b) {
+  if (!b) return;
+  DeviceGuard g(b);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  drop_graphs(b);
+  free_dev(b->d_inst);
+  free_dev(b->d_items);
+  free_dev(b->d_all_items);
+  free_dev(b->d_item_begin);
+  free_dev(b->slab[0]);
+  free_dev(b->slab[1]);
+  free_dev(b->rho_prev);
+  for (auto& f : b->fields) free_dev(f);
+  free_dev(b->d_part_sum);
+  free_dev(b->d_part_max);
+  free_dev(b->d_part_bad);
+  free_dev(b->d_diag);
+  free_dev(b->d_status);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  b->stream = nullptr;
+}
+
+int sweep_occupancy(const Batch* b) {
+  return b->fp64 ? lbm::sweep_occupancy<double>(b->vec) : lbm::sweep_occupancy<float>(b->vec);
+}
+
+// Rows per CTA sweep: enough work items for one full wave of resident CTAs.
+int default_rows(const Batch* b) {
+  const int W = (lbm::NT - 2) * b->vec;
+  long long strip_rows = 0;
+  for (int i = 0; i < b->n_inst; ++i)
+    if (b->active[i]) strip_rows += (long long)((b->inst[i].nx + W - 1) / W) * b->inst[i].ny;
+  const long long target = (long long)std::max(b->sms, 1) * sweep_occupancy(b);
+  long long r = (strip_rows + target - 1) / std::max(target, 1LL);
+  return (int)std::max<long long>(4, r);
+}
+
+void make_items(const Batch* b, bool only_active, int rows, std::vector<WorkItem>& out,
+                std::vector<int>* begin) {
+  const int W = (lbm::NT - 2) * b->vec;
+  out.clear();
+  if (begin) begin->assign(1, 0);
+  for (int i = 0; i < b->n_inst; ++i) {
+    if (!only_active || b->active[i]) {
+      const InstParams& P = b->inst[i];
+      const int strips = (P.nx + W - 1) / W;
+      const int chunks = (P.ny + rows - 1) / rows;
+      for (int c = 0; c < chunks; ++c)
+        for (int s = 0; s < strips; ++s) {
+          WorkItem w{};
+          w.inst = i;
+          w.x0 = s * W;
+          w.y0 = c * rows;
+          w.y1 = std::min(P.ny, (c + 1) * rows);
+          w.dir = (c & 1) ? -1 : 1;
+          out.push_back(w);
+        }
+    }
+    if (begin) begin->push_back((int)out.size());
+  }
+}
+
+// Rebuild and upload the work lists (after a tiling change or a retirement).
+int rebuild_items(Batch* b) {
+  drop_graphs(b);
+  if (b->stream) CK(b, cudaStreamSynchronize(b->stream));
+  b->rows = b->rows_req > 0 ? b->rows_req : default_rows(b);
+  make_items(b, true, b->rows, b->items, nullptr);
+  make_items(b, false, b->rows, b->all_items, &b->item_begin);
+  b->n_items = (int)b->items.size();
+  const int n_all = (int)b->all_items.size();
+  if (n_all > b->n_all || !b->d_all_items) {
+    free_dev(b->d_all_items);
+    free_dev(b->d_items);
+    free_dev(b->d_part_sum);
+    free_dev(b->d_part_max);
+    free_dev(b->d_part_bad);
+    CK(b, cudaMalloc(&b->d_all_items, sizeof(WorkItem) * std::max(n_all, 1)));
+    CK(b, cudaMalloc(&b->d_items, sizeof(WorkItem) * std::max(n_all, 1)));
+    CK(b, cudaMalloc(&b->d_part_sum, sizeof(double) * 3 * std::max(n_all, 1)));
+    CK(b, cudaMalloc(&b->d_part_max, sizeof(float) * 2 * std::max(n_all, 1)));
+    CK(b, cudaMalloc(&b->d_part_bad, sizeof(int) * std::max(n_all, 1)));
+  }
+  b->n_all = n_all;
+  CK(b, cudaMemcpy(b->d_all_items, b->all_items.data(), sizeof(WorkItem) * n_all,
+                   cudaMemcpyHostToDevice));
+  if (b->n_items)
+    CK(b, cudaMemcpy(b->d_items, b->items.data(), sizeof(WorkItem) * b->n_items,
+                     cudaMemcpyHostToDevice));
+  if (!b->d_item_begin) CK(b, cudaMalloc(&b->d_item_begin, sizeof(int) * (b->n_inst + 1)));
+  CK(b, cudaMemcpy(b->d_item_begin, b->item_begin.data(), sizeof(int) * (b->n_inst + 1),
+                   cudaMemcpyHostToDevice));
+  return LBM_OK;
+}
+
+// Fill the device parameters of one instance; validates the physical arguments.
+int fill_params(std::string& err, InstParams& P, const lbm_instance& in, bool fp64,
+                int psi_fp64) {
+  if (in.nx < 1 || in.ny < 1) return set_err(err, LBM_EINVAL, "nx, ny must be >= 1");
+  if (!(in.eos.a > 0) || !(in.eos.b > 0) || !(in.eos.R > 0) || !(in.eos.T > 0))
+    return set_err(err, LBM_EINVAL, "EOS parameters a, b, R, T must be positive");
+  if (!(in.G != 0) || !std::isfinite(in.G)) return set_err(err, LBM_EINVAL, "G must be nonzero");
+  if (!std::isfinite(in.sigma)) return set_err(err, LBM_EINVAL, "sigma must be finite");
+  for (int i = 0; i < 9; ++i)
+    if (!(in.s[i] > 0 && in.s[i] < 2))
+      return set_err(err, LBM_EINVAL, "s[%d] = %g is not in (0, 2)", i, in.s[i]);
+  if (in.visc_mode < LBM_VISC_CONST || in.visc_mode > LBM_VISC_LINEAR)
+    return set_err(err, LBM_EINVAL, "unknown viscosity mode %d", in.visc_mode);
+  if (in.visc_mode != LBM_VISC_CONST && !(in.nu_l > 0 && in.nu_v > 0))
+    return set_err(err, LBM_EINVAL, "nu_l and nu_v must be positive for this viscosity mode");
+  if (in.bc != LBM_BC_PERIODIC && in.bc != LBM_BC_WALLS_Y)
+    return set_err(err, LBM_EINVAL, "unknown boundary %d", in.bc);
+  std::memset(&P, 0, sizeof P);
+  P.nx = in.nx;
+  P.ny = in.ny;
+  P.pitch = (int)round_up((size_t)in.nx, 4);
+  P.plane = (long long)in.ny * P.pitch;
+  P.walls = in.bc == LBM_BC_WALLS_Y;
+  P.visc_mode = in.visc_mode;
+  P.psi_fp64 = fp64 ? 0 : psi_fp64;
+  P.b4 = in.eos.b / 4.0;
+  P.RT = in.eos.R * in.eos.T;
+  P.a = in.eos.a;
+  P.two_over_G = 2.0 / in.G;
+  P.G = in.G;
+  for (int i = 0; i < 9; ++i) P.s[i] = in.s[i];
+  P.sig12_e = 12.0 * in.sigma * in.s[1];
+  P.sig12_z = 12.0 * in.sigma * in.s[2];
+  P.tau_l = 3.0 * in.nu_l + 0.5;
+  P.tau_v = 3.0 * in.nu_v + 0.5;
+  P.rho_c = in.rho_c > 0 ? in.rho_c : 0.5218 / in.eos.b;
+  double rl = in.rho_l, rv = in.rho_v;
+  const bool need_maxwell = (in.visc_mode == LBM_VISC_LINEAR && (rl <= 0 || rv <= 0)) ||
+                            (!fp64 && in.rho_ref < 0);
+  double ml = 0, mv = 0;
+  const bool have_maxwell = need_maxwell && lbm_maxwell(in.eos, &ml, &mv) == LBM_OK;
+  if (in.visc_mode == LBM_VISC_LINEAR) {
+    if (rl <= 0 || rv <= 0) {
+      if (!have_maxwell)
+        return set_err(err, LBM_EINVAL,
+                       "LINEAR viscosity needs rho_l, rho_v (no Maxwell solution at this T)");
+      rl = ml;
+      rv = mv;
+    }
+    if (!(rl > rv)) return set_err(err, LBM_EINVAL, "LINEAR viscosity needs rho_l > rho_v");
+  }
+  P.rho_l = rl;
+  P.rho_v = rv;
+  P.rho_ref = fp64 ? 0.0 : (in.rho_ref >= 0 ? in.rho_ref : (have_maxwell ? mv : 0.0));
+  return LBM_OK;
+}
+
+
+int create_batch(Batch* b, int n, const lbm_instance* in, bool fp64, int psi_fp64,
+                 void* stream, int device, int vec, int rows) {
+  if (n < 1 || !in) return set_err(b->err, LBM_EINVAL, "need at least one instance");
+  if (vec != 0 && !lbm::vec_supported(fp64, vec))
+    return set_err(b->err, LBM_EINVAL, "tile_vec %d not available for this precision", vec);
+  if (rows < 0) return set_err(b->err, LBM_EINVAL, "tile_rows must be >= 0");
+  b->fp64 = fp64;
+  b->esz = fp64 ? sizeof(double) : sizeof(float);
+  b->n_inst = n;
+  b->inst.resize(n);
+  b->active.assign(n, 1);
+  b->steps.assign(n, 0);
+  b->dinf_valid.assign(n, 0);
+  size_t off = 0, dense = 0;
+  for (int i = 0; i < n; ++i) {
+    int rc = fill_params(b->err, b->inst[i], in[i], fp64, psi_fp64);
+    if (rc) return rc;
+    b->inst[i].off = (long long)off;
+    b->inst[i].dense_off = (long long)dense;
+    // Keep every instance's block 256-byte aligned.
+    off += round_up((size_t)9 * (size_t)b->inst[i].plane, 64);
+    dense += (size_t)in[i].nx * (size_t)in[i].ny;
+  }
+  b->slab_elems = off;
+  b->dense_elems = dense;
+  b->vec = vec ? vec : (fp64 ? 1 : 4);
+  b->rows_req = rows;
+  int dev_count = 0;
+  if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1)
+    return set_err(b->err, LBM_ECUDA, "no CUDA device available");
+  int dev = 0;
+  if (device >= 0) {
+    if (device >= dev_count) return set_err(b->err, LBM_EINVAL, "device %d out of range", device);
+    CK(b, cudaSetDevice(device));
+  }
+  CK(b, cudaGetDevice(&dev));
+  b->device = dev;
+  CK(b, cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev));
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {
+    CK(b, cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+    b->own_stream = true;
+  }
+  CK(b, cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+  for (int k = 0; k < 2; ++k) {
+    CK(b, cudaMalloc(&b->slab[k], b->slab_elems * b->esz));
+    CK(b, cudaMemsetAsync(b->slab[k], 0, b->slab_elems * b->esz, b->stream));
+  }
+  CK(b, cudaMalloc(&b->rho_prev, b->dense_elems * b->esz));
+  CK(b, cudaMalloc(&b->d_inst, sizeof(InstParams) * n));
+  CK(b, cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(InstParams) * n,
+                        cudaMemcpyHostToDevice, b->stream));
+  CK(b, cudaMalloc(&b->d_diag, sizeof(double) * 6 * n));
+  CK(b, cudaMalloc(&b->d_status, sizeof(int)));
+  CK(b, cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream));
+  return rebuild_items(b);
+}
+
+int launch_step(Batch* b, cudaStream_t st) {
+  const int c = b->cur;
+  cudaError_t e;
+  if (b->fp64) {
+    MomArgs<double> mo{};
+    e = lbm::launch_sweep<double>(b->vec, lbm::MODE_STEP, (const double*)b->slab[c],
+                                  (double*)b->slab[c ^ 1], b->d_inst, b->d_items, b->n_items,
+                                  mo, b->d_status, st);
+  } else {
+    MomArgs<float> mo{};
+    e = lbm::launch_sweep<float>(b->vec, lbm::MODE_STEP, (const float*)b->slab[c],
+                                 (float*)b->slab[c ^ 1], b->d_inst, b->d_items, b->n_items,
+                                 mo, b->d_status, st);
+  }
+  if (e != cudaSuccess)
+    return set_err(b->err, LBM_ECUDA, "step kernel launch failed: %s", cudaGetErrorString(e));
+  b->cur ^= 1;
+  return LBM_OK;
+}
+
+// Capture kGraphSteps consecutive steps that start from slab `start`.
+int capture_graph(Batch* b, int start) {
+  const int saved = b->cur;
+  b->cur = start;
+  cudaGraph_t g = nullptr;
+  CK(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = LBM_OK;
+  for (int k = 0; k < kGraphSteps && rc == LBM_OK; ++k) rc = launch_step(b, b->cap_stream);
+  cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+  b->cur = saved;
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess)
+    return set_err(b->err, LBM_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&b->graph[start], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    b->graph[start] = nullptr;
+    return set_err(b->err, LBM_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+  }
+  return LBM_OK;
+}
+
+int do_steps(Batch* b, long long n) {
+  if (n < 0) return set_err(b->err, LBM_EINVAL, "step count must be >= 0");
+  if (b->n_items == 0) return LBM_OK;
+  const long long n0 = n;
+  while (n > 0) {
+    if (n >= kGraphSteps) {
+      if (!b->graph[b->cur]) {
+        int rc = capture_graph(b, b->cur);
+        if (rc) return rc;
+      }
+      CK(b, cudaGraphLaunch(b->graph[b->cur], b->stream));
+      n -= kGraphSteps;
+    } else {
+      int rc = launch_step(b, b->stream);
+      if (rc) return rc;
+      --n;
+    }
+  }
+  for (int i = 0; i < b->n_inst; ++i)
+    if (b->active[i]) b->steps[i] += n0;
+  return LBM_OK;
+}
+
+int sync_status(Batch* b) {
+  CK(b, cudaStreamSynchronize(b->stream));
+  int st = 0;
+  CK(b, cudaMemcpy(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st & lbm::STATUS_NONFINITE)
+    return set_err(b->err, LBM_EUNSTABLE,
+                   "a density became non-finite or non-positive during stepping");
+  return LBM_OK;
+}
+
+// Device scratch of `bytes`, freed by the caller.
+int dev_alloc(Batch* b, void** p, size_t bytes) {
+  CK(b, cudaMalloc(p, std::max<size_t>(bytes, 16)));
+  return LBM_OK;
+}
+
+int init_instance(Batch* b, int i, const double* rho, const double* ux, const double* uy,
+                  bool device_ptrs) {
+  if (i < 0 || i >= b->n_inst) return set_err(b->err, LBM_EINVAL, "instance %d out of range", i);
+  if (!rho) return set_err(b->err, LBM_EINVAL, "rho must not be NULL");
+  const InstParams& P = b->inst[i];
+  const size_t N = (size_t)P.nx * P.ny;
+  const double *dr = rho, *du = ux, *dv = uy;
+  void* tmp = nullptr;
+  int* dbad = nullptr;
+  int rc = LBM_OK;
+  if (!device_ptrs) {
+    const int nf = 1 + (ux ? 1 : 0) + (uy ? 1 : 0);
+    rc = dev_alloc(b, &tmp, nf * N * sizeof(double));
+    if (rc) return rc;
+    double* t = (double*)tmp;
+    cudaMemcpyAsync(t, rho, N * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+    dr = t;
+    t += N;
+    if (ux) {
+      cudaMemcpyAsync(t, ux, N * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+      du = t;
+      t += N;
+    }
+    if (uy) {
+      cudaMemcpyAsync(t, uy, N * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+      dv = t;
+    }
+  }
+  rc = dev_alloc(b, (void**)&dbad, sizeof(int));
+  if (rc) {
+    cudaFree(tmp);
+    return rc;
+  }
+  cudaMemsetAsync(dbad, 0, sizeof(int), b->stream);
+  cudaError_t e;
+  if (b->fp64)
+    e = lbm::launch_init_eq<double>(dr, du, dv, (double*)b->slab[b->cur], P, dbad, b->stream);
+  else
+    e = lbm::launch_init_eq<float>(dr, du, dv, (float*)b->slab[b->cur], P, dbad, b->stream);
+  int bad = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  cudaFree(tmp);
+  cudaFree(dbad);
+  if (e != cudaSuccess)
+    return set_err(b->err, LBM_ECUDA, "initialisation failed: %s", cudaGetErrorString(e));
+  // The other slab mirrors the state so frozen and active instances agree.
+  CK(b, cudaMemcpyAsync((char*)b->slab[b->cur ^ 1] + P.off * b->esz,
+                        (char*)b->slab[b->cur] + P.off * b->esz, 9 * P.plane * b->esz,
+                        cudaMemcpyDeviceToDevice, b->stream));
+  CK(b, cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream));
+  CK(b, cudaStreamSynchronize(b->stream));
+  b->steps[i] = 0;
+  b->dinf_valid[i] = 0;
+  if (!b->active[i]) {
+    b->active[i] = 1;
+    rc = rebuild_items(b);
+    if (rc) return rc;
+  }
+  if (bad)
+    return set_err(b->err, LBM_EINVAL,
+                   "%d nodes have a density outside (0, 4/b), a negative psi^2 (Eq. 24) or "
+                   "a non-finite velocity", bad);
+  return LBM_OK;
+}
+
+int set_pops(Batch* b, int i, const double* f) {
+  if (!f) return set_err(b->err, LBM_EINVAL, "f must not be NULL");
+  const InstParams& P = b->inst[i];
+  const size_t N = (size_t)P.nx * P.ny;
+  void* tmp = nullptr;
+  int rc = dev_alloc(b, &tmp, 9 * N * sizeof(double));
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpyAsync(tmp, f, 9 * N * sizeof(double), cudaMemcpyHostToDevice,
+                                  b->stream);
+  if (e == cudaSuccess)
+    e = b->fp64 ? lbm::launch_set_pops<double>((double*)tmp, (double*)b->slab[b->cur], P, b->stream)
+                : lbm::launch_set_pops<float>((double*)tmp, (float*)b->slab[b->cur], P, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync((char*)b->slab[b->cur ^ 1] + P.off * b->esz,
+                        (char*)b->slab[b->cur] + P.off * b->esz, 9 * P.plane * b->esz,
+                        cudaMemcpyDeviceToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  cudaFree(tmp);
+  if (e != cudaSuccess)
+    return set_err(b->err, LBM_ECUDA, "set populations failed: %s", cudaGetErrorString(e));
+  b->steps[i] = 0;
+  b->dinf_valid[i] = 0;
+  return LBM_OK;
+}
+
+int get_pops(Batch* b, int i, double* f) {
+  if (!f) return set_err(b->err, LBM_EINVAL, "f must not be NULL");
+  const InstParams& P = b->inst[i];
+  const size_t N = (size_t)P.nx * P.ny;
+  void* tmp = nullptr;
+  int rc = dev_alloc(b, &tmp, 9 * N * sizeof(double));
+  if (rc) return rc;
+  cudaError_t e = b->fp64
+      ? lbm::launch_get_pops<double>((const double*)b->slab[b->cur], (double*)tmp, P, b->stream)
+      : lbm::launch_get_pops<float>((const float*)b->slab[b->cur], (double*)tmp, P, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(f, tmp, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  cudaFree(tmp);
+  if (e != cudaSuccess)
+    return set_err(b->err, LBM_ECUDA, "get populations failed: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+// Moments/diagnostics pass over `items` (device list of n entries).
+template <typename S>
+int moments_pass(Batch* b, const WorkItem* d_items, int n, MomArgs<S> mo) {
+  mo.part_sum = b->d_part_sum;
+  mo.part_max = b->d_part_max;
+  mo.part_bad = b->d_part_bad;
+  cudaError_t e = lbm::launch_sweep<S>(b->vec, lbm::MODE_MOMENTS, (const S*)b->slab[b->cur],
+                                       nullptr, b->d_inst, d_items, n, mo, b->d_status,
+                                       b->stream);
+  if (e != cudaSuccess)
+    return set_err(b->err, LBM_ECUDA, "moments kernel launch failed: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+int ensure_fields(Batch* b) {
+  for (auto& f : b->fields)
+    if (!f) CK(b, cudaMalloc(&f, std::max<size_t>(b->dense_elems, 1) * b->esz));
+  return LBM_OK;
+}
+
+// Fields of instance i into device arrays (storage type) at the instance's dense offset
+// (or, with direct pointers, at offset 0 of the caller's arrays).
+int moments_device(Batch* b, int i, void* rho, void* ux, void* uy, bool caller_ptrs) {
+  const int lo = b->item_begin[i], hi = b->item_begin[i + 1];
+  const long long shift = caller_ptrs ? b->inst[i].dense_off : 0;
+  if (b->fp64) {
+    MomArgs<double> mo{};
+    mo.rho = rho ? (double*)rho - shift : nullptr;
+    mo.ux = ux ? (double*)ux - shift : nullptr;
+    mo.uy = uy ? (double*)uy - shift : nullptr;
+    mo.flags = lbm::MOM_FIELDS;
+    return moments_pass<double>(b, b->d_all_items + lo, hi - lo, mo);
+  }
+  MomArgs<float> mo{};
+  mo.rho = rho ? (float*)rho - shift : nullptr;
+  mo.ux = ux ? (float*)ux - shift : nullptr;
+  mo.uy = uy ? (float*)uy - shift : nullptr;
+  mo.flags = lbm::MOM_FIELDS;
+  return moments_pass<float>(b, b->d_all_items + lo, hi - lo, mo);
+}
+
+int moments_host(Batch* b, int i, double* rho, double* ux, double* uy) {
+  int rc = ensure_fields(b);
+  if (rc) return rc;
+  rc = moments_device(b, i, rho ? b->fields[0] : nullptr, ux ? b->fields[1] : nullptr,
+                      uy ? b->fields[2] : nullptr, false);
+  if (rc) return rc;
+  const InstParams& P = b->inst[i];
+  const size_t N = (size_t)P.nx * P.ny;
+  double* outs[3] = {rho, ux, uy};
+  std::vector<float> tmp;
+  for (int k = 0; k < 3; ++k) {
+    if (!outs[k]) continue;
+    const char* src = (const char*)b->fields[k] + P.dense_off * b->esz;
+    if (b->fp64) {
+      CK(b, cudaMemcpyAsync(outs[k], src, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    } else {
+      tmp.resize(N);
+      CK(b, cudaMemcpyAsync(tmp.data(), src, N * sizeof(float), cudaMemcpyDeviceToHost, b->stream));
+      CK(b, cudaStreamSynchronize(b->stream));
+      for (size_t n = 0; n < N; ++n) outs[k][n] = tmp[n];
+    }
+  }
+  CK(b, cudaStreamSynchronize(b->stream));
+  return LBM_OK;
+}
+
+// Diagnostics of every instance (out: n_inst entries).
+int diagnostics(Batch* b, lbm_diag* out) {
+  int rc;
+  if (b->fp64) {
+    MomArgs<double> mo{};
+    mo.rho_prev = (double*)b->rho_prev;
+    mo.flags = lbm::MOM_DIAG | lbm::MOM_UPDATE_PREV;
+    rc = moments_pass<double>(b, b->d_all_items, b->n_all, mo);
+  } else {
+    MomArgs<float> mo{};
+    mo.rho_prev = (float*)b->rho_prev;
+    mo.flags = lbm::MOM_DIAG | lbm::MOM_UPDATE_PREV;
+    rc = moments_pass<float>(b, b->d_all_items, b->n_all, mo);
+  }
+  if (rc) return rc;
+  cudaError_t e = lbm::launch_diag_finalize(b->d_part_sum, b->d_part_max, b->d_part_bad,
+                                            b->d_item_begin, b->n_inst, b->d_diag, b->stream);
+  if (e != cudaSuccess)
+    return set_err(b->err, LBM_ECUDA, "diagnostics reduction failed: %s", cudaGetErrorString(e));
+  std::vector<double> h(6 * (size_t)b->n_inst);
+  CK(b, cudaMemcpyAsync(h.data(), b->d_diag, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
+                        b->stream));
+  CK(b, cudaStreamSynchronize(b->stream));
+  for (int i = 0; i < b->n_inst; ++i) {
+    out[i].mass = h[6 * i];
+    out[i].mom_x = h[6 * i + 1];
+    out[i].mom_y = h[6 * i + 2];
+    out[i].max_u = h[6 * i + 3];
+    out[i].dinf = b->dinf_valid[i] ? h[6 * i + 4] : -1.0;
+    out[i].nonfinite = (long long)h[6 * i + 5];
+    out[i].step = b->steps[i];
+    b->dinf_valid[i] = 1;
+  }
+  return LBM_OK;
+}
+
+// Stop stepping instance i; both slabs then hold its state.
+int freeze(Batch* b, int i) {
+  const InstParams& P = b->inst[i];
+  CK(b, cudaMemcpyAsync((char*)b->slab[b->cur ^ 1] + P.off * b->esz,
+                        (char*)b->slab[b->cur] + P.off * b->esz, 9 * P.plane * b->esz,
+                        cudaMemcpyDeviceToDevice, b->stream));
+  b->active[i] = 0;
+  return LBM_OK;
+}
+
+int eval_psi(Batch* b, const double* rho, double* psi, size_t n) {
+  if (!rho || !psi) return set_err(b->err, LBM_EINVAL, "rho and psi must not be NULL");
+  if (n == 0) return LBM_OK;
+  void* tmp = nullptr;
+  int rc = dev_alloc(b, &tmp, 2 * n * sizeof(double));
+  if (rc) return rc;
+  double* dr = (double*)tmp;
+  double* dp = dr + n;
+  cudaError_t e = cudaMemcpyAsync(dr, rho, n * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = b->fp64 ? lbm::launch_psi<double>(dr, dp, (long long)n, b->d_inst, b->stream)
+                : lbm::launch_psi<float>(dr, dp, (long long)n, b->d_inst, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(psi, dp, n * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return set_err(b->err, LBM_ECUDA, "psi evaluation failed: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+// CRC-32 (IEEE 802.3 polynomial, reflected), bytewise.
+uint32_t crc32_update(uint32_t crc, const void* data, size_t n) {
+  const unsigned char* p = (const unsigned char*)data;
+  crc = ~crc;
+  for (size_t i = 0; i < n; ++i) {
+    crc ^= p[i];
+    for (int k = 0; k < 8; ++k) crc = (crc >> 1) ^ (0xEDB88320u & (0u - (crc & 1u)));
+  }
+  return ~crc;
+}
+
+struct FileHeader {
+  char magic[8];
+  uint32_t version, precision;
+  int32_t nx, ny, pitch, walls;
+  int64_t step;
+  uint64_t payload_bytes;
+  InstParams params;
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Single-lattice handle
+
+struct lbm_handle {
+  Batch b;
+};
+struct lbm_batch {
+  Batch b;
+};
+
+extern "C" {
+
+void lbm_options_default(lbm_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->precision = LBM_FP32_DEV;
+  o->visc_mode = -1;
+  o->bc = LBM_BC_PERIODIC;
+  o->psi_fp64 = 0;
+  o->rho_ref = -1.0;
+  o->rho_c = 0.0;
+  o->rho_l = 0.0;
+  o->rho_v = 0.0;
+  o->stream = nullptr;
+  o->device = -1;
+  o->tile_vec = 0;
+  o->tile_rows = 0;
+}
+
+int lbm_create(lbm_handle** out, int nx, int ny, lbm_eos eos, double G, double sigma,
+               const double s[9], double nu_l, double nu_v, const lbm_options* opt) {
+  if (!out || !s) return set_err(g_thread_err, LBM_EINVAL, "out and s must not be NULL");
+  *out = nullptr;
+  lbm_options o;
+  lbm_options_default(&o);
+  if (opt) o = *opt;
+  if (o.precision != LBM_FP64 && o.precision != LBM_FP32_DEV)
+    return set_err(g_thread_err, LBM_EINVAL, "unknown precision %d", o.precision);
+  lbm_instance in{};
+  in.nx = nx;
+  in.ny = ny;
+  in.eos = eos;
+  in.G = G;
+  in.sigma = sigma;
+  for (int i = 0; i < 9; ++i) in.s[i] = s[i];
+  in.nu_l = nu_l;
+  in.nu_v = nu_v;
+  in.visc_mode = o.visc_mode >= 0 ? o.visc_mode
+                                  : ((nu_l > 0 && nu_v > 0) ? LBM_VISC_STEP : LBM_VISC_CONST);
+  in.bc = o.bc;
+  in.rho_c = o.rho_c;
+  in.rho_l = o.rho_l;
+  in.rho_v = o.rho_v;
+  in.rho_ref = o.rho_ref;
+  lbm_handle* h = new (std::nothrow) lbm_handle();
+  if (!h) return set_err(g_thread_err, LBM_ENOMEM, "out of host memory");
+  int rc = create_batch(&h->b, 1, &in, o.precision == LBM_FP64, o.psi_fp64, o.stream,
+                        o.device, o.tile_vec, o.tile_rows);
+  if (rc) {
+    g_thread_err = h->b.err;
+    destroy_batch(&h->b);
+    delete h;
+    return rc;
+  }
+  g_thread_err.clear();
+  *out = h;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle* h) {
+  if (!h) return;
+  destroy_batch(&h->b);
+  delete h;
+}
+
+const char* lbm_last_error(const lbm_handle* h) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  return h ? h->b.err.c_str() : g_thread_err.c_str();
+}
+
+int lbm_init_fields(lbm_handle* h, const double* rho, const double* ux, const double* uy) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  return init_instance(&h->b, 0, rho, ux, uy, false);
+}
+
+int lbm_init_fields_device(lbm_handle* h, const double* rho, const double* ux,
+                           const double* uy) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  return init_instance(&h->b, 0, rho, ux, uy, true);
+}
+
+int lbm_set_populations(lbm_handle* h, const double* f) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  return set_pops(&h->b, 0, f);
+}
+
+int lbm_get_populations(lbm_handle* h, double* f) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  int rc = get_pops(&h->b, 0, f);
+  if (rc) return rc;
+  return sync_status(&h->b);
+}
+
+int lbm_step(lbm_handle* h, int n) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  return do_steps(&h->b, n);
+}
+
+int lbm_sync(lbm_handle* h) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  return sync_status(&h->b);
+}
+
+int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  int rc = moments_host(&h->b, 0, rho, ux, uy);
+  if (rc) return rc;
+  return sync_status(&h->b);
+}
+
+int lbm_moments_device(lbm_handle* h, void* rho, void* ux, void* uy) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  return moments_device(&h->b, 0, rho, ux, uy, true);
+}
+
+int lbm_diagnostics(lbm_handle* h, lbm_diag* out) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h || !out) return h ? set_err(h->b.err, LBM_EINVAL, "out must not be NULL") : LBM_EINVAL;
+  return diagnostics(&h->b, out);
+}
+
+long long lbm_step_count(const lbm_handle* h) { return h ? h->b.steps[0] : -1; }
+
+int lbm_eval_psi(lbm_handle* h, const double* rho, double* psi, size_t n) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  return eval_psi(&h->b, rho, psi, n);
+}
+
+int lbm_get_tiling(const lbm_handle* h, int* vec, int* rows) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  if (vec) *vec = h->b.vec;
+  if (rows) *rows = h->b.rows;
+  return LBM_OK;
+}
+
+int lbm_set_tiling(lbm_handle* h, int vec, int rows) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  Batch* b = &h->b;
+  if (vec != 0 && !lbm::vec_supported(b->fp64, vec))
+    return set_err(b->err, LBM_EINVAL, "tile_vec %d not available for this precision", vec);
+  if (rows < 0) return set_err(b->err, LBM_EINVAL, "tile_rows must be >= 0");
+  b->vec = vec ? vec : (b->fp64 ? 1 : 4);
+  b->rows_req = rows;
+  return rebuild_items(b);
+}
+
+void* lbm_stream(const lbm_handle* h) { return h ? (void*)h->b.stream : nullptr; }
+
+int lbm_save(lbm_handle* h, const char* path) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h || !path) return LBM_EINVAL;
+  Batch* b = &h->b;
+  const InstParams& P = b->inst[0];
+  const size_t bytes = 9 * (size_t)P.plane * b->esz;
+  std::vector<char> buf(bytes);
+  CK(b, cudaMemcpyAsync(buf.data(), (char*)b->slab[b->cur] + P.off * b->esz, bytes,
+                        cudaMemcpyDeviceToHost, b->stream));
+  CK(b, cudaStreamSynchronize(b->stream));
+  FileHeader hd;
+  std::memset(&hd, 0, sizeof hd);
+  std::memcpy(hd.magic, "LBMSTATE", 8);
+  hd.version = 1;
+  hd.precision = b->fp64 ? LBM_FP64 : LBM_FP32_DEV;
+  hd.nx = P.nx;
+  hd.ny = P.ny;
+  hd.pitch = P.pitch;
+  hd.walls = P.walls;
+  hd.step = b->steps[0];
+  hd.payload_bytes = bytes;
+  hd.params = P;
+  uint32_t crc = crc32_update(0, &hd, sizeof hd);
+  crc = crc32_update(crc, buf.data(), bytes);
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) return set_err(b->err, LBM_EIO, "cannot open %s for writing", path);
+  bool ok = std::fwrite(&hd, sizeof hd, 1, fp) == 1 &&
+            std::fwrite(buf.data(), 1, bytes, fp) == bytes &&
+            std::fwrite(&crc, sizeof crc, 1, fp) == 1;
+  ok = (std::fclose(fp) == 0) && ok;
+  return ok ? LBM_OK : set_err(b->err, LBM_EIO, "short write to %s", path);
+}
+
+int lbm_load(lbm_handle* h, const char* path) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h || !path) return LBM_EINVAL;
+  Batch* b = &h->b;
+  const InstParams& P = b->inst[0];
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return set_err(b->err, LBM_EIO, "cannot open %s", path);
+  FileHeader hd;
+  if (std::fread(&hd, sizeof hd, 1, fp) != 1 || std::memcmp(hd.magic, "LBMSTATE", 8) != 0) {
+    std::fclose(fp);
+    return set_err(b->err, LBM_EIO, "%s is not a state file", path);
+  }
+  if (hd.nx != P.nx || hd.ny != P.ny || hd.pitch != P.pitch ||
+      (int)hd.precision != (b->fp64 ? LBM_FP64 : LBM_FP32_DEV) ||
+      hd.payload_bytes != 9 * (uint64_t)P.plane * b->esz) {
+    std::fclose(fp);
+    return set_err(b->err, LBM_EINVAL, "state file does not match this handle's size/precision");
+  }
+  std::vector<char> buf(hd.payload_bytes);
+  uint32_t crc_file = 0;
+  const bool ok = std::fread(buf.data(), 1, buf.size(), fp) == buf.size() &&
+                  std::fread(&crc_file, sizeof crc_file, 1, fp) == 1;
+  std::fclose(fp);
+  if (!ok) return set_err(b->err, LBM_EIO, "short read from %s", path);
+  uint32_t crc = crc32_update(0, &hd, sizeof hd);
+  crc = crc32_update(crc, buf.data(), buf.size());
+  if (crc != crc_file) return set_err(b->err, LBM_EIO, "checksum mismatch in %s", path);
+  for (int k = 0; k < 2; ++k)
+    CK(b, cudaMemcpyAsync((char*)b->slab[k] + P.off * b->esz, buf.data(), buf.size(),
+                          cudaMemcpyHostToDevice, b->stream));
+  CK(b, cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream));
+  CK(b, cudaStreamSynchronize(b->stream));
+  b->steps[0] = hd.step;
+  b->dinf_valid[0] = 0;
+  return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Batches
+
+int lbm_batch_create(lbm_batch** out, int n, const lbm_instance* inst, int precision,
+                     void* stream, int device, int tile_vec, int tile_rows) {
+  if (!out) return set_err(g_thread_err, LBM_EINVAL, "out must not be NULL");
+  *out = nullptr;
+  if (precision != LBM_FP64 && precision != LBM_FP32_DEV)
+    return set_err(g_thread_err, LBM_EINVAL, "unknown precision %d", precision);
+  lbm_batch* b = new (std::nothrow) lbm_batch();
+  if (!b) return set_err(g_thread_err, LBM_ENOMEM, "out of host memory");
+  int rc = create_batch(&b->b, n, inst, precision == LBM_FP64, 0, stream, device, tile_vec,
+                        tile_rows);
+  if (rc) {
+    g_thread_err = b->b.err;
+    destroy_batch(&b->b);
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return;
+  destroy_batch(&b->b);
+  delete b;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) {
+  DeviceGuard g_(b ? &b->b : nullptr);
+  return b ? b->b.err.c_str() : g_thread_err.c_str();
+}
+
+int lbm_batch_init_fields(lbm_batch* b, int i, const double* rho, const double* ux,
+                          const double* uy) {
+  DeviceGuard g_(b ? &b->b : nullptr);
+  if (!b) return LBM_EINVAL;
+  return init_instance(&b->b, i, rho, ux, uy, false);
+}
+
+int lbm_batch_step(lbm_batch* b, int n) {
+  DeviceGuard g_(b ? &b->b : nullptr);
+  if (!b) return LBM_EINVAL;
+  return do_steps(&b->b, n);
+}
+
+int lbm_batch_moments(lbm_batch* b, int i, double* rho, double* ux, double* uy) {
+  DeviceGuard g_(b ? &b->b : nullptr);
+  if (!b) return LBM_EINVAL;
+  if (i < 0 || i >= b->b.n_inst) return set_err(b->b.err, LBM_EINVAL, "instance out of range");
+  return moments_host(&b->b, i, rho, ux, uy);
+}
+
+int lbm_batch_get_populations(lbm_batch* b, int i, double* f) {
+  DeviceGuard g_(b ? &b->b : nullptr);
+  if (!b) return LBM_EINVAL;
+  if (i < 0 || i >= b->b.n_inst) return set_err(b->b.err, LBM_EINVAL, "instance out of range");
+  return get_pops(&b->b, i, f);
+}
+
+int lbm_batch_diagnostics(lbm_batch* b, lbm_diag* out) {
+  DeviceGuard g_(b ? &b->b : nullptr);
+  if (!b || !out) return LBM_EINVAL;
+  return diagnostics(&b->b, out);
+}
+
+int lbm_batch_active(const lbm_batch* b) {
+  DeviceGuard g_(b ? &b->b : nullptr);
+  if (!b) return LBM_EINVAL;
+  int n = 0;
+  for (int a : b->b.active) n += a;
+  return n;
+}
+
+int lbm_batch_run_to_equilibrium(lbm_batch* bb, double tol, int check_every,
+                                 long long max_steps, long long* steps_out) {
+  DeviceGuard g_(bb ? &bb->b : nullptr);
+  if (!bb) return LBM_EINVAL;
+  Batch* b = &bb->b;
+  if (!(tol > 0) || check_every < 1 || max_steps < 0)
+    return set_err(b->err, LBM_EINVAL, "need tol > 0, check_every >= 1, max_steps >= 0");
+  std::vector<lbm_diag> d(b->n_inst);
+  if (steps_out)
+    for (int i = 0; i < b->n_inst; ++i) steps_out[i] = -1;
+  int rc = diagnostics(b, d.data());  // seeds the dinf reference
+  if (rc) return rc;
+  long long taken = 0;
+  while (taken < max_steps && b->n_items > 0) {
+    const long long k = std::min<long long>(check_every, max_steps - taken);
+    rc = do_steps(b, k);
+    if (rc) return rc;
+    taken += k;
+    rc = diagnostics(b, d.data());
+    if (rc) return rc;
+    bool changed = false;
+    for (int i = 0; i < b->n_inst; ++i) {
+      if (!b->active[i]) continue;
+      const bool bad = d[i].nonfinite > 0;
+      const bool conv = !bad && d[i].dinf >= 0 && d[i].dinf < tol && k == check_every;
+      if (conv || bad) {
+        if (conv && steps_out) steps_out[i] = b->steps[i];
+        rc = freeze(b, i);
+        if (rc) return rc;
+        changed = true;
+      }
+    }
+    if (changed) {
+      rc = rebuild_items(b);
+      if (rc) return rc;
+    }
+  }
+  int left = 0;
+  for (int a : b->active) left += a;
+  return left;
+}
+
+}  // extern "C"

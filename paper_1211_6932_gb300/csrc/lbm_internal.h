@@ -1,0 +1,38 @@
+// Host-side declarations shared by the C-ABI and the kernel translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// Launch the fused sweep (MODE_STEP) or the moments/diagnostics pass (MODE_MOMENTS) over
+// n_items work items; vec selects the columns-per-thread instantiation.
+template <typename S>
+cudaError_t launch_sweep(int vec, int mode, const S* fin, S* fout, const InstParams* d_inst,
+                         const WorkItem* d_items, int n_items, const MomArgs<S>& mo,
+                         int* d_status, cudaStream_t st);
+template <typename S>
+cudaError_t launch_set_pops(const double* d_fc, S* buf, const InstParams& P, cudaStream_t st);
+template <typename S>
+cudaError_t launch_get_pops(const S* buf, double* d_fc, const InstParams& P, cudaStream_t st);
+template <typename S>
+cudaError_t launch_init_eq(const double* rho, const double* ux, const double* uy, S* buf,
+                           const InstParams& P, int* d_bad, cudaStream_t st);
+template <typename S>
+cudaError_t launch_psi(const double* d_rho, double* d_out, long long n,
+                       const InstParams* d_inst, cudaStream_t st);
+cudaError_t launch_diag_finalize(const double* part_sum, const float* part_max,
+                                 const int* part_bad, const int* item_begin, int n_inst,
+                                 double* out, cudaStream_t st);
+
+// Resident CTAs per SM of the step kernel instantiation (at least 1).
+template <typename S>
+int sweep_occupancy(int vec);
+
+// Whether a (storage type, vec) pair has a kernel.
+inline bool vec_supported(bool fp64, int vec) {
+  return vec == 1 || vec == 2 || (vec == 4 && !fp64);
+}
+
+}  // namespace lbm

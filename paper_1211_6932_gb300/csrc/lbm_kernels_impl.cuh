@@ -1,0 +1,64 @@
+// Launchers of the step and helper kernels for one storage type (included once per type).
+#pragma once
+#include "lbm_aux.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+template <typename S, int VEC>
+static cudaError_t launch_sweep_vec(int mode, const S* fin, S* fout, const InstParams* d_inst,
+                                    const WorkItem* d_items, int n_items,
+                                    const MomArgs<S>& mo, int* d_status, cudaStream_t st) {
+  if (n_items <= 0) return cudaSuccess;
+  if (mode == MODE_STEP)
+    sweep_kernel<S, VEC, MODE_STEP><<<n_items, NT, 0, st>>>(fin, fout, d_inst, d_items,
+                                                           n_items, mo, d_status);
+  else
+    sweep_kernel<S, VEC, MODE_MOMENTS><<<n_items, NT, 0, st>>>(fin, fout, d_inst, d_items,
+                                                              n_items, mo, d_status);
+  return cudaGetLastError();
+}
+
+static inline int grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  if (g < 1) g = 1;
+  if (g > 152 * 16) g = 152 * 16;
+  return (int)g;
+}
+
+template <typename S>
+cudaError_t launch_set_pops(const double* d_fc, S* buf, const InstParams& P, cudaStream_t st) {
+  set_pops_kernel<S><<<grid_for((long long)P.nx * P.ny), 256, 0, st>>>(d_fc, buf, P);
+  return cudaGetLastError();
+}
+template <typename S>
+cudaError_t launch_get_pops(const S* buf, double* d_fc, const InstParams& P, cudaStream_t st) {
+  get_pops_kernel<S><<<grid_for((long long)P.nx * P.ny), 256, 0, st>>>(buf, d_fc, P);
+  return cudaGetLastError();
+}
+template <typename S>
+cudaError_t launch_init_eq(const double* rho, const double* ux, const double* uy, S* buf,
+                           const InstParams& P, int* d_bad, cudaStream_t st) {
+  init_eq_kernel<S><<<grid_for((long long)P.nx * P.ny), 256, 0, st>>>(rho, ux, uy, buf, P,
+                                                                      d_bad);
+  return cudaGetLastError();
+}
+template <typename S>
+cudaError_t launch_psi(const double* d_rho, double* d_out, long long n,
+                       const InstParams* d_inst, cudaStream_t st) {
+  psi_kernel<S><<<grid_for(n), 256, 0, st>>>(d_rho, d_out, n, d_inst);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm
+
+#define LBM_INSTANTIATE_HELPERS(S)                                                          \
+  template cudaError_t lbm::launch_set_pops<S>(const double*, S*, const lbm::InstParams&,   \
+                                               cudaStream_t);                               \
+  template cudaError_t lbm::launch_get_pops<S>(const S*, double*, const lbm::InstParams&,   \
+                                               cudaStream_t);                               \
+  template cudaError_t lbm::launch_init_eq<S>(const double*, const double*, const double*,  \
+                                              S*, const lbm::InstParams&, int*,             \
+                                              cudaStream_t);                                \
+  template cudaError_t lbm::launch_psi<S>(const double*, double*, long long,                \
+                                          const lbm::InstParams*, cudaStream_t);

@@ -1,0 +1,332 @@
+"""Python front end of the C ABI (include/lbm.h).  Marshalling only: every step of the
+method runs in the CUDA library."""
+import ctypes
+import dataclasses
+
+import numpy as np
+
+from . import _lib as C
+
+_PREC = {"fp64": C.LBM_FP64, "fp32": C.LBM_FP32_DEV, "fp32_dev": C.LBM_FP32_DEV}
+_VISC = {None: -1, "const": C.LBM_VISC_CONST, "step": C.LBM_VISC_STEP,
+         "linear": C.LBM_VISC_LINEAR}
+_BC = {"periodic": C.LBM_BC_PERIODIC, "walls": C.LBM_BC_WALLS_Y, "walls_y": C.LBM_BC_WALLS_Y}
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("lbm error %d: %s" % (code, msg))
+        self.code = code
+
+
+@dataclasses.dataclass
+class Eos:
+    """Carnahan-Starling parameters (Eq. 30)."""
+    a: float
+    T: float
+    b: float = 4.0
+    R: float = 1.0
+
+    def c(self):
+        return C.lbm_eos(self.a, self.b, self.R, self.T)
+
+
+def _d(a):
+    return a.ctypes.data_as(C.dptr) if a is not None else None
+
+
+def _f64(a, shape):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != shape:
+        raise ValueError("expected shape %s, got %s" % (shape, a.shape))
+    return a
+
+
+def _device_of(stream, device):
+    if device is not None:
+        return int(device)
+    dev = getattr(stream, "device", None)
+    if dev is not None and getattr(dev, "index", None) is not None:
+        return int(dev.index)
+    return -1
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def maxwell(eos: Eos):
+    """Maxwell equal-area coexistence densities (Eq. 22) from the library's host solver."""
+    L = C.lib()
+    rl, rv = ctypes.c_double(), ctypes.c_double()
+    rc = L.lbm_maxwell(eos.c(), ctypes.byref(rl), ctypes.byref(rv))
+    if rc != 0:
+        raise LbmError(rc, "no Maxwell solution (T must be below T_c)")
+    return rl.value, rv.value
+
+
+def _diag_dict(d):
+    return {"mass": d.mass, "mom_x": d.mom_x, "mom_y": d.mom_y, "max_u": d.max_u,
+            "dinf": d.dinf, "step": d.step, "nonfinite": d.nonfinite}
+
+
+class Lattice:
+    """One nx x ny lattice (lbm_create ... lbm_destroy)."""
+
+    def __init__(self, nx, ny, eos: Eos, G=-1.0, sigma=0.0, s=None, nu_l=0.0, nu_v=0.0,
+                 precision="fp32", visc_mode=None, bc="periodic", psi_fp64=False,
+                 rho_ref=None, rho_c=None, rho_l=None, rho_v=None, stream=None, tile_vec=0,
+                 tile_rows=0, device=None):
+        self._L = C.lib()
+        self.nx, self.ny = int(nx), int(ny)
+        self.precision = precision
+        s = (1.0, 1.1, 1.1, 1.0, 1.1, 1.0, 1.1, 1.0, 1.0) if s is None else s
+        sv = (ctypes.c_double * 9)(*[float(v) for v in s])
+        o = C.lbm_options()
+        self._L.lbm_options_default(ctypes.byref(o))
+        o.precision = _PREC[precision]
+        o.visc_mode = _VISC[visc_mode]
+        o.bc = _BC[bc]
+        o.psi_fp64 = int(bool(psi_fp64))
+        if rho_ref is not None:
+            o.rho_ref = float(rho_ref)
+        if rho_c is not None:
+            o.rho_c = float(rho_c)
+        if rho_l is not None:
+            o.rho_l = float(rho_l)
+        if rho_v is not None:
+            o.rho_v = float(rho_v)
+        sp = _stream_ptr(stream)
+        o.stream = sp.value if sp is not None else None
+        o.device = _device_of(stream, device)
+        o.tile_vec = int(tile_vec)
+        o.tile_rows = int(tile_rows)
+        h = ctypes.c_void_p()
+        rc = self._L.lbm_create(ctypes.byref(h), self.nx, self.ny, eos.c(), float(G),
+                                float(sigma), sv, float(nu_l), float(nu_v), ctypes.byref(o))
+        if rc != 0:
+            raise LbmError(rc, self._L.lbm_last_error(None).decode())
+        self._h = h
+        self.stream_keepalive = stream
+
+    # -- helpers -----------------------------------------------------------------------
+    def _check(self, rc):
+        if rc != 0:
+            raise LbmError(rc, self._L.lbm_last_error(self._h).decode())
+        return rc
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def shape(self):
+        return (self.ny, self.nx)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- state ---------------------------------------------------------------------------
+    def init_fields(self, rho, ux=None, uy=None):
+        r = _f64(rho, self.shape)
+        u = _f64(ux, self.shape)
+        v = _f64(uy, self.shape)
+        self._check(self._L.lbm_init_fields(self._h, _d(r), _d(u), _d(v)))
+
+    def init_fields_device(self, rho, ux=None, uy=None):
+        """rho/ux/uy: contiguous float64 CUDA tensors of shape (ny, nx)."""
+        ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())  # noqa: E731
+        self._check(self._L.lbm_init_fields_device(self._h, ptr(rho), ptr(ux), ptr(uy)))
+
+    def set_populations(self, f):
+        f = _f64(f, (9,) + self.shape)
+        self._check(self._L.lbm_set_populations(self._h, _d(f)))
+
+    def get_populations(self):
+        f = np.empty((9,) + self.shape)
+        self._check(self._L.lbm_get_populations(self._h, _d(f)))
+        return f
+
+    def step(self, n=1):
+        self._check(self._L.lbm_step(self._h, int(n)))
+
+    def sync(self):
+        self._check(self._L.lbm_sync(self._h))
+
+    def moments(self, out=None):
+        """rho, ux, uy of Eq. 6 as host arrays.  With out= (a float64 (ny, nx) array, e.g.
+        a pinned buffer) only the density is copied, into out."""
+        if out is not None:
+            if out.dtype != np.float64 or out.shape != self.shape or not out.flags.c_contiguous:
+                raise ValueError("out must be a C-contiguous float64 array of shape %s" % (self.shape,))
+            self._check(self._L.lbm_moments(self._h, _d(out), None, None))
+            return out
+        res = {k: np.empty(self.shape) for k in ("rho", "ux", "uy")}
+        self._check(self._L.lbm_moments(self._h, _d(res["rho"]), _d(res["ux"]), _d(res["uy"])))
+        return res
+
+    def moments_device(self, rho=None, ux=None, uy=None):
+        ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())  # noqa: E731
+        self._check(self._L.lbm_moments_device(self._h, ptr(rho), ptr(ux), ptr(uy)))
+
+    def diagnostics(self):
+        d = C.lbm_diag()
+        self._check(self._L.lbm_diagnostics(self._h, ctypes.byref(d)))
+        return _diag_dict(d)
+
+    @property
+    def step_count(self):
+        return self._L.lbm_step_count(self._h)
+
+    def eval_psi(self, rho):
+        r = np.ascontiguousarray(rho, dtype=np.float64).ravel()
+        out = np.empty_like(r)
+        self._check(self._L.lbm_eval_psi(self._h, _d(r), _d(out), r.size))
+        return out.reshape(np.shape(rho))
+
+    def save(self, path):
+        self._check(self._L.lbm_save(self._h, str(path).encode()))
+
+    def load(self, path):
+        self._check(self._L.lbm_load(self._h, str(path).encode()))
+
+    @property
+    def tiling(self):
+        v, r = ctypes.c_int(), ctypes.c_int()
+        self._check(self._L.lbm_get_tiling(self._h, ctypes.byref(v), ctypes.byref(r)))
+        return v.value, r.value
+
+    def set_tiling(self, vec=0, rows=0):
+        self._check(self._L.lbm_set_tiling(self._h, int(vec), int(rows)))
+
+    @property
+    def stream(self):
+        return self._L.lbm_stream(self._h)
+
+
+@dataclasses.dataclass
+class Instance:
+    """One member of a Batch (fields as lbm_instance)."""
+    nx: int
+    ny: int
+    eos: Eos
+    G: float = -1.0
+    sigma: float = 0.0
+    s: tuple = (1.0, 1.1, 1.1, 1.0, 1.1, 1.0, 1.1, 1.0, 1.0)
+    nu_l: float = 0.0
+    nu_v: float = 0.0
+    visc_mode: str = "const"
+    bc: str = "periodic"
+    rho_c: float = 0.0
+    rho_l: float = 0.0
+    rho_v: float = 0.0
+    rho_ref: float = -1.0
+
+    def c(self):
+        ci = C.lbm_instance()
+        ci.nx, ci.ny = int(self.nx), int(self.ny)
+        ci.eos = self.eos.c()
+        ci.G, ci.sigma = float(self.G), float(self.sigma)
+        for i in range(9):
+            ci.s[i] = float(self.s[i])
+        ci.nu_l, ci.nu_v = float(self.nu_l), float(self.nu_v)
+        ci.visc_mode = _VISC[self.visc_mode]
+        ci.bc = _BC[self.bc]
+        ci.rho_c, ci.rho_l, ci.rho_v = float(self.rho_c), float(self.rho_l), float(self.rho_v)
+        ci.rho_ref = float(self.rho_ref)
+        return ci
+
+
+class Batch:
+    """Many independent lattices advanced by one launch per step (lbm_batch_*)."""
+
+    def __init__(self, instances, precision="fp32", stream=None, tile_vec=0, tile_rows=0,
+                 device=None):
+        self._L = C.lib()
+        self.instances = list(instances)
+        arr = (C.lbm_instance * len(self.instances))(*[i.c() for i in self.instances])
+        h = ctypes.c_void_p()
+        sp = _stream_ptr(stream)
+        rc = self._L.lbm_batch_create(ctypes.byref(h), len(self.instances), arr,
+                                      _PREC[precision], sp, _device_of(stream, device),
+                                      int(tile_vec), int(tile_rows))
+        if rc != 0:
+            raise LbmError(rc, self._L.lbm_batch_last_error(None).decode())
+        self._h = h
+        self.stream_keepalive = stream
+
+    def _check(self, rc):
+        if rc < 0:
+            raise LbmError(rc, self._L.lbm_batch_last_error(self._h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return len(self.instances)
+
+    def init_fields(self, i, rho, ux=None, uy=None):
+        inst = self.instances[i]
+        shp = (inst.ny, inst.nx)
+        r, u, v = _f64(rho, shp), _f64(ux, shp), _f64(uy, shp)
+        self._check(self._L.lbm_batch_init_fields(self._h, int(i), _d(r), _d(u), _d(v)))
+
+    def step(self, n=1):
+        self._check(self._L.lbm_batch_step(self._h, int(n)))
+
+    def moments(self, i):
+        inst = self.instances[i]
+        out = {k: np.empty((inst.ny, inst.nx)) for k in ("rho", "ux", "uy")}
+        self._check(self._L.lbm_batch_moments(self._h, int(i), _d(out["rho"]), _d(out["ux"]),
+                                              _d(out["uy"])))
+        return out
+
+    def get_populations(self, i):
+        inst = self.instances[i]
+        f = np.empty((9, inst.ny, inst.nx))
+        self._check(self._L.lbm_batch_get_populations(self._h, int(i), _d(f)))
+        return f
+
+    def diagnostics(self):
+        arr = (C.lbm_diag * len(self.instances))()
+        self._check(self._L.lbm_batch_diagnostics(self._h, arr))
+        return [_diag_dict(d) for d in arr]
+
+    def run_to_equilibrium(self, tol, check_every=100, max_steps=100000):
+        steps = (ctypes.c_longlong * len(self.instances))()
+        left = self._check(self._L.lbm_batch_run_to_equilibrium(
+            self._h, float(tol), int(check_every), int(max_steps), steps))
+        return left, np.array(steps[:], dtype=np.int64)
+
+    @property
+    def active(self):
+        return self._check(self._L.lbm_batch_active(self._h))

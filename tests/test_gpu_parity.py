@@ -1,0 +1,263 @@
+"""CUDA step vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (written here, derived in the design notes):
+  FP64 mode   per step max|df| / max|f| <= 1e-12 (spec bound); in practice ~1e-16.
+  FP32 mode   per step, from the same state: |df_q| <= 2e-6 * (t_q rho + |f_q|) -- a few
+              hundred ulps of float for ~150 operations per node on O(rho) quantities;
+              over runs: max relative density error <= 1e-4 and coexistence densities
+              within 1e-3 (spec bounds).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from tests import pairs
+from tests.textbook import T_W
+
+pytestmark = pytest.mark.gpu
+
+GRIDS = [(128, 128), (130, 67), (5, 3), (3, 40), (257, 129), (1, 7)]
+
+
+def fp32_close(got, ref, rho, tol=2e-6):
+    scale = T_W[:, None, None] * rho[None] + np.abs(ref)
+    return float(np.max(np.abs(got - ref) / scale)) <= tol, float(np.max(np.abs(got - ref) / scale))
+
+
+@pytest.mark.parametrize("nx,ny", GRIDS)
+@pytest.mark.parametrize("walls", [False, True])
+@pytest.mark.parametrize("vec", [1, 2])
+def test_fp64_per_step_parity(nx, ny, walls, vec):
+    c = pairs.case(nx, ny, tr=0.7, sigma=0.114, walls=walls,
+                   s=(1.0, 1.1, 1.1, 1.0, 1.1, 1.0, 1.1, 1.25, 1.25))
+    p = pairs.oracle_params(c)
+    f = pairs.droplet_state(c, vel=0.01)
+    with pairs.gpu_lattice(c, "fp64", tile_vec=vec, tile_rows=16) as L:
+        for k in range(4):
+            L.set_populations(f)
+            L.step(1)
+            got = L.get_populations()
+            ref = oracle.run(p, f, 1)
+            assert pairs.rel_err(got, ref) <= 1e-12, (k, pairs.rel_err(got, ref))
+            f = ref
+
+
+@pytest.mark.parametrize("visc", ["const", "step", "linear"])
+@pytest.mark.parametrize("sigma", [0.0, 0.11])
+def test_fp64_viscosity_modes_and_sigma(visc, sigma):
+    c = pairs.case(96, 80, a=0.5, tr=0.65, sigma=sigma, visc=visc, nu_l=0.05, nu_v=0.2)
+    p = pairs.oracle_params(c)
+    f = pairs.droplet_state(c, vel=0.02, seed=3)
+    with pairs.gpu_lattice(c, "fp64") as L:
+        L.set_populations(f)
+        L.step(1)
+        assert pairs.rel_err(L.get_populations(), oracle.run(p, f, 1)) <= 1e-12
+        # and a 60-step trajectory, graph replay included, stays within 60 x the bound
+        L.set_populations(f)
+        L.step(60)
+        assert pairs.rel_err(L.get_populations(), oracle.run(p, f, 60)) <= 60e-12
+
+
+@pytest.mark.parametrize("vec", [1, 2, 4])
+@pytest.mark.parametrize("walls", [False, True])
+def test_fp32_per_step_parity(vec, walls):
+    c = pairs.case(131, 70, tr=0.6, sigma=0.114, walls=walls, visc="linear", nu_l=0.05,
+                   nu_v=0.5)
+    p = pairs.oracle_params(c)
+    f = pairs.droplet_state(c, vel=0.01, seed=1)
+    with pairs.gpu_lattice(c, "fp32", tile_vec=vec, tile_rows=24) as L:
+        for k in range(3):
+            L.set_populations(f)
+            f_in = L.get_populations()  # the float-rounded state the GPU starts from
+            L.step(1)
+            got = L.get_populations()
+            ref = oracle.run(p, f_in, 1)
+            ok, err = fp32_close(got, ref, oracle.fields(p, f_in)["rho"])
+            assert ok, (k, err)
+            f = ref
+
+
+def test_fp32_psi_fp64_option_matches():
+    c = pairs.case(64, 64, tr=0.6, sigma=0.114)
+    p = pairs.oracle_params(c)
+    f = pairs.droplet_state(c, vel=0.01)
+    with pairs.gpu_lattice(c, "fp32", psi_fp64=True) as L:
+        L.set_populations(f)
+        f_in = L.get_populations()
+        L.step(1)
+        ok, err = fp32_close(L.get_populations(), oracle.run(p, f_in, 1),
+                             oracle.fields(p, f_in)["rho"])
+        assert ok, err
+
+
+def test_fp32_droplet_run_density_and_coexistence():
+    """128^2 stationary droplet (a = 0.25, T = 0.7 T_c, sigma = 0.114, tau = 1): after
+    3000 steps the FP32 density is within 1e-4 (max relative) of the FP64 oracle and the
+    liquid/vapour densities within 1e-3."""
+    c = pairs.case(128, 128, a=0.25, tr=0.7, sigma=0.114, s=pairs.RATES_C1)
+    p = pairs.oracle_params(c)
+    f = pairs.droplet_state(c, r0=30, W=4.0)
+    steps = 3000
+    ref = oracle.fields(p, oracle.run(p, f, steps))["rho"]
+    with pairs.gpu_lattice(c, "fp32") as L:
+        L.set_populations(f)
+        L.step(steps)
+        rho = L.moments()["rho"]
+    assert float(np.max(np.abs(rho - ref) / ref)) <= 1e-4
+    for (y, x) in ((64, 64), (0, 0)):
+        assert abs(rho[y, x] - ref[y, x]) / ref[y, x] <= 1e-3
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
+def test_moments_match_oracle_fields(prec, tol):
+    c = pairs.case(70, 45, tr=0.6, sigma=0.114, walls=True)
+    p = pairs.oracle_params(c)
+    f = pairs.droplet_state(c, vel=0.02)
+    with pairs.gpu_lattice(c, prec) as L:
+        L.set_populations(f)
+        f_in = L.get_populations()
+        m = L.moments()
+    o = oracle.fields(p, f_in)
+    assert np.max(np.abs(m["rho"] - o["rho"]) / o["rho"]) <= tol
+    umax = max(np.max(np.abs(o["ux"])), np.max(np.abs(o["uy"])))
+    assert np.max(np.abs(m["ux"] - o["ux"])) <= 50 * tol * umax + tol * 1e-3
+    assert np.max(np.abs(m["uy"] - o["uy"])) <= 50 * tol * umax + tol * 1e-3
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_diagnostics_match_oracle(prec):
+    c = pairs.case(100, 60, tr=0.7, sigma=0.114)
+    p = pairs.oracle_params(c)
+    f = pairs.droplet_state(c, vel=0.02)
+    with pairs.gpu_lattice(c, prec) as L:
+        L.set_populations(f)
+        d0 = L.diagnostics()
+        assert d0["dinf"] == -1.0 and d0["step"] == 0 and d0["nonfinite"] == 0
+        L.step(10)
+        f_in = L.get_populations()
+        d1 = L.diagnostics()
+    o = oracle.fields(p, f_in)
+    o0 = oracle.fields(p, f)
+    rtol = 1e-12 if prec == "fp64" else 1e-6
+    assert abs(d1["mass"] - o["rho"].sum()) <= rtol * o["rho"].sum()
+    mx = (o["rho"] * o["ux"]).sum()
+    my = (o["rho"] * o["uy"]).sum()
+    scale = o["rho"].sum() * 1e-2
+    assert abs(d1["mom_x"] - mx) <= rtol * 10 * scale and abs(d1["mom_y"] - my) <= rtol * 10 * scale
+    umax = np.sqrt(o["ux"] ** 2 + o["uy"] ** 2).max()
+    assert abs(d1["max_u"] - umax) <= (1e-6 if prec == "fp32" else 1e-7) * max(umax, 1e-3)
+    assert abs(d1["dinf"] - np.max(np.abs(o["rho"] - o0["rho"]))) <= 1e-6 * o["rho"].max()
+    assert d1["step"] == 10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_psi_evaluation_accuracy(prec):
+    """psi as the kernel computes it vs the oracle's FP64 psi at the same densities
+    (the densities are float-representable, so only the evaluation differs)."""
+    c = pairs.case(8, 8, a=0.25, tr=0.5)
+    rho = np.concatenate([np.geomspace(1e-5, 0.05, 300), np.linspace(0.05, 0.6, 300)])
+    rho = rho.astype(np.float32).astype(np.float64)
+    ref = np.array([oracle.psi(r, c["a"], 4.0, 1.0, c["T"], -1.0) for r in rho])
+    with pairs.gpu_lattice(c, prec) as L:
+        got = L.eval_psi(rho)
+    rel = np.abs(got - ref) / ref
+    assert rel.max() <= (1e-15 if prec == "fp64" else 4e-7), rel.max()
+
+
+def test_tiling_and_graph_do_not_change_results():
+    """Columns per thread, rows per CTA and graph replay only move data: the per-node
+    arithmetic is identical, so FP32 results are bitwise equal."""
+    c = pairs.case(203, 77, tr=0.65, sigma=0.114, visc="step", nu_l=0.04, nu_v=0.3)
+    f = pairs.droplet_state(c, vel=0.01)
+    outs = []
+    for vec, rows in ((4, 0), (1, 5), (2, 33), (4, 77)):
+        with pairs.gpu_lattice(c, "fp32", tile_vec=vec, tile_rows=rows) as L:
+            L.set_populations(f)
+            L.step(70)  # one 64-step graph replay + 6 single launches
+            outs.append(L.get_populations())
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    with pairs.gpu_lattice(c, "fp32") as L:
+        L.set_populations(f)
+        for _ in range(70):
+            L.step(1)
+        assert np.array_equal(L.get_populations(), outs[0])
+
+
+def test_save_load_resume_is_bitwise(tmp_path):
+    c = pairs.case(64, 48, tr=0.7, sigma=0.114)
+    f = pairs.droplet_state(c, vel=0.01)
+    path = os.path.join(tmp_path, "state.lbm")
+    with pairs.gpu_lattice(c, "fp32") as L:
+        L.set_populations(f)
+        L.step(30)
+        L.save(path)
+        L.step(40)
+        straight = L.get_populations()
+    with pairs.gpu_lattice(c, "fp32") as L2:
+        L2.load(path)
+        assert L2.step_count == 30
+        L2.step(40)
+        assert np.array_equal(L2.get_populations(), straight)
+    with open(path, "r+b") as fh:  # a flipped byte is caught by the checksum
+        fh.seek(200)
+        b = fh.read(1)
+        fh.seek(200)
+        fh.write(bytes([b[0] ^ 0xFF]))
+    from paper_1211_6932_gb300 import LbmError
+    with pairs.gpu_lattice(c, "fp32") as L3:
+        with pytest.raises(LbmError) as ei:
+            L3.load(path)
+        assert ei.value.code == -7
+
+
+def test_nonfinite_state_is_reported():
+    """A NaN placed in the input populations (on the host) is reported by lbm_sync."""
+    from paper_1211_6932_gb300 import LbmError
+    c = pairs.case(32, 32, tr=0.7, sigma=0.114)
+    f = pairs.droplet_state(c)
+    f[:, 5, 7] = np.nan
+    with pairs.gpu_lattice(c, "fp32") as L:
+        L.set_populations(f)
+        L.step(2)
+        with pytest.raises(LbmError) as ei:
+            L.sync()
+        assert ei.value.code == -4
+        assert L.diagnostics()["nonfinite"] > 0
+
+
+def test_init_fields_validates_and_matches_equilibrium():
+    from paper_1211_6932_gb300 import LbmError
+    c = pairs.case(40, 30, tr=0.7, sigma=0.114)
+    rl, rv = pairs.maxwell(c)
+    from paper_1211_6932_gb300 import workloads as wl
+    rho = wl.droplet(40, 30, rl, rv, 9.0, 4.0)
+    ux = np.full_like(rho, 0.01)
+    uy = np.full_like(rho, -0.02)
+    with pairs.gpu_lattice(c, "fp64") as L:
+        L.init_fields(rho, ux, uy)
+        assert np.max(np.abs(L.get_populations() - oracle.equilibrium(rho, ux, uy))) < 1e-15
+        bad = rho.copy()
+        bad[3, 3] = 1.5  # beyond 4/b
+        with pytest.raises(LbmError) as ei:
+            L.init_fields(bad)
+        assert ei.value.code == -1
+
+
+def test_fp32_deviation_reference_choice():
+    """Deviation storage around the vapour density (default) is at least as accurate as
+    plain float storage (rho_ref = 0) against the oracle after 500 steps."""
+    c = pairs.case(96, 96, a=0.25, tr=0.55, sigma=0.114)
+    p = pairs.oracle_params(c)
+    f = pairs.droplet_state(c, r0=25)
+    ref = oracle.fields(p, oracle.run(p, f, 500))
+    errs = []
+    for rr in (None, 0.0):
+        with pairs.gpu_lattice(c, "fp32", rho_ref=rr) as L:
+            L.set_populations(f)
+            L.step(500)
+            m = L.moments()
+        errs.append(float(np.max(np.abs(m["rho"] - ref["rho"]) / ref["rho"])))
+    assert errs[0] <= 1e-4 and errs[0] <= 1.5 * errs[1], errs
