@@ -36,7 +36,8 @@ extern "C" {
 #define LBM_ENOMEM (-2)    /* a device or host allocation failed */
 #define LBM_ECUDA (-3)     /* a CUDA runtime call failed (message names it) */
 #define LBM_EUNSTABLE (-4) /* a density became non-finite or non-positive */
-#define LBM_ETIMEOUT (-5)  /* a bounded device-side wait ran out */
+#define LBM_ETIMEOUT (-5)  /* a bounded device-side wait ran out (the kernel gave up and
+                              returned; the state was not advanced correctly) */
 #define LBM_ESTATE (-6)    /* call not valid in the handle's current state */
 #define LBM_EIO (-7)       /* file could not be read/written, or failed its checksum */
 
@@ -75,8 +76,8 @@ typedef struct {
   void* stream;   /* cudaStream_t to queue work on; NULL: a stream the handle owns */
   int device;     /* CUDA device ordinal; -1 (default): the library's current device.
                      Every call on the handle makes this device current first. */
-  int tile_vec;   /* columns per thread in the step kernel: 1, 2, 4 (4 is FP32 only);
-                     0 (default): 4 for FP32_DEV, 1 for FP64 */
+  int tile_threads; /* threads (one column each) per CTA of the step kernel: 64, 128 or
+                       256 (256 is FP32 only); 0 (default): 256 for FP32_DEV, 128 for FP64 */
   int tile_rows;  /* rows per CTA sweep; 0 (default): sized to fill the GPU */
 } lbm_options;
 
@@ -181,10 +182,10 @@ int lbm_eval_psi(lbm_handle* h, const double* rho, double* psi, size_t n);
 int lbm_save(lbm_handle* h, const char* path);
 int lbm_load(lbm_handle* h, const char* path);
 
-/* Kernel configuration in use: columns per thread and rows per CTA sweep. */
-int lbm_get_tiling(const lbm_handle* h, int* vec, int* rows);
+/* Kernel configuration in use: threads (columns) per CTA and rows per CTA sweep. */
+int lbm_get_tiling(const lbm_handle* h, int* threads, int* rows);
 /* Change it (same meaning as the lbm_options fields; 0 picks the default). */
-int lbm_set_tiling(lbm_handle* h, int vec, int rows);
+int lbm_set_tiling(lbm_handle* h, int threads, int rows);
 
 /* The CUDA stream the handle queues work on (a cudaStream_t). */
 void* lbm_stream(const lbm_handle* h);
@@ -219,9 +220,9 @@ typedef struct {
 } lbm_instance;
 
 /* Create a batch of n >= 1 instances in one precision; stream may be NULL; device,
- * tile_vec and tile_rows as in lbm_options (-1, 0, 0 = defaults). */
+ * tile_threads and tile_rows as in lbm_options (-1, 0, 0 = defaults). */
 int lbm_batch_create(lbm_batch** out, int n, const lbm_instance* inst, int precision,
-                     void* stream, int device, int tile_vec, int tile_rows);
+                     void* stream, int device, int tile_threads, int tile_rows);
 void lbm_batch_destroy(lbm_batch* b);
 const char* lbm_batch_last_error(const lbm_batch* b);
 

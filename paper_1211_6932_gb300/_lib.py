@@ -26,7 +26,7 @@ class lbm_options(ctypes.Structure):
     _fields_ = [("precision", c_int), ("visc_mode", c_int), ("bc", c_int), ("psi_fp64", c_int),
                 ("rho_ref", c_double), ("rho_c", c_double), ("rho_l", c_double),
                 ("rho_v", c_double), ("stream", c_void_p), ("device", c_int),
-                ("tile_vec", c_int), ("tile_rows", c_int)]
+                ("tile_threads", c_int), ("tile_rows", c_int)]
 
 
 class lbm_diag(ctypes.Structure):

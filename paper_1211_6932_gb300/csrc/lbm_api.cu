@@ -58,7 +58,7 @@ struct Batch {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaStream_t cap_stream = nullptr;
-  int vec = 0, rows_req = 0, rows = 0;
+  int nt = 0, rows_req = 0, rows = 0;  // threads (= columns) per CTA, rows per sweep
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   std::string err;
   int sms = 0;
@@ -130,12 +130,12 @@ void destroy_batch(Batch* b) {
 }
 
 int sweep_occupancy(const Batch* b) {
-  return b->fp64 ? lbm::sweep_occupancy<double>(b->vec) : lbm::sweep_occupancy<float>(b->vec);
+  return b->fp64 ? lbm::sweep_occupancy<double>(b->nt) : lbm::sweep_occupancy<float>(b->nt);
 }
 
 // Rows per CTA sweep: enough work items for one full wave of resident CTAs.
 int default_rows(const Batch* b) {
-  const int W = (lbm::NT - 2) * b->vec;
+  const int W = b->nt;
   long long strip_rows = 0;
   for (int i = 0; i < b->n_inst; ++i)
     if (b->active[i]) strip_rows += (long long)((b->inst[i].nx + W - 1) / W) * b->inst[i].ny;
@@ -146,7 +146,7 @@ int default_rows(const Batch* b) {
 
 void make_items(const Batch* b, bool only_active, int rows, std::vector<WorkItem>& out,
                 std::vector<int>* begin) {
-  const int W = (lbm::NT - 2) * b->vec;
+  const int W = b->nt;
   out.clear();
   if (begin) begin->assign(1, 0);
   for (int i = 0; i < b->n_inst; ++i) {
@@ -222,7 +222,7 @@ int fill_params(std::string& err, InstParams& P, const lbm_instance& in, bool fp
   std::memset(&P, 0, sizeof P);
   P.nx = in.nx;
   P.ny = in.ny;
-  P.pitch = (int)round_up((size_t)in.nx, 4);
+  P.pitch = (int)round_up((size_t)in.nx + 2 * lbm::GHOST, 8);
   P.plane = (long long)in.ny * P.pitch;
   P.walls = in.bc == LBM_BC_WALLS_Y;
   P.visc_mode = in.visc_mode;
@@ -261,10 +261,10 @@ int fill_params(std::string& err, InstParams& P, const lbm_instance& in, bool fp
 
 
 int create_batch(Batch* b, int n, const lbm_instance* in, bool fp64, int psi_fp64,
-                 void* stream, int device, int vec, int rows) {
+                 void* stream, int device, int nt, int rows) {
   if (n < 1 || !in) return set_err(b->err, LBM_EINVAL, "need at least one instance");
-  if (vec != 0 && !lbm::vec_supported(fp64, vec))
-    return set_err(b->err, LBM_EINVAL, "tile_vec %d not available for this precision", vec);
+  if (nt != 0 && !lbm::nt_supported(fp64, nt))
+    return set_err(b->err, LBM_EINVAL, "tile_threads %d not available for this precision", nt);
   if (rows < 0) return set_err(b->err, LBM_EINVAL, "tile_rows must be >= 0");
   b->fp64 = fp64;
   b->esz = fp64 ? sizeof(double) : sizeof(float);
@@ -285,7 +285,7 @@ int create_batch(Batch* b, int n, const lbm_instance* in, bool fp64, int psi_fp6
   }
   b->slab_elems = off;
   b->dense_elems = dense;
-  b->vec = vec ? vec : (fp64 ? 1 : 4);
+  b->nt = nt ? nt : (fp64 ? 128 : 256);
   b->rows_req = rows;
   int dev_count = 0;
   if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1)
@@ -324,12 +324,12 @@ int launch_step(Batch* b, cudaStream_t st) {
   cudaError_t e;
   if (b->fp64) {
     MomArgs<double> mo{};
-    e = lbm::launch_sweep<double>(b->vec, lbm::MODE_STEP, (const double*)b->slab[c],
+    e = lbm::launch_sweep<double>(b->nt, lbm::MODE_STEP, (const double*)b->slab[c],
                                   (double*)b->slab[c ^ 1], b->d_inst, b->d_items, b->n_items,
                                   mo, b->d_status, st);
   } else {
     MomArgs<float> mo{};
-    e = lbm::launch_sweep<float>(b->vec, lbm::MODE_STEP, (const float*)b->slab[c],
+    e = lbm::launch_sweep<float>(b->nt, lbm::MODE_STEP, (const float*)b->slab[c],
                                  (float*)b->slab[c ^ 1], b->d_inst, b->d_items, b->n_items,
                                  mo, b->d_status, st);
   }
@@ -391,6 +391,9 @@ int sync_status(Batch* b) {
   CK(b, cudaStreamSynchronize(b->stream));
   int st = 0;
   CK(b, cudaMemcpy(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st & lbm::STATUS_TIMEOUT)
+    return set_err(b->err, LBM_ETIMEOUT,
+                   "a bounded wait for a shared-memory copy ran out in the step kernel");
   if (st & lbm::STATUS_NONFINITE)
     return set_err(b->err, LBM_EUNSTABLE,
                    "a density became non-finite or non-positive during stepping");
@@ -442,6 +445,9 @@ int init_instance(Batch* b, int i, const double* rho, const double* ux, const do
     e = lbm::launch_init_eq<double>(dr, du, dv, (double*)b->slab[b->cur], P, dbad, b->stream);
   else
     e = lbm::launch_init_eq<float>(dr, du, dv, (float*)b->slab[b->cur], P, dbad, b->stream);
+  if (e == cudaSuccess)
+    e = b->fp64 ? lbm::launch_fill_ghosts<double>((double*)b->slab[b->cur], P, b->stream)
+                : lbm::launch_fill_ghosts<float>((float*)b->slab[b->cur], P, b->stream);
   int bad = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -482,6 +488,9 @@ int set_pops(Batch* b, int i, const double* f) {
     e = b->fp64 ? lbm::launch_set_pops<double>((double*)tmp, (double*)b->slab[b->cur], P, b->stream)
                 : lbm::launch_set_pops<float>((double*)tmp, (float*)b->slab[b->cur], P, b->stream);
   if (e == cudaSuccess)
+    e = b->fp64 ? lbm::launch_fill_ghosts<double>((double*)b->slab[b->cur], P, b->stream)
+                : lbm::launch_fill_ghosts<float>((float*)b->slab[b->cur], P, b->stream);
+  if (e == cudaSuccess)
     e = cudaMemcpyAsync((char*)b->slab[b->cur ^ 1] + P.off * b->esz,
                         (char*)b->slab[b->cur] + P.off * b->esz, 9 * P.plane * b->esz,
                         cudaMemcpyDeviceToDevice, b->stream);
@@ -520,7 +529,7 @@ int moments_pass(Batch* b, const WorkItem* d_items, int n, MomArgs<S> mo) {
   mo.part_sum = b->d_part_sum;
   mo.part_max = b->d_part_max;
   mo.part_bad = b->d_part_bad;
-  cudaError_t e = lbm::launch_sweep<S>(b->vec, lbm::MODE_MOMENTS, (const S*)b->slab[b->cur],
+  cudaError_t e = lbm::launch_sweep<S>(b->nt, lbm::MODE_MOMENTS, (const S*)b->slab[b->cur],
                                        nullptr, b->d_inst, d_items, n, mo, b->d_status,
                                        b->stream);
   if (e != cudaSuccess)
@@ -694,7 +703,7 @@ void lbm_options_default(lbm_options* o) {
   o->rho_v = 0.0;
   o->stream = nullptr;
   o->device = -1;
-  o->tile_vec = 0;
+  o->tile_threads = 0;
   o->tile_rows = 0;
 }
 
@@ -726,7 +735,7 @@ int lbm_create(lbm_handle** out, int nx, int ny, lbm_eos eos, double G, double s
   lbm_handle* h = new (std::nothrow) lbm_handle();
   if (!h) return set_err(g_thread_err, LBM_ENOMEM, "out of host memory");
   int rc = create_batch(&h->b, 1, &in, o.precision == LBM_FP64, o.psi_fp64, o.stream,
-                        o.device, o.tile_vec, o.tile_rows);
+                        o.device, o.tile_threads, o.tile_rows);
   if (rc) {
     g_thread_err = h->b.err;
     destroy_batch(&h->b);
@@ -816,22 +825,23 @@ int lbm_eval_psi(lbm_handle* h, const double* rho, double* psi, size_t n) {
   return eval_psi(&h->b, rho, psi, n);
 }
 
-int lbm_get_tiling(const lbm_handle* h, int* vec, int* rows) {
+int lbm_get_tiling(const lbm_handle* h, int* threads, int* rows) {
   DeviceGuard g_(h ? &h->b : nullptr);
   if (!h) return LBM_EINVAL;
-  if (vec) *vec = h->b.vec;
+  if (threads) *threads = h->b.nt;
   if (rows) *rows = h->b.rows;
   return LBM_OK;
 }
 
-int lbm_set_tiling(lbm_handle* h, int vec, int rows) {
+int lbm_set_tiling(lbm_handle* h, int threads, int rows) {
   DeviceGuard g_(h ? &h->b : nullptr);
   if (!h) return LBM_EINVAL;
   Batch* b = &h->b;
-  if (vec != 0 && !lbm::vec_supported(b->fp64, vec))
-    return set_err(b->err, LBM_EINVAL, "tile_vec %d not available for this precision", vec);
+  if (threads != 0 && !lbm::nt_supported(b->fp64, threads))
+    return set_err(b->err, LBM_EINVAL, "tile_threads %d not available for this precision",
+                   threads);
   if (rows < 0) return set_err(b->err, LBM_EINVAL, "tile_rows must be >= 0");
-  b->vec = vec ? vec : (b->fp64 ? 1 : 4);
+  b->nt = threads ? threads : (b->fp64 ? 128 : 256);
   b->rows_req = rows;
   return rebuild_items(b);
 }
@@ -912,15 +922,15 @@ int lbm_load(lbm_handle* h, const char* path) {
 // Batches
 
 int lbm_batch_create(lbm_batch** out, int n, const lbm_instance* inst, int precision,
-                     void* stream, int device, int tile_vec, int tile_rows) {
+                     void* stream, int device, int tile_threads, int tile_rows) {
   if (!out) return set_err(g_thread_err, LBM_EINVAL, "out must not be NULL");
   *out = nullptr;
   if (precision != LBM_FP64 && precision != LBM_FP32_DEV)
     return set_err(g_thread_err, LBM_EINVAL, "unknown precision %d", precision);
   lbm_batch* b = new (std::nothrow) lbm_batch();
   if (!b) return set_err(g_thread_err, LBM_ENOMEM, "out of host memory");
-  int rc = create_batch(&b->b, n, inst, precision == LBM_FP64, 0, stream, device, tile_vec,
-                        tile_rows);
+  int rc = create_batch(&b->b, n, inst, precision == LBM_FP64, 0, stream, device,
+                        tile_threads, tile_rows);
   if (rc) {
     g_thread_err = b->b.err;
     destroy_batch(&b->b);

@@ -23,7 +23,23 @@ __device__ __forceinline__ long long slot_of(const InstParams& P, int q, int x, 
     }
   }
   xs = xs < 0 ? xs + P.nx : (xs >= P.nx ? xs - P.nx : xs);
-  return P.off + (long long)qs * P.plane + (long long)ys * P.pitch + xs;
+  return P.off + (long long)qs * P.plane + (long long)ys * P.pitch + GHOST + xs;
+}
+
+// Refresh the ghost columns -2, -1, nx, nx+1 of every row from the columns they mirror
+// (periodic x); the step kernel keeps them current afterwards.
+template <typename S>
+__global__ void fill_ghosts_kernel(S* __restrict__ buf, InstParams P) {
+  const long long total = (long long)Q * P.ny * 4;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(i & 3);
+    const long long qy = i >> 2;
+    const int y = (int)(qy % P.ny), q = (int)(qy / P.ny);
+    const int g = k == 0 ? -2 : (k == 1 ? -1 : (k == 2 ? P.nx : P.nx + 1));
+    S* row = buf + P.off + (long long)q * P.plane + (long long)y * P.pitch + GHOST;
+    row[g] = row[wrapi(g, P.nx)];
+  }
 }
 
 // Canonical host-order populations (Q, ny, nx) -> storage.

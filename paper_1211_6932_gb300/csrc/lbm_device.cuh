@@ -1,20 +1,27 @@
 // Device side of the D2Q9 MRT pseudopotential step (Li, Luo & Li, arXiv:1211.6932).
 //
-// One fused kernel per time step.  A CTA owns a strip of W columns and a chunk of rows of
-// one lattice instance and sweeps the chunk row by row:
-//   pull the nine populations of the next row (Eq. 5, pull form), sum them to rho (Eq. 6),
-//   evaluate psi (Eqs. 24 and 30) into a four-row ring in shared memory, and, one row
-//   behind, form F from the 3x3 psi stencil (Eq. 7), v (Eq. 6), the MRT collision with the
-//   improved forcing term (Eqs. 3, 4, 25) and store the post-collision populations at the
-//   node itself (aligned, vectorised stores).
-// psi of the two halo columns and halo rows is recomputed from the populations, so every
-// population value is read from DRAM once per step and written once: 72 B per lattice
-// update in FP32.
+// One fused kernel per time step.  A CTA owns a strip of NT columns (one column per
+// thread) and a chunk of rows of one lattice instance, and sweeps the chunk row by row:
+//   - one elected thread streams the population rows of the strip (plus a 4-column halo
+//     on each side) into an 8-row ring in shared memory with bulk asynchronous copies
+//     (cp.async.bulk, completion on an mbarrier per slot), up to six rows ahead;
+//   - every thread pulls the nine populations of its node from the ring (Eq. 5, pull
+//     form), sums them to rho (Eq. 6) and evaluates psi (Eqs. 24, 30) into a four-row
+//     psi ring, keeping the pulled values in registers;
+//   - one row behind, it forms F from the 3x3 psi stencil (Eq. 7), v (Eq. 6) and the MRT
+//     collision with the improved forcing (Eqs. 3, 4, 25), and stores the post-collision
+//     populations at the node itself.
+// psi of halo rows and columns is recomputed from the populations, so every population
+// value is read from DRAM once per step and written once: 72 B per lattice update (FP32).
 //
-// Storage: structure of arrays, plane q at fin[off + q*plane + y*pitch + x].  The stored
-// value is the post-collision population of the previous step minus t_q * rho_ref
-// (deviation storage; rho_ref = 0 gives plain storage).  The population at node x and the
-// current time is the pulled value f_q(x) = buf_q(x - e_q) + t_q rho_ref.
+// Storage: structure of arrays.  Plane q of instance P holds row y at
+//   base + P.off + q*P.plane + y*P.pitch + GHOST + x,    x in [-GHOST, pitch - GHOST),
+// i.e. every row carries GHOST columns on each side.  Columns -2, -1, nx, nx+1 are kept
+// equal to columns nx-2, nx-1, 0, 1 (periodic x), so the halo of any strip is one
+// contiguous, 16-byte aligned copy whatever nx is.  The stored value is the
+// post-collision population of the previous step minus t_q rho_ref (deviation storage;
+// rho_ref = 0 gives plain storage): the population at node x and the current time is
+// buf_q(x - e_q) + t_q rho_ref.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -22,7 +29,11 @@
 namespace lbm {
 
 constexpr int Q = 9;
-constexpr int NT = 128;  // threads per CTA in the sweep kernel
+constexpr int GHOST = 8;     // storage columns kept on each side of a row (32 B in FP32)
+constexpr int SEG_HALO = 4;  // shared-memory row segment starts 4 columns left of a strip
+constexpr int NSLOT = 8;     // population rows in the shared-memory ring (power of 2)
+constexpr int PSI_ROWS = 4;  // psi rows in the psi ring (power of 2)
+constexpr long long WAIT_LIMIT = 1LL << 26;  // bounded mbarrier polls before giving up
 
 // D2Q9 velocities: rest, E, N, W, S, NE, NW, SW, SE.
 __host__ __device__ constexpr int ex_of(int q) {
@@ -42,12 +53,12 @@ __host__ __device__ constexpr double tw_of(int q) {
 enum { VISC_CONST = 0, VISC_STEP = 1, VISC_LINEAR = 2 };
 enum { MODE_STEP = 0, MODE_MOMENTS = 1 };
 enum { MOM_FIELDS = 1, MOM_DIAG = 2, MOM_UPDATE_PREV = 4 };
-enum { STATUS_NONFINITE = 1 };
+enum { STATUS_NONFINITE = 1, STATUS_TIMEOUT = 2 };
 
 // Parameters of one lattice instance (host fills, kernels read).
 struct InstParams {
   int nx, ny;
-  int pitch;           // row stride in elements, a multiple of 4
+  int pitch;           // row stride in elements: a multiple of 8, >= nx + 2 GHOST
   int walls;           // 0: periodic in y; 1: halfway bounce-back walls at y=-1/2, ny-1/2
   long long off;       // element offset of plane 0 inside the population slab
   long long plane;     // elements per population plane (ny * pitch)
@@ -67,10 +78,10 @@ struct InstParams {
   double rho_ref;      // deviation reference density
 };
 
-// One CTA's share of the work: columns [x0, x0 + W) and rows [y0, y1) of instance inst.
+// One CTA's share of the work: columns [x0, x0 + NT) and rows [y0, y1) of instance inst.
 // dir = +1 sweeps upwards, -1 downwards.  Alternating the direction between neighbouring
-// chunks makes the two CTAs that share a halo row reach it at about the same time, so the
-// second read of that row hits L2.
+// chunks makes the two CTAs that share halo rows read them at about the same time, so
+// the second read hits L2.
 struct WorkItem {
   int inst, x0, y0, y1;
   int dir, pad0, pad1, pad2;
@@ -115,12 +126,14 @@ __device__ __forceinline__ Phys<R> load_phys(const InstParams& P) {
   return p;
 }
 
+// Reciprocal and square root.  FP32 uses the hardware approximations (a couple of ulps);
+// FP64 keeps IEEE division and sqrt.
 __device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
-__device__ __forceinline__ float recip(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ float recip(float a) { return __fdividef(1.0f, a); }
 __device__ __forceinline__ double recip(double a) { return 1.0 / a; }
-__device__ __forceinline__ float sqrt_(float a) { return __fsqrt_rn(a); }
-__device__ __forceinline__ double sqrt_(double a) { return sqrt(a); }
+__device__ __forceinline__ float sqrt_pos(float a) { return a > 0.f ? a * rsqrtf(a) : 0.f; }
+__device__ __forceinline__ double sqrt_pos(double a) { return a > 0.0 ? sqrt(a) : 0.0; }
 
 // psi of Eq. 24 with the Carnahan-Starling pressure of Eq. 30, written in factored form
 //   psi^2 = (2/G) * rho * (R T Z(x) - a rho - 1/3),  x = b rho / 4,
@@ -134,8 +147,7 @@ __device__ __forceinline__ R psi_eval(R rho, const Phys<R>& p) {
   R omx = (R)1 - x;
   R z = fast_div(num, omx * omx * omx);
   R brk = p.RT * z - p.a * rho - (R)(1.0 / 3.0);
-  R arg = p.two_over_G * rho * brk;
-  return sqrt_(arg > (R)0 ? arg : (R)0);
+  return sqrt_pos(p.two_over_G * rho * brk);
 }
 __device__ __forceinline__ double psi_eval_f64(double rho, double b4, double RT, double a,
                                                double two_over_G) {
@@ -144,7 +156,7 @@ __device__ __forceinline__ double psi_eval_f64(double rho, double b4, double RT,
   double omx = 1.0 - x;
   double z = num / (omx * omx * omx);
   double arg = two_over_G * rho * (RT * z - a * rho - (1.0 / 3.0));
-  return sqrt(arg > 0.0 ? arg : 0.0);
+  return arg > 0.0 ? sqrt(arg) : 0.0;
 }
 template <typename R>
 __device__ __forceinline__ R psi_of(R rho, const Phys<R>& p) {
@@ -168,33 +180,6 @@ __device__ __forceinline__ R stress_rate(R rho, R s_const, const Phys<R>& p) {
   return recip(tau);
 }
 
-// ---------------------------------------------------------------------------------------
-// Vector memory helpers.  VEC consecutive elements of type S, aligned to VEC*sizeof(S).
-template <typename S, int VEC> struct VecT;
-template <> struct VecT<float, 1> { typedef float T; };
-template <> struct VecT<float, 2> { typedef float2 T; };
-template <> struct VecT<float, 4> { typedef float4 T; };
-template <> struct VecT<double, 1> { typedef double T; };
-template <> struct VecT<double, 2> { typedef double2 T; };
-
-template <typename S, int VEC>
-__device__ __forceinline__ void vload(const S* __restrict__ p, S (&v)[VEC]) {
-  typedef typename VecT<S, VEC>::T V;
-  V t = __ldg(reinterpret_cast<const V*>(p));
-  const S* e = reinterpret_cast<const S*>(&t);
-#pragma unroll
-  for (int k = 0; k < VEC; ++k) v[k] = e[k];
-}
-template <typename S, int VEC>
-__device__ __forceinline__ void vstore(S* p, const S (&v)[VEC]) {
-  typedef typename VecT<S, VEC>::T V;
-  V t;
-  S* e = reinterpret_cast<S*>(&t);
-#pragma unroll
-  for (int k = 0; k < VEC; ++k) e[k] = v[k];
-  *reinterpret_cast<V*>(p) = t;
-}
-
 __device__ __forceinline__ int wrapi(int i, int n) {
   // Any integer to [0, n): cheap for the common one-period offsets.
   if (i >= 0 && i < n) return i;
@@ -204,79 +189,53 @@ __device__ __forceinline__ int wrapi(int i, int n) {
   return r < 0 ? r + n : r;
 }
 
-// Context of one CTA sweeping one work item.
-template <typename S, int VEC>
-struct Sweep {
-  const S* __restrict__ base;  // plane 0 of this instance, input buffer
-  int nx, ny, pitch, walls;
-  long long plane;
-  int c0;       // first logical column of this thread
-  bool fast;    // all VEC logical columns of this thread lie in [0, nx)
-  int lane;
-
-  // Pull the nine populations for the VEC nodes (logical columns c0..c0+VEC-1) of
-  // physical row y (0 <= y < ny).  out[q][k] = buf_q(x - e_q) with periodic x, periodic or
-  // bounce-back y.
-  __device__ __forceinline__ void pull_row(int y, S (&out)[Q][VEC]) const {
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      const int exq = ex_of(q), eyq = ey_of(q);
-      int ys = y - eyq;
-      int qs = q;
-      bool bounce = false;
-      if (eyq != 0) {
-        if (ys < 0 || ys >= ny) {
-          if (walls) {
-            bounce = true;
-            qs = opp_of(q);
-            ys = y;
-          } else {
-            ys = ys < 0 ? ys + ny : ys - ny;
-          }
-        }
-      }
-      const S* row = base + (long long)qs * plane + (long long)ys * pitch;
-      S v[VEC];
-      if (fast) {
-        vload<S, VEC>(row + c0, v);
-      } else {
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) v[k] = __ldg(row + wrapi(c0 + k, nx));
-      }
-      if (bounce || exq == 0) {
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) out[q][k] = v[k];
-      } else if (exq == 1) {
-        // node column c needs column c - 1
-        S left = __shfl_up_sync(0xffffffffu, v[VEC - 1], 1);
-        if (lane == 0) left = __ldg(row + wrapi(c0 - 1, nx));
-        out[q][0] = left;
-#pragma unroll
-        for (int k = 1; k < VEC; ++k) out[q][k] = v[k - 1];
-      } else {
-        // node column c needs column c + 1
-        S right = __shfl_down_sync(0xffffffffu, v[0], 1);
-        if (lane == 31) right = __ldg(row + wrapi(c0 + VEC, nx));
-#pragma unroll
-        for (int k = 0; k < VEC - 1; ++k) out[q][k] = v[k + 1];
-        out[q][VEC - 1] = right;
-      }
-    }
-  }
-};
-
-template <typename S, typename R, int VEC>
-__device__ __forceinline__ void density_row(const S (&f)[Q][VEC], R rho_ref, R (&drho)[VEC],
-                                            R (&rho)[VEC]) {
-#pragma unroll
-  for (int k = 0; k < VEC; ++k) {
-    R d = ((R)f[0][k] + ((R)f[1][k] + (R)f[3][k])) + (((R)f[2][k] + (R)f[4][k]) +
-          (((R)f[5][k] + (R)f[7][k]) + ((R)f[6][k] + (R)f[8][k])));
-    drho[k] = d;
-    rho[k] = rho_ref + d;
-  }
+// ---------------------------------------------------------------------------------------
+// Bulk asynchronous copies and mbarriers (inline PTX, sm_90 and later).
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the completion of phase `parity` of bar; false after WAIT_LIMIT polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (long long i = 0; i < WAIT_LIMIT; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
 }
 
+// ---------------------------------------------------------------------------------------
 // Collision of one node in moment space (Eqs. 3, 4, 25), deviation form.
 //   h: pulled deviation populations (in), post-collision deviations (out)
 //   drho = sum h, rho = rho_ref + drho
@@ -289,15 +248,13 @@ __device__ __forceinline__ void density_row(const S (&f)[Q][VEC], R rho_ref, R (
 // 12 sigma s |F/psi|^2 (because tau - 1/2 = (1 - s/2)/s).
 template <typename R>
 __device__ __forceinline__ void collide_node(R (&h)[Q], R drho, R rho, R psi_c, R fpx, R fpy,
-                                             const Phys<R>& p, R& ux_out, R& uy_out) {
+                                             const Phys<R>& p) {
   const R Fx = psi_c * fpx, Fy = psi_c * fpy;
   const R jx = (h[1] - h[3]) + ((h[5] - h[6]) - (h[7] - h[8]));
   const R jy = (h[2] - h[4]) + ((h[5] + h[6]) - (h[7] + h[8]));
   const R ir = recip(rho);
   const R ux = (jx + (R)0.5 * Fx) * ir;
   const R uy = (jy + (R)0.5 * Fy) * ir;
-  ux_out = ux;
-  uy_out = uy;
   const R sa = (h[1] + h[3]) + (h[2] + h[4]);
   const R sd = (h[5] + h[7]) + (h[6] + h[8]);
   const R m1 = (R)2 * sd - sa - (R)4 * h[0];
@@ -342,14 +299,20 @@ __device__ __forceinline__ void collide_node(R (&h)[Q], R drho, R rho, R psi_c, 
   h[8] += B + X - Y - a8;
 }
 
-template <typename R>
-__device__ __forceinline__ bool finite_(R v) { return isfinite(v); }
+// Shared-memory layout of the sweep kernel (dynamic), in bytes.
+template <typename S, int NT>
+struct SweepSmem {
+  static constexpr int SEG = NT + 2 * SEG_HALO;                    // columns per ring row
+  static constexpr size_t BARS = 128;                              // NSLOT mbarriers
+  static constexpr size_t POP = (size_t)NSLOT * Q * SEG * sizeof(S);
+  static constexpr size_t PSI = (size_t)PSI_ROWS * (NT + 2) * sizeof(S);
+  static constexpr size_t BYTES = BARS + POP + PSI;
+};
 
 // ---------------------------------------------------------------------------------------
-// The fused sweep kernel.  One CTA per work item; NT threads, VEC columns per thread.
-// Threads 1..NT-2 own columns [x0, x0 + (NT-2) VEC); threads 0 and NT-1 hold the halo
-// columns x0 - 1 and x0 + W (their psi is needed by the owned edge nodes).
-template <typename S, int VEC, int MODE>
+// The fused sweep kernel.  One CTA per work item, NT threads, thread t owns column x0 + t.
+// Threads 0 and 1 also evaluate psi of the halo columns x0 - 1 and x0 + NT.
+template <typename S, int NT, int MODE>
 __global__ void __launch_bounds__(NT) sweep_kernel(const S* __restrict__ fin,
                                                    S* __restrict__ fout,
                                                    const InstParams* __restrict__ insts,
@@ -357,8 +320,13 @@ __global__ void __launch_bounds__(NT) sweep_kernel(const S* __restrict__ fin,
                                                    int n_items, MomArgs<S> mo,
                                                    int* __restrict__ status) {
   typedef S R;  // arithmetic type follows the storage type
-  constexpr int W = (NT - 2) * VEC;
-  __shared__ R psi_s[4][NT * VEC];
+  typedef SweepSmem<S, NT> L;
+  constexpr int SEG = L::SEG;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+  S* ring = reinterpret_cast<S*>(smem_raw + L::BARS);
+  R* psis = reinterpret_cast<R*>(smem_raw + L::BARS + L::POP);
+  __shared__ int s_abort;
   __shared__ double red_d[NT / 32][3];
   __shared__ float red_f[NT / 32][2];
   __shared__ int red_i[NT / 32];
@@ -369,183 +337,216 @@ __global__ void __launch_bounds__(NT) sweep_kernel(const S* __restrict__ fin,
   const Phys<R> ph = load_phys<R>(P);
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-
-  Sweep<S, VEC> sw;
-  sw.nx = P.nx;
-  sw.ny = P.ny;
-  sw.pitch = P.pitch;
-  sw.walls = P.walls;
-  sw.plane = P.plane;
-  sw.base = fin + P.off;
-  sw.lane = lane;
-  sw.c0 = it.x0 - VEC + tid * VEC;
-  sw.fast = sw.c0 >= 0 && sw.c0 + VEC <= sw.nx;
-  const int nx = sw.nx, ny = sw.ny;
-
-  // Owned columns of this thread: logical columns in [x0, min(x0 + W, nx)).
-  const int xend = min(it.x0 + W, nx);
-  const bool owner = tid >= 1 && tid <= NT - 2 && sw.c0 < xend;
-  const bool full_owner = owner && sw.c0 + VEC <= xend;
-  const int sidx = tid * VEC;  // this thread's first slot in a psi row
-
-  // Rows: psi is needed on rows y0-1 .. y1 (ghost rows mirror the wall row).
-  const int y0 = it.y0, y1 = it.y1;
+  const int nx = P.nx, ny = P.ny, pitch = P.pitch, walls = P.walls;
+  const long long plane = P.plane;
+  const int x0 = it.x0;
+  const int x = x0 + tid;
+  const int xend = min(x0 + NT, nx);
+  const bool owner = x < xend;
   const int dir = it.dir < 0 ? -1 : 1;
-  const int r_first = dir > 0 ? y0 - 1 : y1;      // first psi row
-  const int nrows = y1 - y0 + 2;
+  const int y0 = it.y0, y1 = it.y1;
+  const int nload = y1 - y0 + 4;              // population rows y0-2 .. y1+1
+  const int rstart = dir > 0 ? y0 - 2 : y1 + 1;
+  const int seg0 = GHOST + x0 - SEG_HALO;     // storage column of the ring's column 0
+  const int len = min(SEG, pitch - seg0);     // elements per copied plane-row
+  const uint32_t plane_bytes = (uint32_t)len * (uint32_t)sizeof(S);
+  const S* gsrc = fin + P.off + seg0;
 
-  auto phys_row = [&](int r) -> int {
-    if (sw.walls) return r < 0 ? 0 : (r >= ny ? ny - 1 : r);
-    return r < 0 ? r + ny : (r >= ny ? r - ny : r);
+  // Physical row held by ring row j (walls: clamped, so every slot is filled uniformly;
+  // the clamped copies are never pulled from because bounce-back replaces those reads).
+  auto phys_load_row = [&](int j) -> int {
+    const int r = rstart + j * dir;
+    if (walls) return r < 0 ? 0 : (r >= ny ? ny - 1 : r);
+    return wrapi(r, ny);
+  };
+  auto issue_row = [&](int j) {
+    const int slot = j & (NSLOT - 1);
+    const S* src = gsrc + (long long)phys_load_row(j) * pitch;
+    mbar_arrive_expect_tx(&bars[slot], plane_bytes * Q);
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+      bulk_g2s(ring + ((size_t)slot * Q + q) * SEG, src + (long long)q * plane, plane_bytes,
+               &bars[slot]);
   };
 
-  S cur[Q][VEC], nxt[Q][VEC];
-  R cur_drho[VEC], cur_rho[VEC];
+  if (tid == 0) {
+    s_abort = 0;
+    for (int k = 0; k < NSLOT; ++k) mbar_init(&bars[k], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  int issued = 0;  // meaningful in thread 0 only
+  if (tid == 0) {
+    const int n0 = min(nload, NSLOT);
+    for (int j = 0; j < n0; ++j) issue_row(j);
+    issued = n0;
+  }
+
+  S cur[Q], nxt[Q];
+  R cur_drho = 0, cur_rho = 1;
+  bool flag_bad = false;
   double acc_m = 0.0, acc_x = 0.0, acc_y = 0.0;
   float mx_u = 0.f, mx_d = 0.f;
   int bad = 0;
-  bool flag_bad = false;
+  int waited = 0;  // ring rows waited for so far (all threads)
 
-  // Prologue: row r_first (psi only), then row r_first+dir (psi and kept as centre).
-  sw.pull_row(phys_row(r_first), nxt);
-  {
-    R d[VEC], rr[VEC];
-    density_row<S, R, VEC>(nxt, ph.rho_ref, d, rr);
+  for (int s = 1; s <= nload - 2; ++s) {
+    // Refill the slot freed by row s-2 (all threads left it at the previous barrier).
+    if (tid == 0 && s >= 2 && issued < nload) {
+      fence_proxy_async_smem();
+      issue_row(issued);
+      ++issued;
+    }
+    // Rows s-1, s, s+1 must be resident.
+    while (waited <= s + 1) {
+      if (!mbar_wait_bounded(&bars[waited & (NSLOT - 1)], (uint32_t)((waited / NSLOT) & 1)))
+        s_abort = 1;
+      ++waited;
+    }
+    const int rpsi = rstart + s * dir;  // psi row of this iteration
+    const bool ghost = walls && (rpsi < 0 || rpsi >= ny);
+    R* ps_now = psis + (s & (PSI_ROWS - 1)) * (NT + 2);
+    R nrho = 1, ndrho = 0;
+    if (!ghost) {
+      const int rp = walls ? rpsi : wrapi(rpsi, ny);
+      const bool bb_low = walls && rp == 0;          // e_y = +1 would come from row -1
+      const bool bb_high = walls && rp == ny - 1;    // e_y = -1 would come from row ny
+      // Pull for columns c (CTA-relative): own column, and the halo columns for t < 2.
+      auto pull = [&](int c, S (&v)[Q]) {
 #pragma unroll
-    for (int k = 0; k < VEC; ++k) psi_s[r_first & 3][sidx + k] = psi_of<R>(rr[k], ph);
-  }
-  int r = r_first + dir;
-  sw.pull_row(phys_row(r), cur);
-  density_row<S, R, VEC>(cur, ph.rho_ref, cur_drho, cur_rho);
-#pragma unroll
-  for (int k = 0; k < VEC; ++k) psi_s[r & 3][sidx + k] = psi_of<R>(cur_rho[k], ph);
-  r += dir;
-  sw.pull_row(phys_row(r), nxt);
-
-  for (int i = 2; i < nrows; ++i, r += dir) {
-    // psi of row r from the populations loaded in the previous iteration.
-    R nd[VEC], nr[VEC];
-    density_row<S, R, VEC>(nxt, ph.rho_ref, nd, nr);
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) psi_s[r & 3][sidx + k] = psi_of<R>(nr[k], ph);
-    // Prefetch the populations of the next psi row while this row is collided.
-    S pre[Q][VEC];
-    const bool more = i + 1 < nrows;
-    if (more) sw.pull_row(phys_row(r + dir), pre);
+        for (int q = 0; q < Q; ++q) {
+          const int eyq = ey_of(q), exq = ex_of(q);
+          const bool bb = (eyq > 0 && bb_low) || (eyq < 0 && bb_high);
+          const int j = bb ? s : s - eyq * dir;
+          const int qs = bb ? opp_of(q) : q;
+          const int col = SEG_HALO + c - (bb ? 0 : exq);
+          v[q] = ring[((size_t)(j & (NSLOT - 1)) * Q + qs) * SEG + col];
+        }
+      };
+      auto density = [&](const S (&v)[Q], R& d) {
+        d = ((R)v[0] + ((R)v[1] + (R)v[3])) +
+            (((R)v[2] + (R)v[4]) + (((R)v[5] + (R)v[7]) + ((R)v[6] + (R)v[8])));
+        return ph.rho_ref + d;
+      };
+      pull(tid, nxt);
+      nrho = density(nxt, ndrho);
+      ps_now[1 + tid] = psi_of<R>(nrho, ph);
+      if (tid < 2) {
+        S hv[Q];
+        const int c = tid == 0 ? -1 : NT;
+        pull(c, hv);
+        R hd;
+        ps_now[1 + c] = psi_of<R>(density(hv, hd), ph);
+      }
+      if (walls && s == 2) {
+        // The first psi row of a sweep that starts at a wall is the ghost row: it mirrors
+        // the row just computed.
+        const int rfirst = rstart + dir;
+        if (rfirst < 0 || rfirst >= ny) {
+          R* ps_g = psis + (1 & (PSI_ROWS - 1)) * (NT + 2);
+          ps_g[1 + tid] = ps_now[1 + tid];
+          if (tid < 2) ps_g[tid == 0 ? 0 : NT + 1] = ps_now[tid == 0 ? 0 : NT + 1];
+        }
+      }
+    } else if (s > 1) {
+      // Ghost row at the end of a sweep: mirror the previous (wall) row.
+      const R* ps_prev = psis + ((s - 1) & (PSI_ROWS - 1)) * (NT + 2);
+      ps_now[1 + tid] = ps_prev[1 + tid];
+      if (tid < 2) ps_now[tid == 0 ? 0 : NT + 1] = ps_prev[tid == 0 ? 0 : NT + 1];
+    }
     __syncthreads();
+    if (s_abort) break;
 
-    // Centre row rc = r - dir.
-    const int rc = r - dir;
-    const int yc = rc;  // always inside [0, ny) for centre rows
-    const R* ps_m = psi_s[(rc - 1) & 3];
-    const R* ps_0 = psi_s[rc & 3];
-    const R* ps_p = psi_s[(rc + 1) & 3];
-    if (owner) {
-      R outv[Q][VEC];
-      R uxv[VEC], uyv[VEC];
-#pragma unroll
-      for (int k = 0; k < VEC; ++k) {
-        const int s0 = sidx + k;
-        const R pE = ps_0[s0 + 1], pW = ps_0[s0 - 1];
-        const R pN = ps_p[s0], pS = ps_m[s0];
-        const R pNE = ps_p[s0 + 1], pNW = ps_p[s0 - 1];
-        const R pSW = ps_m[s0 - 1], pSE = ps_m[s0 + 1];
+    if (s >= 3) {
+      // Centre row rc = rstart + (s-1) dir; psi rows rc - dir and rc + dir around it.
+      const int yc = rstart + (s - 1) * dir;
+      const R* ps_c = psis + ((s - 1) & (PSI_ROWS - 1)) * (NT + 2);
+      const R* ps_a = psis + ((s - 2) & (PSI_ROWS - 1)) * (NT + 2);  // row yc - dir
+      const R* ps_b = ps_now;                                         // row yc + dir
+      const R* ps_n = dir > 0 ? ps_b : ps_a;  // north (y + 1)
+      const R* ps_s = dir > 0 ? ps_a : ps_b;  // south (y - 1)
+      if (owner) {
+        const int c = 1 + tid;
+        const R pE = ps_c[c + 1], pW = ps_c[c - 1];
+        const R pN = ps_n[c], pS = ps_s[c];
+        const R pNE = ps_n[c + 1], pNW = ps_n[c - 1];
+        const R pSW = ps_s[c - 1], pSE = ps_s[c + 1];
         const R w1 = (R)(1.0 / 3.0), w2 = (R)(1.0 / 12.0);
         const R fpx = -ph.G * (w1 * (pE - pW) + w2 * ((pNE - pNW) + (pSE - pSW)));
         const R fpy = -ph.G * (w1 * (pN - pS) + w2 * ((pNE + pNW) - (pSE + pSW)));
-        const R pc = ps_0[s0];
+        const R pc = ps_c[c];
         R h[Q];
 #pragma unroll
-        for (int q = 0; q < Q; ++q) h[q] = (R)cur[q][k];
+        for (int q = 0; q < Q; ++q) h[q] = (R)cur[q];
         if (MODE == MODE_STEP) {
-          R ux, uy;
-          collide_node<R>(h, cur_drho[k], cur_rho[k], pc, fpx, fpy, ph, ux, uy);
+          collide_node<R>(h, cur_drho, cur_rho, pc, fpx, fpy, ph);
+          if (!(cur_rho > (R)0) || !isfinite(cur_rho)) flag_bad = true;
+          S* dst = fout + P.off + (long long)yc * pitch + GHOST;
 #pragma unroll
-          for (int q = 0; q < Q; ++q) outv[q][k] = h[q];
-          if (!(cur_rho[k] > (R)0) || !finite_(cur_rho[k])) flag_bad = true;
+          for (int q = 0; q < Q; ++q) dst[(long long)q * plane + x] = (S)h[q];
+          if (x < 2 || x >= nx - 2) {
+            // Keep the ghost columns -2, -1, nx, nx+1 equal to the columns they mirror.
+            auto put = [&](int g) {
+              if (wrapi(g, nx) == x) {
+#pragma unroll
+                for (int q = 0; q < Q; ++q) dst[(long long)q * plane + g] = (S)h[q];
+              }
+            };
+            put(-2);
+            put(-1);
+            put(nx);
+            put(nx + 1);
+          }
         } else {
           const R Fx = pc * fpx, Fy = pc * fpy;
           const R jx = (h[1] - h[3]) + ((h[5] - h[6]) - (h[7] - h[8]));
           const R jy = (h[2] - h[4]) + ((h[5] + h[6]) - (h[7] + h[8]));
           const R px = jx + (R)0.5 * Fx, py = jy + (R)0.5 * Fy;
-          const R ir = (R)1 / cur_rho[k];
-          uxv[k] = px * ir;
-          uyv[k] = py * ir;
+          const R ir = (R)1 / cur_rho;
+          const R ux = px * ir, uy = py * ir;
+          const long long di = P.dense_off + (long long)yc * nx + x;
+          if (mo.flags & MOM_FIELDS) {
+            if (mo.rho) mo.rho[di] = (S)cur_rho;
+            if (mo.ux) mo.ux[di] = (S)ux;
+            if (mo.uy) mo.uy[di] = (S)uy;
+          }
           if (mo.flags & MOM_DIAG) {
-            const int col = sw.c0 + k;
-            if (col < xend) {
-              const R rh = cur_rho[k];
-              const bool fin_ok = finite_(rh) && finite_(uxv[k]) && finite_(uyv[k]);
-              if (!fin_ok) {
-                ++bad;
-              } else {
-                acc_m += (double)rh;
-                acc_x += (double)px;
-                acc_y += (double)py;
-                const float u = (float)sqrt((double)(uxv[k] * uxv[k] + uyv[k] * uyv[k]));
-                mx_u = fmaxf(mx_u, u);
-                if (mo.rho_prev) {
-                  const long long di = P.dense_off + (long long)yc * nx + col;
-                  const float dd = (float)fabs((double)rh - (double)mo.rho_prev[di]);
-                  mx_d = fmaxf(mx_d, dd);
-                }
-              }
+            const bool ok = isfinite(cur_rho) && isfinite(ux) && isfinite(uy);
+            if (!ok) {
+              ++bad;
+            } else {
+              acc_m += (double)cur_rho;
+              acc_x += (double)px;
+              acc_y += (double)py;
+              mx_u = fmaxf(mx_u, (float)sqrt((double)ux * ux + (double)uy * uy));
+              if (mo.rho_prev)
+                mx_d = fmaxf(mx_d, (float)fabs((double)cur_rho - (double)mo.rho_prev[di]));
             }
           }
-        }
-      }
-      if (MODE == MODE_STEP) {
-        S* dst = fout + P.off + (long long)yc * sw.pitch + sw.c0;
-        if (full_owner) {
-#pragma unroll
-          for (int q = 0; q < Q; ++q) {
-            S v[VEC];
-#pragma unroll
-            for (int k = 0; k < VEC; ++k) v[k] = (S)outv[q][k];
-            vstore<S, VEC>(dst + (long long)q * sw.plane, v);
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < VEC; ++k)
-            if (sw.c0 + k < xend) {
-#pragma unroll
-              for (int q = 0; q < Q; ++q) dst[(long long)q * sw.plane + k] = (S)outv[q][k];
-            }
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) {
-          const int col = sw.c0 + k;
-          if (col < xend) {
-            const long long di = P.dense_off + (long long)yc * nx + col;
-            if (mo.flags & MOM_FIELDS) {
-              if (mo.rho) mo.rho[di] = (S)cur_rho[k];
-              if (mo.ux) mo.ux[di] = (S)uxv[k];
-              if (mo.uy) mo.uy[di] = (S)uyv[k];
-            }
-            if ((mo.flags & MOM_UPDATE_PREV) && mo.rho_prev) mo.rho_prev[di] = (S)cur_rho[k];
-          }
+          if ((mo.flags & MOM_UPDATE_PREV) && mo.rho_prev) mo.rho_prev[di] = (S)cur_rho;
         }
       }
     }
-    // Rotate: the row whose psi was just computed becomes the centre row.
 #pragma unroll
-    for (int q = 0; q < Q; ++q)
-#pragma unroll
-      for (int k = 0; k < VEC; ++k) cur[q][k] = nxt[q][k];
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) {
-      cur_drho[k] = nd[k];
-      cur_rho[k] = nr[k];
-    }
-    if (more) {
-#pragma unroll
-      for (int q = 0; q < Q; ++q)
-#pragma unroll
-        for (int k = 0; k < VEC; ++k) nxt[q][k] = pre[q][k];
-    }
+    for (int q = 0; q < Q; ++q) cur[q] = nxt[q];
+    cur_drho = ndrho;
+    cur_rho = nrho;
   }
 
+  if (s_abort) {
+    // A copy did not complete in time: wait (bounded) for the copies still in flight so
+    // no write lands in shared memory after this CTA has exited, then report.
+    if (tid == 0) {
+      // The newest row issued into each slot: once its phase completed, every earlier
+      // copy into that slot has too.
+      for (int k = 0; k < NSLOT && k < issued; ++k) {
+        const int j = issued - 1 - ((issued - 1 - k) & (NSLOT - 1));
+        mbar_wait_bounded(&bars[k], (uint32_t)((j / NSLOT) & 1));
+      }
+      atomicOr(status, STATUS_TIMEOUT);
+    }
+    return;
+  }
   if (MODE == MODE_STEP) {
     if (flag_bad) atomicOr(status, STATUS_NONFINITE);
   } else if (mo.flags & MOM_DIAG) {

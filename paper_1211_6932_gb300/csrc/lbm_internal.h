@@ -7,11 +7,13 @@
 namespace lbm {
 
 // Launch the fused sweep (MODE_STEP) or the moments/diagnostics pass (MODE_MOMENTS) over
-// n_items work items; vec selects the columns-per-thread instantiation.
+// n_items work items; nt (threads = columns per CTA) selects the instantiation.
 template <typename S>
-cudaError_t launch_sweep(int vec, int mode, const S* fin, S* fout, const InstParams* d_inst,
+cudaError_t launch_sweep(int nt, int mode, const S* fin, S* fout, const InstParams* d_inst,
                          const WorkItem* d_items, int n_items, const MomArgs<S>& mo,
                          int* d_status, cudaStream_t st);
+template <typename S>
+cudaError_t launch_fill_ghosts(S* buf, const InstParams& P, cudaStream_t st);
 template <typename S>
 cudaError_t launch_set_pops(const double* d_fc, S* buf, const InstParams& P, cudaStream_t st);
 template <typename S>
@@ -28,11 +30,11 @@ cudaError_t launch_diag_finalize(const double* part_sum, const float* part_max,
 
 // Resident CTAs per SM of the step kernel instantiation (at least 1).
 template <typename S>
-int sweep_occupancy(int vec);
+int sweep_occupancy(int nt);
 
-// Whether a (storage type, vec) pair has a kernel.
-inline bool vec_supported(bool fp64, int vec) {
-  return vec == 1 || vec == 2 || (vec == 4 && !fp64);
+// Whether a (storage type, threads per CTA) pair has a kernel.
+inline bool nt_supported(bool fp64, int nt) {
+  return nt == 64 || nt == 128 || (nt == 256 && !fp64);
 }
 
 }  // namespace lbm

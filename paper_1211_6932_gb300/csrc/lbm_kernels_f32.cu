@@ -33,14 +33,13 @@ __global__ void diag_finalize_kernel(const double* __restrict__ part_sum,
 
 
 template <>
-cudaError_t launch_sweep<float>(int vec, int mode, const float* fin, float* fout,
-                                const InstParams* d_inst, const WorkItem* d_items,
-                                int n_items, const MomArgs<float>& mo, int* d_status,
-                                cudaStream_t st) {
-  switch (vec) {
-    case 1: return launch_sweep_vec<float, 1>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
-    case 2: return launch_sweep_vec<float, 2>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
-    case 4: return launch_sweep_vec<float, 4>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
+cudaError_t launch_sweep<float>(int nt, int mode, const float* fin, float* fout,
+                             const InstParams* d_inst, const WorkItem* d_items, int n_items,
+                             const MomArgs<float>& mo, int* d_status, cudaStream_t st) {
+  switch (nt) {
+    case 64: return launch_sweep_mode<float, 64>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
+    case 128: return launch_sweep_mode<float, 128>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
+    case 256: return launch_sweep_mode<float, 256>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -54,16 +53,13 @@ cudaError_t launch_diag_finalize(const double* part_sum, const float* part_max,
 }
 
 template <>
-int sweep_occupancy<float>(int vec) {
-  int occ = 0;
-  cudaError_t e = cudaErrorInvalidValue;
-  switch (vec) {
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_kernel<float, 1, MODE_STEP>, NT, 0); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_kernel<float, 2, MODE_STEP>, NT, 0); break;
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_kernel<float, 4, MODE_STEP>, NT, 0); break;
-    default: break;
+int sweep_occupancy<float>(int nt) {
+  switch (nt) {
+    case 64: return occupancy_nt<float, 64>();
+    case 128: return occupancy_nt<float, 128>();
+    case 256: return occupancy_nt<float, 256>();
+    default: return 1;
   }
-  return (e == cudaSuccess && occ > 0) ? occ : 1;
 }
 
 }  // namespace lbm

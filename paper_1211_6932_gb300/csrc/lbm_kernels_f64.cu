@@ -4,27 +4,23 @@
 namespace lbm {
 
 template <>
-cudaError_t launch_sweep<double>(int vec, int mode, const double* fin, double* fout,
-                                 const InstParams* d_inst, const WorkItem* d_items,
-                                 int n_items, const MomArgs<double>& mo, int* d_status,
-                                 cudaStream_t st) {
-  switch (vec) {
-    case 1: return launch_sweep_vec<double, 1>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
-    case 2: return launch_sweep_vec<double, 2>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
+cudaError_t launch_sweep<double>(int nt, int mode, const double* fin, double* fout,
+                             const InstParams* d_inst, const WorkItem* d_items, int n_items,
+                             const MomArgs<double>& mo, int* d_status, cudaStream_t st) {
+  switch (nt) {
+    case 64: return launch_sweep_mode<double, 64>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
+    case 128: return launch_sweep_mode<double, 128>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <>
-int sweep_occupancy<double>(int vec) {
-  int occ = 0;
-  cudaError_t e = cudaErrorInvalidValue;
-  switch (vec) {
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_kernel<double, 1, MODE_STEP>, NT, 0); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sweep_kernel<double, 2, MODE_STEP>, NT, 0); break;
-    default: break;
+int sweep_occupancy<double>(int nt) {
+  switch (nt) {
+    case 64: return occupancy_nt<double, 64>();
+    case 128: return occupancy_nt<double, 128>();
+    default: return 1;
   }
-  return (e == cudaSuccess && occ > 0) ? occ : 1;
 }
 
 }  // namespace lbm

@@ -5,18 +5,45 @@
 
 namespace lbm {
 
-template <typename S, int VEC>
-static cudaError_t launch_sweep_vec(int mode, const S* fin, S* fout, const InstParams* d_inst,
-                                    const WorkItem* d_items, int n_items,
-                                    const MomArgs<S>& mo, int* d_status, cudaStream_t st) {
+template <typename S, int NT, int MODE>
+static cudaError_t launch_sweep_nt(const S* fin, S* fout, const InstParams* d_inst,
+                                   const WorkItem* d_items, int n_items, const MomArgs<S>& mo,
+                                   int* d_status, cudaStream_t st) {
+  constexpr size_t smem = SweepSmem<S, NT>::BYTES;
+  static bool configured = false;  // one attribute call per instantiation and process
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<S, NT, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
   if (n_items <= 0) return cudaSuccess;
-  if (mode == MODE_STEP)
-    sweep_kernel<S, VEC, MODE_STEP><<<n_items, NT, 0, st>>>(fin, fout, d_inst, d_items,
-                                                           n_items, mo, d_status);
-  else
-    sweep_kernel<S, VEC, MODE_MOMENTS><<<n_items, NT, 0, st>>>(fin, fout, d_inst, d_items,
-                                                              n_items, mo, d_status);
+  sweep_kernel<S, NT, MODE><<<n_items, NT, smem, st>>>(fin, fout, d_inst, d_items, n_items,
+                                                       mo, d_status);
   return cudaGetLastError();
+}
+
+template <typename S, int NT>
+static cudaError_t launch_sweep_mode(int mode, const S* fin, S* fout, const InstParams* d_inst,
+                                     const WorkItem* d_items, int n_items,
+                                     const MomArgs<S>& mo, int* d_status, cudaStream_t st) {
+  if (mode == MODE_STEP)
+    return launch_sweep_nt<S, NT, MODE_STEP>(fin, fout, d_inst, d_items, n_items, mo,
+                                             d_status, st);
+  return launch_sweep_nt<S, NT, MODE_MOMENTS>(fin, fout, d_inst, d_items, n_items, mo,
+                                              d_status, st);
+}
+
+template <typename S, int NT>
+static int occupancy_nt() {
+  constexpr size_t smem = SweepSmem<S, NT>::BYTES;
+  cudaFuncSetAttribute(sweep_kernel<S, NT, MODE_STEP>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &occ, sweep_kernel<S, NT, MODE_STEP>, NT, smem);
+  return (e == cudaSuccess && occ > 0) ? occ : 1;
 }
 
 static inline int grid_for(long long n) {
@@ -44,6 +71,11 @@ cudaError_t launch_init_eq(const double* rho, const double* ux, const double* uy
   return cudaGetLastError();
 }
 template <typename S>
+cudaError_t launch_fill_ghosts(S* buf, const InstParams& P, cudaStream_t st) {
+  fill_ghosts_kernel<S><<<grid_for((long long)Q * P.ny * 4), 256, 0, st>>>(buf, P);
+  return cudaGetLastError();
+}
+template <typename S>
 cudaError_t launch_psi(const double* d_rho, double* d_out, long long n,
                        const InstParams* d_inst, cudaStream_t st) {
   psi_kernel<S><<<grid_for(n), 256, 0, st>>>(d_rho, d_out, n, d_inst);
@@ -61,4 +93,5 @@ cudaError_t launch_psi(const double* d_rho, double* d_out, long long n,
                                               S*, const lbm::InstParams&, int*,             \
                                               cudaStream_t);                                \
   template cudaError_t lbm::launch_psi<S>(const double*, double*, long long,                \
-                                          const lbm::InstParams*, cudaStream_t);
+                                          const lbm::InstParams*, cudaStream_t);            \
+  template cudaError_t lbm::launch_fill_ghosts<S>(S*, const lbm::InstParams&, cudaStream_t);

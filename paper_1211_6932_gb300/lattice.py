@@ -81,7 +81,7 @@ class Lattice:
 
     def __init__(self, nx, ny, eos: Eos, G=-1.0, sigma=0.0, s=None, nu_l=0.0, nu_v=0.0,
                  precision="fp32", visc_mode=None, bc="periodic", psi_fp64=False,
-                 rho_ref=None, rho_c=None, rho_l=None, rho_v=None, stream=None, tile_vec=0,
+                 rho_ref=None, rho_c=None, rho_l=None, rho_v=None, stream=None, tile_threads=0,
                  tile_rows=0, device=None):
         self._L = C.lib()
         self.nx, self.ny = int(nx), int(ny)
@@ -105,7 +105,7 @@ class Lattice:
         sp = _stream_ptr(stream)
         o.stream = sp.value if sp is not None else None
         o.device = _device_of(stream, device)
-        o.tile_vec = int(tile_vec)
+        o.tile_threads = int(tile_threads)
         o.tile_rows = int(tile_rows)
         h = ctypes.c_void_p()
         rc = self._L.lbm_create(ctypes.byref(h), self.nx, self.ny, eos.c(), float(G),
@@ -212,12 +212,13 @@ class Lattice:
 
     @property
     def tiling(self):
+        """(threads per CTA, rows per CTA sweep) of the step kernel."""
         v, r = ctypes.c_int(), ctypes.c_int()
         self._check(self._L.lbm_get_tiling(self._h, ctypes.byref(v), ctypes.byref(r)))
         return v.value, r.value
 
-    def set_tiling(self, vec=0, rows=0):
-        self._check(self._L.lbm_set_tiling(self._h, int(vec), int(rows)))
+    def set_tiling(self, threads=0, rows=0):
+        self._check(self._L.lbm_set_tiling(self._h, int(threads), int(rows)))
 
     @property
     def stream(self):
@@ -260,7 +261,7 @@ class Instance:
 class Batch:
     """Many independent lattices advanced by one launch per step (lbm_batch_*)."""
 
-    def __init__(self, instances, precision="fp32", stream=None, tile_vec=0, tile_rows=0,
+    def __init__(self, instances, precision="fp32", stream=None, tile_threads=0, tile_rows=0,
                  device=None):
         self._L = C.lib()
         self.instances = list(instances)
@@ -269,7 +270,7 @@ class Batch:
         sp = _stream_ptr(stream)
         rc = self._L.lbm_batch_create(ctypes.byref(h), len(self.instances), arr,
                                       _PREC[precision], sp, _device_of(stream, device),
-                                      int(tile_vec), int(tile_rows))
+                                      int(tile_threads), int(tile_rows))
         if rc != 0:
             raise LbmError(rc, self._L.lbm_batch_last_error(None).decode())
         self._h = h

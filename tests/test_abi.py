@@ -44,7 +44,7 @@ def test_options_default(lib):
     o = C.lbm_options()
     lib.lbm_options_default(ctypes.byref(o))
     assert o.precision == C.LBM_FP32_DEV and o.visc_mode == -1 and o.rho_ref < 0
-    assert o.tile_vec == 0 and o.tile_rows == 0 and not o.stream
+    assert o.tile_threads == 0 and o.tile_rows == 0 and not o.stream
 
 
 def test_host_maxwell_matches_oracle_quadrature(lib):
