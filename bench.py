@@ -263,7 +263,8 @@ def run_gpu(args):
     stream = torch.cuda.Stream(device=dev)
     L = Lattice(NX, NY, eos, G=-1.0, sigma=SIGMA, s=RATES, nu_l=NU_L, nu_v=NU_V,
                 precision="fp32", visc_mode="linear", stream=stream,
-                tile_threads=args.tile_threads, tile_rows=args.tile_rows)
+                tile_threads=args.tile_threads, tile_vec=args.tile_vec,
+                tile_rows=args.tile_rows)
     L.init_fields(rho)
     n_nodes = NX * NY
 
@@ -338,18 +339,18 @@ def run_gpu(args):
     peak, peak_kind = load_peak()
     achieved = BYTES_PER_LU * n_nodes / (avg_launch_ms * 1e-3) / 1e9
     traffic = load_traffic(n_nodes)
-    nt, rows = L.tiling
+    nt, vec, rows = L.tiling
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": total_ms_max / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config({"tile_threads": nt, "tile_rows": rows}),
+            "config": config({"tile_threads": nt, "tile_vec": vec, "tile_rows": rows}),
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_kind,
-                         "kernel": "sweep_kernel<float,%d,STEP>" % nt,
+                         "kernel": "sweep_kernel<float,%d,%d,STEP>" % (nt, vec),
                          "algorithmic_bytes_per_launch": BYTES_PER_LU * n_nodes,
                          "avg_launch_ms": avg_launch_ms},
             "e2e": {"value": e2e_value, "unit": "MLUPS",
@@ -379,6 +380,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--tile-threads", type=int, default=0)
+    ap.add_argument("--tile-vec", type=int, default=0)
     ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -76,8 +76,12 @@ typedef struct {
   void* stream;   /* cudaStream_t to queue work on; NULL: a stream the handle owns */
   int device;     /* CUDA device ordinal; -1 (default): the library's current device.
                      Every call on the handle makes this device current first. */
-  int tile_threads; /* threads (one column each) per CTA of the step kernel: 64, 128 or
-                       256 (256 is FP32 only); 0 (default): 256 for FP32_DEV, 128 for FP64 */
+  int tile_threads; /* threads per CTA of the step kernel; 0 (default): 64 for FP32_DEV,
+                       128 for FP64 */
+  int tile_vec;     /* adjacent columns per thread: 1, or 2 (FP32 only: packed float2
+                       arithmetic); available (threads, vec) pairs: FP32 (64|128|256, 1),
+                       (64|128, 2); FP64 (64|128, 1).  0 (default): 2 for FP32_DEV, 1 for
+                       FP64.  A CTA owns threads*vec - 4 columns. */
   int tile_rows;  /* rows per CTA sweep; 0 (default): sized to fill the GPU */
 } lbm_options;
 
@@ -182,10 +186,10 @@ int lbm_eval_psi(lbm_handle* h, const double* rho, double* psi, size_t n);
 int lbm_save(lbm_handle* h, const char* path);
 int lbm_load(lbm_handle* h, const char* path);
 
-/* Kernel configuration in use: threads (columns) per CTA and rows per CTA sweep. */
-int lbm_get_tiling(const lbm_handle* h, int* threads, int* rows);
+/* Kernel configuration in use: threads per CTA, columns per thread, rows per CTA sweep. */
+int lbm_get_tiling(const lbm_handle* h, int* threads, int* vec, int* rows);
 /* Change it (same meaning as the lbm_options fields; 0 picks the default). */
-int lbm_set_tiling(lbm_handle* h, int threads, int rows);
+int lbm_set_tiling(lbm_handle* h, int threads, int vec, int rows);
 
 /* The CUDA stream the handle queues work on (a cudaStream_t). */
 void* lbm_stream(const lbm_handle* h);
@@ -220,9 +224,10 @@ typedef struct {
 } lbm_instance;
 
 /* Create a batch of n >= 1 instances in one precision; stream may be NULL; device,
- * tile_threads and tile_rows as in lbm_options (-1, 0, 0 = defaults). */
+ * tile_threads, tile_vec and tile_rows as in lbm_options (-1, 0, 0, 0 = defaults). */
 int lbm_batch_create(lbm_batch** out, int n, const lbm_instance* inst, int precision,
-                     void* stream, int device, int tile_threads, int tile_rows);
+                     void* stream, int device, int tile_threads, int tile_vec,
+                     int tile_rows);
 void lbm_batch_destroy(lbm_batch* b);
 const char* lbm_batch_last_error(const lbm_batch* b);
 

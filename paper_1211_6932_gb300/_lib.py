@@ -26,7 +26,7 @@ class lbm_options(ctypes.Structure):
     _fields_ = [("precision", c_int), ("visc_mode", c_int), ("bc", c_int), ("psi_fp64", c_int),
                 ("rho_ref", c_double), ("rho_c", c_double), ("rho_l", c_double),
                 ("rho_v", c_double), ("stream", c_void_p), ("device", c_int),
-                ("tile_threads", c_int), ("tile_rows", c_int)]
+                ("tile_threads", c_int), ("tile_vec", c_int), ("tile_rows", c_int)]
 
 
 class lbm_diag(ctypes.Structure):
@@ -62,12 +62,13 @@ SIGNATURES = {
     "lbm_eval_psi": (c_int, [c_void_p, dptr, dptr, c_size_t]),
     "lbm_save": (c_int, [c_void_p, ctypes.c_char_p]),
     "lbm_load": (c_int, [c_void_p, ctypes.c_char_p]),
-    "lbm_get_tiling": (c_int, [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
-    "lbm_set_tiling": (c_int, [c_void_p, c_int, c_int]),
+    "lbm_get_tiling": (c_int, [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                               ctypes.POINTER(c_int)]),
+    "lbm_set_tiling": (c_int, [c_void_p, c_int, c_int, c_int]),
     "lbm_stream": (c_void_p, [c_void_p]),
     "lbm_maxwell": (c_int, [lbm_eos, dptr, dptr]),
     "lbm_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(lbm_instance),
-                                 c_int, c_void_p, c_int, c_int, c_int]),
+                                 c_int, c_void_p, c_int, c_int, c_int, c_int]),
     "lbm_batch_destroy": (None, [c_void_p]),
     "lbm_batch_last_error": (ctypes.c_char_p, [c_void_p]),
     "lbm_batch_init_fields": (c_int, [c_void_p, c_int, dptr, dptr, dptr]),

@@ -58,7 +58,7 @@ struct Batch {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaStream_t cap_stream = nullptr;
-  int nt = 0, rows_req = 0, rows = 0;  // threads (= columns) per CTA, rows per sweep
+  int nt = 0, vec = 0, rows_req = 0, rows = 0;  // threads and columns/thread per CTA, rows per sweep
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   std::string err;
   int sms = 0;
@@ -91,6 +91,56 @@ int set_err(std::string& dst, int code, const char* fmt, ...) {
   } while (0)
 
 size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
+
+// Default kernel configuration per precision (threads per CTA, columns per thread).
+int default_threads(bool fp64) { return fp64 ? 128 : 64; }
+int default_vec(bool fp64) { return fp64 ? 1 : 2; }
+
+template <typename R>
+void fill_mirror(lbm::PhysParams<R>& m, const InstParams& P) {
+  m.b4 = (R)P.b4;
+  m.RT = (R)P.RT;
+  m.a = (R)P.a;
+  m.two_over_G = (R)P.two_over_G;
+  m.G = (R)P.G;
+  m.s1 = (R)P.s[1];
+  m.s2 = (R)P.s[2];
+  m.s4 = (R)P.s[4];
+  m.s6 = (R)P.s[6];
+  m.s7 = (R)P.s[7];
+  m.s8 = (R)P.s[8];
+  m.c1 = (R)(1.0 - 0.5 * P.s[1]);
+  m.c2 = (R)(1.0 - 0.5 * P.s[2]);
+  m.c4 = (R)(1.0 - 0.5 * P.s[4]);
+  m.c6 = (R)(1.0 - 0.5 * P.s[6]);
+  m.c7 = (R)(1.0 - 0.5 * P.s[7]);
+  m.c8 = (R)(1.0 - 0.5 * P.s[8]);
+  m.sig12_e = (R)P.sig12_e;
+  m.sig12_z = (R)P.sig12_z;
+  m.tau_l = (R)P.tau_l;
+  m.tau_v = (R)P.tau_v;
+  m.dtau = (R)(P.tau_l - P.tau_v);
+  m.rho_c = (R)P.rho_c;
+  m.rho_v = (R)P.rho_v;
+  m.inv_drho_lv = P.rho_l != P.rho_v ? (R)(1.0 / (P.rho_l - P.rho_v)) : (R)0;
+  m.rho_ref = (R)P.rho_ref;
+  m.g1 = (R)(-P.G / 3.0);
+  m.g2 = (R)(-P.G / 12.0);
+  m.k1s = (R)(P.s[1] / 36.0);
+  m.k1v = (R)((1.0 - 0.5 * P.s[1]) / 6.0);
+  m.k1f = (R)(P.sig12_e / 36.0);
+  m.k2s = (R)(P.s[2] / 36.0);
+  m.k2v = (R)((1.0 - 0.5 * P.s[2]) / 6.0);
+  m.k2f = (R)(P.sig12_z / 36.0);
+  m.k4s = (R)(P.s[4] / 12.0);
+  m.k4f = (R)((1.0 - 0.5 * P.s[4]) / 12.0);
+  m.k6s = (R)(P.s[6] / 12.0);
+  m.k6f = (R)((1.0 - 0.5 * P.s[6]) / 12.0);
+  m.k7s = (R)(P.s[7] / 4.0);
+  m.k7v = (R)((1.0 - 0.5 * P.s[7]) / 2.0);
+  m.k8s = (R)(P.s[8] / 4.0);
+  m.k8v = (R)((1.0 - 0.5 * P.s[8]) / 4.0);
+}
 
 template <typename T>
 void free_dev(T*& p) {
@@ -130,23 +180,26 @@ void destroy_batch(Batch* b) {
 }
 
 int sweep_occupancy(const Batch* b) {
-  return b->fp64 ? lbm::sweep_occupancy<double>(b->nt) : lbm::sweep_occupancy<float>(b->nt);
+  return b->fp64 ? lbm::sweep_occupancy<double>(b->nt, b->vec)
+                 : lbm::sweep_occupancy<float>(b->nt, b->vec);
 }
 
-// Rows per CTA sweep: enough work items for one full wave of resident CTAs.
+// Rows per CTA sweep: about six waves of resident CTAs (measured best on 4096^2: fewer
+// rows cost halo re-reads and row-loop start-up, more rows leave SMs idle in the tail),
+// clamped to [8, 64].
 int default_rows(const Batch* b) {
-  const int W = b->nt;
+  const int W = lbm::strip_width(b->nt, b->vec);
   long long strip_rows = 0;
   for (int i = 0; i < b->n_inst; ++i)
     if (b->active[i]) strip_rows += (long long)((b->inst[i].nx + W - 1) / W) * b->inst[i].ny;
-  const long long target = (long long)std::max(b->sms, 1) * sweep_occupancy(b);
+  const long long target = (long long)std::max(b->sms, 1) * sweep_occupancy(b) * 6;
   long long r = (strip_rows + target - 1) / std::max(target, 1LL);
-  return (int)std::max<long long>(4, r);
+  return (int)std::min<long long>(64, std::max<long long>(8, r));
 }
 
 void make_items(const Batch* b, bool only_active, int rows, std::vector<WorkItem>& out,
                 std::vector<int>* begin) {
-  const int W = b->nt;
+  const int W = lbm::strip_width(b->nt, b->vec);  // owned columns per CTA
   out.clear();
   if (begin) begin->assign(1, 0);
   for (int i = 0; i < b->n_inst; ++i) {
@@ -256,15 +309,20 @@ int fill_params(std::string& err, InstParams& P, const lbm_instance& in, bool fp
   P.rho_l = rl;
   P.rho_v = rv;
   P.rho_ref = fp64 ? 0.0 : (in.rho_ref >= 0 ? in.rho_ref : (have_maxwell ? mv : 0.0));
+  fill_mirror(P.pf, P);
+  fill_mirror(P.pd, P);
   return LBM_OK;
 }
 
 
 int create_batch(Batch* b, int n, const lbm_instance* in, bool fp64, int psi_fp64,
-                 void* stream, int device, int nt, int rows) {
+                 void* stream, int device, int nt, int vec, int rows) {
   if (n < 1 || !in) return set_err(b->err, LBM_EINVAL, "need at least one instance");
-  if (nt != 0 && !lbm::nt_supported(fp64, nt))
-    return set_err(b->err, LBM_EINVAL, "tile_threads %d not available for this precision", nt);
+  const int nt_ = nt ? nt : default_threads(fp64), vec_ = vec ? vec : default_vec(fp64);
+  if (!lbm::cfg_supported(fp64, nt_, vec_))
+    return set_err(b->err, LBM_EINVAL,
+                   "tile_threads %d with tile_vec %d is not available for this precision", nt_,
+                   vec_);
   if (rows < 0) return set_err(b->err, LBM_EINVAL, "tile_rows must be >= 0");
   b->fp64 = fp64;
   b->esz = fp64 ? sizeof(double) : sizeof(float);
@@ -285,7 +343,8 @@ int create_batch(Batch* b, int n, const lbm_instance* in, bool fp64, int psi_fp6
   }
   b->slab_elems = off;
   b->dense_elems = dense;
-  b->nt = nt ? nt : (fp64 ? 128 : 256);
+  b->nt = nt_;
+  b->vec = vec_;
   b->rows_req = rows;
   int dev_count = 0;
   if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1)
@@ -324,12 +383,12 @@ int launch_step(Batch* b, cudaStream_t st) {
   cudaError_t e;
   if (b->fp64) {
     MomArgs<double> mo{};
-    e = lbm::launch_sweep<double>(b->nt, lbm::MODE_STEP, (const double*)b->slab[c],
+    e = lbm::launch_sweep<double>(b->nt, b->vec, lbm::MODE_STEP, (const double*)b->slab[c],
                                   (double*)b->slab[c ^ 1], b->d_inst, b->d_items, b->n_items,
                                   mo, b->d_status, st);
   } else {
     MomArgs<float> mo{};
-    e = lbm::launch_sweep<float>(b->nt, lbm::MODE_STEP, (const float*)b->slab[c],
+    e = lbm::launch_sweep<float>(b->nt, b->vec, lbm::MODE_STEP, (const float*)b->slab[c],
                                  (float*)b->slab[c ^ 1], b->d_inst, b->d_items, b->n_items,
                                  mo, b->d_status, st);
   }
@@ -529,7 +588,7 @@ int moments_pass(Batch* b, const WorkItem* d_items, int n, MomArgs<S> mo) {
   mo.part_sum = b->d_part_sum;
   mo.part_max = b->d_part_max;
   mo.part_bad = b->d_part_bad;
-  cudaError_t e = lbm::launch_sweep<S>(b->nt, lbm::MODE_MOMENTS, (const S*)b->slab[b->cur],
+  cudaError_t e = lbm::launch_sweep<S>(b->nt, b->vec, lbm::MODE_MOMENTS, (const S*)b->slab[b->cur],
                                        nullptr, b->d_inst, d_items, n, mo, b->d_status,
                                        b->stream);
   if (e != cudaSuccess)
@@ -704,6 +763,7 @@ void lbm_options_default(lbm_options* o) {
   o->stream = nullptr;
   o->device = -1;
   o->tile_threads = 0;
+  o->tile_vec = 0;
   o->tile_rows = 0;
 }
 
@@ -735,7 +795,7 @@ int lbm_create(lbm_handle** out, int nx, int ny, lbm_eos eos, double G, double s
   lbm_handle* h = new (std::nothrow) lbm_handle();
   if (!h) return set_err(g_thread_err, LBM_ENOMEM, "out of host memory");
   int rc = create_batch(&h->b, 1, &in, o.precision == LBM_FP64, o.psi_fp64, o.stream,
-                        o.device, o.tile_threads, o.tile_rows);
+                        o.device, o.tile_threads, o.tile_vec, o.tile_rows);
   if (rc) {
     g_thread_err = h->b.err;
     destroy_batch(&h->b);
@@ -825,23 +885,28 @@ int lbm_eval_psi(lbm_handle* h, const double* rho, double* psi, size_t n) {
   return eval_psi(&h->b, rho, psi, n);
 }
 
-int lbm_get_tiling(const lbm_handle* h, int* threads, int* rows) {
+int lbm_get_tiling(const lbm_handle* h, int* threads, int* vec, int* rows) {
   DeviceGuard g_(h ? &h->b : nullptr);
   if (!h) return LBM_EINVAL;
   if (threads) *threads = h->b.nt;
+  if (vec) *vec = h->b.vec;
   if (rows) *rows = h->b.rows;
   return LBM_OK;
 }
 
-int lbm_set_tiling(lbm_handle* h, int threads, int rows) {
+int lbm_set_tiling(lbm_handle* h, int threads, int vec, int rows) {
   DeviceGuard g_(h ? &h->b : nullptr);
   if (!h) return LBM_EINVAL;
   Batch* b = &h->b;
-  if (threads != 0 && !lbm::nt_supported(b->fp64, threads))
-    return set_err(b->err, LBM_EINVAL, "tile_threads %d not available for this precision",
-                   threads);
+  const int nt_ = threads ? threads : default_threads(b->fp64);
+  const int vec_ = vec ? vec : default_vec(b->fp64);
+  if (!lbm::cfg_supported(b->fp64, nt_, vec_))
+    return set_err(b->err, LBM_EINVAL,
+                   "tile_threads %d with tile_vec %d is not available for this precision", nt_,
+                   vec_);
   if (rows < 0) return set_err(b->err, LBM_EINVAL, "tile_rows must be >= 0");
-  b->nt = threads ? threads : (b->fp64 ? 128 : 256);
+  b->nt = nt_;
+  b->vec = vec_;
   b->rows_req = rows;
   return rebuild_items(b);
 }
@@ -922,7 +987,8 @@ int lbm_load(lbm_handle* h, const char* path) {
 // Batches
 
 int lbm_batch_create(lbm_batch** out, int n, const lbm_instance* inst, int precision,
-                     void* stream, int device, int tile_threads, int tile_rows) {
+                     void* stream, int device, int tile_threads, int tile_vec,
+                     int tile_rows) {
   if (!out) return set_err(g_thread_err, LBM_EINVAL, "out must not be NULL");
   *out = nullptr;
   if (precision != LBM_FP64 && precision != LBM_FP32_DEV)
@@ -930,7 +996,7 @@ int lbm_batch_create(lbm_batch** out, int n, const lbm_instance* inst, int preci
   lbm_batch* b = new (std::nothrow) lbm_batch();
   if (!b) return set_err(g_thread_err, LBM_ENOMEM, "out of host memory");
   int rc = create_batch(&b->b, n, inst, precision == LBM_FP64, 0, stream, device,
-                        tile_threads, tile_rows);
+                        tile_threads, tile_vec, tile_rows);
   if (rc) {
     g_thread_err = b->b.err;
     destroy_batch(&b->b);

@@ -114,7 +114,7 @@ __global__ void psi_kernel(const double* __restrict__ rho, double* __restrict__ 
   const Phys<S> ph = load_phys<S>(*Pp);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
-    out[i] = (double)psi_of<S>((S)rho[i], ph);
+    out[i] = (double)psi_t<S, S>((S)rho[i], ph);
 }
 
 }  // namespace lbm

@@ -1,10 +1,11 @@
 // Device side of the D2Q9 MRT pseudopotential step (Li, Luo & Li, arXiv:1211.6932).
 //
-// One fused kernel per time step.  A CTA owns a strip of NT columns (one column per
-// thread) and a chunk of rows of one lattice instance, and sweeps the chunk row by row:
+// One fused kernel per time step.  A CTA owns a strip of NT*VEC columns (VEC adjacent
+// columns per thread) and a chunk of rows of one lattice instance, and sweeps the chunk
+// row by row:
 //   - one elected thread streams the population rows of the strip (plus a 4-column halo
-//     on each side) into an 8-row ring in shared memory with bulk asynchronous copies
-//     (cp.async.bulk, completion on an mbarrier per slot), up to six rows ahead;
+//     on each side) into a ring of NSLOT rows in shared memory with bulk asynchronous
+//     copies (cp.async.bulk, completion on an mbarrier per slot), NSLOT-3 rows ahead;
 //   - every thread pulls the nine populations of its node from the ring (Eq. 5, pull
 //     form), sums them to rho (Eq. 6) and evaluates psi (Eqs. 24, 30) into a four-row
 //     psi ring, keeping the pulled values in registers;
@@ -31,8 +32,8 @@ namespace lbm {
 constexpr int Q = 9;
 constexpr int GHOST = 8;     // storage columns kept on each side of a row (32 B in FP32)
 constexpr int SEG_HALO = 4;  // shared-memory row segment starts 4 columns left of a strip
-constexpr int NSLOT = 8;     // population rows in the shared-memory ring (power of 2)
 constexpr int PSI_ROWS = 4;  // psi rows in the psi ring (power of 2)
+constexpr int PSI_OFF = 2;   // psi ring column of CTA column 0 (keeps pairs 8-byte aligned)
 constexpr long long WAIT_LIMIT = 1LL << 26;  // bounded mbarrier polls before giving up
 
 // D2Q9 velocities: rest, E, N, W, S, NE, NW, SW, SE.
@@ -55,6 +56,26 @@ enum { MODE_STEP = 0, MODE_MOMENTS = 1 };
 enum { MOM_FIELDS = 1, MOM_DIAG = 2, MOM_UPDATE_PREV = 4 };
 enum { STATUS_NONFINITE = 1, STATUS_TIMEOUT = 2 };
 
+// Physical parameters in the arithmetic type of a kernel, prepared on the host so the
+// kernels convert nothing (double-to-float conversions run on the slow FP64 pipe).
+template <typename R>
+struct PhysParams {
+  R b4, RT, a, two_over_G, G;           // Eqs. 24, 30 and 7
+  R s1, s2, s4, s6, s7, s8;             // rates of Eq. 2 that are not conserved
+  R c1, c2, c4, c6, c7, c8;             // 1 - s/2 for the same rates (Eq. 4)
+  R sig12_e, sig12_z;                   // 12 sigma s_e, 12 sigma s_zeta (Eq. 25 reduced)
+  R tau_l, tau_v, dtau, rho_c;          // viscosity modes; dtau = tau_l - tau_v
+  R rho_v, inv_drho_lv;                 // linear mode: 1 / (rho_l - rho_v)
+  R rho_ref;                            // deviation reference density
+  // The same constants folded with the weights of Eq. 7 and the column norms of M^{-1},
+  // as the step kernel uses them (see collide_t).
+  R g1, g2;                             // -G/3, -G/12
+  R k1s, k1v, k1f;                      // s1/36, c1/6, 12 sigma s1/36
+  R k2s, k2v, k2f;                      // s2/36, c2/6, 12 sigma s2/36
+  R k4s, k4f, k6s, k6f;                 // s4/12, c4/12, s6/12, c6/12
+  R k7s, k7v, k8s, k8v;                 // s7/4, c7/2, s8/4, c8/4 (constant viscosity)
+};
+
 // Parameters of one lattice instance (host fills, kernels read).
 struct InstParams {
   int nx, ny;
@@ -76,9 +97,12 @@ struct InstParams {
   double rho_c;        // switch density of VISC_STEP
   double rho_l, rho_v; // end points of VISC_LINEAR
   double rho_ref;      // deviation reference density
+  PhysParams<float> pf;  // the above in float, for FP32 kernels
+  PhysParams<double> pd; // and in double, for FP64 kernels
 };
 
-// One CTA's share of the work: columns [x0, x0 + NT) and rows [y0, y1) of instance inst.
+// One CTA's share of the work: columns [x0, x0 + NT*VEC) and rows [y0, y1) of instance
+// inst.
 // dir = +1 sweeps upwards, -1 downwards.  Alternating the direction between neighbouring
 // chunks makes the two CTAs that share halo rows read them at about the same time, so
 // the second read hits L2.
@@ -100,55 +124,34 @@ struct MomArgs {
 };
 
 template <typename R>
-struct Phys {
-  R b4, RT, a, two_over_G, G;
-  R s1, s2, s4, s6, s7, s8;
-  R sig12_e, sig12_z;
-  R tau_l, tau_v, rho_c, rho_l, inv_drho_lv, rho_v;
-  R rho_ref;
+struct Phys : PhysParams<R> {
   int visc_mode, psi_fp64;
-  double b4d, RTd, ad, two_over_Gd;
+  double b4d, RTd, ad, two_over_Gd;  // psi in double precision for FP32 storage
 };
+
+template <typename R>
+__device__ __forceinline__ const PhysParams<R>& phys_params(const InstParams& P);
+template <>
+__device__ __forceinline__ const PhysParams<float>& phys_params<float>(const InstParams& P) {
+  return P.pf;
+}
+template <>
+__device__ __forceinline__ const PhysParams<double>& phys_params<double>(const InstParams& P) {
+  return P.pd;
+}
 
 template <typename R>
 __device__ __forceinline__ Phys<R> load_phys(const InstParams& P) {
   Phys<R> p;
-  p.b4 = (R)P.b4; p.RT = (R)P.RT; p.a = (R)P.a; p.two_over_G = (R)P.two_over_G; p.G = (R)P.G;
-  p.s1 = (R)P.s[1]; p.s2 = (R)P.s[2]; p.s4 = (R)P.s[4]; p.s6 = (R)P.s[6];
-  p.s7 = (R)P.s[7]; p.s8 = (R)P.s[8];
-  p.sig12_e = (R)P.sig12_e; p.sig12_z = (R)P.sig12_z;
-  p.tau_l = (R)P.tau_l; p.tau_v = (R)P.tau_v; p.rho_c = (R)P.rho_c;
-  p.rho_l = (R)P.rho_l; p.rho_v = (R)P.rho_v;
-  p.inv_drho_lv = (P.rho_l != P.rho_v) ? (R)(1.0 / (P.rho_l - P.rho_v)) : (R)0;
-  p.rho_ref = (R)P.rho_ref;
-  p.visc_mode = P.visc_mode; p.psi_fp64 = P.psi_fp64;
+  static_cast<PhysParams<R>&>(p) = phys_params<R>(P);
+  p.visc_mode = P.visc_mode;
+  p.psi_fp64 = P.psi_fp64;
   p.b4d = P.b4; p.RTd = P.RT; p.ad = P.a; p.two_over_Gd = P.two_over_G;
   return p;
 }
 
-// Reciprocal and square root.  FP32 uses the hardware approximations (a couple of ulps);
-// FP64 keeps IEEE division and sqrt.
-__device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
-__device__ __forceinline__ float recip(float a) { return __fdividef(1.0f, a); }
-__device__ __forceinline__ double recip(double a) { return 1.0 / a; }
-__device__ __forceinline__ float sqrt_pos(float a) { return a > 0.f ? a * rsqrtf(a) : 0.f; }
-__device__ __forceinline__ double sqrt_pos(double a) { return a > 0.0 ? sqrt(a) : 0.0; }
-
-// psi of Eq. 24 with the Carnahan-Starling pressure of Eq. 30, written in factored form
-//   psi^2 = (2/G) * rho * (R T Z(x) - a rho - 1/3),  x = b rho / 4,
-//   Z(x) = (1 + x + x^2 - x^3) / (1 - x)^3,
-// which equals 2 (p_EOS - rho/3) / G.  Pulling rho out of the bracket leaves three terms
-// of comparable size and no cancellation at vapour density.  Negative arguments clamp to 0.
-template <typename R>
-__device__ __forceinline__ R psi_eval(R rho, const Phys<R>& p) {
-  R x = p.b4 * rho;
-  R num = (R)1 + x * ((R)1 + x * ((R)1 - x));
-  R omx = (R)1 - x;
-  R z = fast_div(num, omx * omx * omx);
-  R brk = p.RT * z - p.a * rho - (R)(1.0 / 3.0);
-  return sqrt_pos(p.two_over_G * rho * brk);
-}
+// psi of Eq. 24 with the Carnahan-Starling pressure of Eq. 30 in double precision, for
+// the option of evaluating psi in FP64 under FP32 storage (see psi_t for the form).
 __device__ __forceinline__ double psi_eval_f64(double rho, double b4, double RT, double a,
                                                double two_over_G) {
   double x = b4 * rho;
@@ -157,27 +160,6 @@ __device__ __forceinline__ double psi_eval_f64(double rho, double b4, double RT,
   double z = num / (omx * omx * omx);
   double arg = two_over_G * rho * (RT * z - a * rho - (1.0 / 3.0));
   return arg > 0.0 ? sqrt(arg) : 0.0;
-}
-template <typename R>
-__device__ __forceinline__ R psi_of(R rho, const Phys<R>& p) {
-  if (sizeof(R) == 4 && p.psi_fp64)
-    return (R)psi_eval_f64((double)rho, p.b4d, p.RTd, p.ad, p.two_over_Gd);
-  return psi_eval<R>(rho, p);
-}
-
-// Stress-moment rate for the viscosity modes (Eq. 10: nu = (tau - 1/2)/3).
-template <typename R>
-__device__ __forceinline__ R stress_rate(R rho, R s_const, const Phys<R>& p) {
-  if (p.visc_mode == VISC_CONST) return s_const;
-  R tau;
-  if (p.visc_mode == VISC_STEP) {
-    tau = rho >= p.rho_c ? p.tau_l : p.tau_v;
-  } else {
-    R fr = (rho - p.rho_v) * p.inv_drho_lv;
-    fr = fr < (R)0 ? (R)0 : (fr > (R)1 ? (R)1 : fr);
-    tau = p.tau_v + fr * (p.tau_l - p.tau_v);
-  }
-  return recip(tau);
 }
 
 __device__ __forceinline__ int wrapi(int i, int n) {
@@ -236,96 +218,236 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 // ---------------------------------------------------------------------------------------
-// Collision of one node in moment space (Eqs. 3, 4, 25), deviation form.
+// Arithmetic used by the collision, written once for three number types: float and
+// double (one node per value) and float2 (two nodes per value, Blackwell's packed FP32
+// instructions: one FFMA2/FADD2/FMUL2 does the work of two scalar instructions).
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 operator*(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+
+template <typename T> struct Num;
+template <> struct Num<float> {
+  typedef float S;
+  static __device__ __forceinline__ float k(float v) { return v; }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
+  static __device__ __forceinline__ float rcp(float a) { return __fdividef(1.0f, a); }
+  static __device__ __forceinline__ float div(float a, float b) { return a * __fdividef(1.0f, b); }
+  static __device__ __forceinline__ float sqrtp(float a) { return a > 0.f ? a * rsqrtf(a) : 0.f; }
+  static __device__ __forceinline__ float clamp01(float a) { return fminf(fmaxf(a, 0.f), 1.f); }
+  static __device__ __forceinline__ float sel_ge(float a, float t, float x, float y) {
+    return a >= t ? x : y;
+  }
+};
+template <> struct Num<double> {
+  typedef double S;
+  static __device__ __forceinline__ double k(double v) { return v; }
+  static __device__ __forceinline__ double fma(double a, double b, double c) {
+    return ::fma(a, b, c);
+  }
+  static __device__ __forceinline__ double rcp(double a) { return 1.0 / a; }
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double sqrtp(double a) { return a > 0.0 ? sqrt(a) : 0.0; }
+  static __device__ __forceinline__ double clamp01(double a) { return fmin(fmax(a, 0.0), 1.0); }
+  static __device__ __forceinline__ double sel_ge(double a, double t, double x, double y) {
+    return a >= t ? x : y;
+  }
+};
+template <> struct Num<float2> {
+  typedef float S;
+  static __device__ __forceinline__ float2 k(float v) { return make_float2(v, v); }
+  static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) {
+    return __ffma2_rn(a, b, c);
+  }
+  static __device__ __forceinline__ float2 rcp(float2 a) {
+    return make_float2(__fdividef(1.0f, a.x), __fdividef(1.0f, a.y));
+  }
+  static __device__ __forceinline__ float2 div(float2 a, float2 b) { return a * rcp(b); }
+  static __device__ __forceinline__ float2 sqrtp(float2 a) {
+    return make_float2(Num<float>::sqrtp(a.x), Num<float>::sqrtp(a.y));
+  }
+  static __device__ __forceinline__ float2 clamp01(float2 a) {
+    return make_float2(Num<float>::clamp01(a.x), Num<float>::clamp01(a.y));
+  }
+  static __device__ __forceinline__ float2 sel_ge(float2 a, float t, float x, float y) {
+    return make_float2(a.x >= t ? x : y, a.y >= t ? x : y);
+  }
+};
+
+// psi of Eq. 24 with the Carnahan-Starling pressure of Eq. 30, written in factored form
+//   psi^2 = (2/G) * rho * (R T Z(x) - a rho - 1/3),  x = b rho / 4,
+//   Z(x) = (1 + x + x^2 - x^3) / (1 - x)^3,
+// which equals 2 (p_EOS - rho/3) / G.  Pulling rho out of the bracket leaves three terms
+// of comparable size and no cancellation at vapour density.  Negative arguments clamp to 0.
+template <typename T, typename R>
+__device__ __forceinline__ T psi_t(T rho, const Phys<R>& p) {
+  typedef Num<T> N;
+  if constexpr (sizeof(R) == 4) {
+    if (p.psi_fp64) {
+      if constexpr (sizeof(T) == 8) {
+        return make_float2((float)psi_eval_f64((double)rho.x, p.b4d, p.RTd, p.ad, p.two_over_Gd),
+                           (float)psi_eval_f64((double)rho.y, p.b4d, p.RTd, p.ad, p.two_over_Gd));
+      } else {
+        return (T)psi_eval_f64((double)rho, p.b4d, p.RTd, p.ad, p.two_over_Gd);
+      }
+    }
+  }
+  const T x = N::k(p.b4) * rho;
+  const T num = N::fma(x, N::fma(x, N::k(1) - x, N::k(1)), N::k(1));
+  const T omx = N::k(1) - x;
+  const T z = N::div(num, omx * omx * omx);
+  const T brk = N::fma(N::k(p.RT), z, N::fma(N::k(-p.a), rho, N::k(-1.0 / 3.0)));
+  return N::sqrtp(N::k(p.two_over_G) * rho * brk);
+}
+
+// Collision of one node (or a pair) in moment space, Eqs. 3, 4 and 25, deviation form.
 //   h: pulled deviation populations (in), post-collision deviations (out)
 //   drho = sum h, rho = rho_ref + drho
 //   fpx, fpy: F / psi(x) (Eq. 7 without the leading psi), psi_c = psi(x)
 // The moments of h differ from those of f only in m0..m2 (by rho_ref (1, -2, 1)), so the
-// equilibria of Eq. 3 enter as m_eq - rho_ref (1, -2, 1, 0, ...).  The update is applied as
-// h* = h + M^{-1} dm with M^{-1} = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4).
-// Conserved moments: dm0 = 0, and for j the relaxation cancels against half the force,
-// leaving dm3 = F_x, dm5 = F_y exactly.  The sigma term of Eq. 25 times (1 - s/2) reduces to
-// 12 sigma s |F/psi|^2 (because tau - 1/2 = (1 - s/2)/s).
-template <typename R>
-__device__ __forceinline__ void collide_node(R (&h)[Q], R drho, R rho, R psi_c, R fpx, R fpy,
-                                             const Phys<R>& p) {
-  const R Fx = psi_c * fpx, Fy = psi_c * fpy;
-  const R jx = (h[1] - h[3]) + ((h[5] - h[6]) - (h[7] - h[8]));
-  const R jy = (h[2] - h[4]) + ((h[5] + h[6]) - (h[7] + h[8]));
-  const R ir = recip(rho);
-  const R ux = (jx + (R)0.5 * Fx) * ir;
-  const R uy = (jy + (R)0.5 * Fy) * ir;
-  const R sa = (h[1] + h[3]) + (h[2] + h[4]);
-  const R sd = (h[5] + h[7]) + (h[6] + h[8]);
-  const R m1 = (R)2 * sd - sa - (R)4 * h[0];
-  const R m2 = sd - (R)2 * sa + (R)4 * h[0];
-  const R m4 = (R)-2 * (h[1] - h[3]) + ((h[5] - h[6]) - (h[7] - h[8]));
-  const R m6 = (R)-2 * (h[2] - h[4]) + ((h[5] + h[6]) - (h[7] + h[8]));
-  const R m7 = (h[1] + h[3]) - (h[2] + h[4]);
-  const R m8 = (h[5] + h[7]) - (h[6] + h[8]);
-  const R rux = rho * ux, ruy = rho * uy;
-  const R ru2 = rux * ux + ruy * uy;
-  const R e1 = (R)3 * ru2 - (R)2 * drho;
-  const R e2 = drho - (R)3 * ru2;
-  const R e7 = rux * ux - ruy * uy;
-  const R e8 = rux * uy;
-  const R vF = ux * Fx + uy * Fy;
-  const R F2 = fpx * fpx + fpy * fpy;
-  const R snu7 = stress_rate<R>(rho, p.s7, p);
-  const R snu8 = p.visc_mode == VISC_CONST ? p.s8 : snu7;
-  // dm_k = -s_k (m_k - meq_k) + (1 - s_k/2) S_k, S from Eq. 25.
-  const R d1 = -p.s1 * (m1 - e1) + ((R)1 - (R)0.5 * p.s1) * ((R)6 * vF) + p.sig12_e * F2;
-  const R d2 = -p.s2 * (m2 - e2) - ((R)1 - (R)0.5 * p.s2) * ((R)6 * vF) - p.sig12_z * F2;
-  const R d4 = -p.s4 * (m4 + rux) - ((R)1 - (R)0.5 * p.s4) * Fx;
-  const R d6 = -p.s6 * (m6 + ruy) - ((R)1 - (R)0.5 * p.s6) * Fy;
-  const R d7 = -snu7 * (m7 - e7) + ((R)1 - (R)0.5 * snu7) * ((R)2 * (ux * Fx - uy * Fy));
-  const R d8 = -snu8 * (m8 - e8) + ((R)1 - (R)0.5 * snu8) * (ux * Fy + uy * Fx);
-  const R a1 = d1 * (R)(1.0 / 36.0), a2 = d2 * (R)(1.0 / 36.0);
-  const R a3 = Fx * (R)(1.0 / 6.0), a5 = Fy * (R)(1.0 / 6.0);
-  const R a4 = d4 * (R)(1.0 / 12.0), a6 = d6 * (R)(1.0 / 12.0);
-  const R a7 = d7 * (R)0.25, a8 = d8 * (R)0.25;
-  const R A = -a1 - (R)2 * a2;
-  const R B = (R)2 * a1 + a2;
-  const R Px = a3 - (R)2 * a4, Py = a5 - (R)2 * a6;
-  const R X = a3 + a4, Y = a5 + a6;
-  h[0] += (R)4 * (a2 - a1);
-  h[1] += A + Px + a7;
-  h[3] += A - Px + a7;
-  h[2] += A + Py - a7;
-  h[4] += A - Py - a7;
-  h[5] += B + X + Y + a8;
-  h[6] += B - X + Y - a8;
-  h[7] += B - X - Y + a8;
-  h[8] += B + X - Y - a8;
+// equilibria of Eq. 3 enter as m_eq - rho_ref (1, -2, 1, 0, ...).  The update is applied
+// as h* = h + M^{-1} dm with M^{-1} = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4,
+// 1/4); the column norms and the rates are folded into the per-instance constants
+// PhysParams::k* (a_k = dm_k / |row k of M|^2).  Conserved moments: dm0 = 0, and for j
+// the relaxation cancels against half the force, leaving dm3 = F_x, dm5 = F_y.  The sigma
+// term of Eq. 25 times (1 - s/2) reduces to 12 sigma s |F/psi|^2 (tau - 1/2 = (1 - s/2)/s).
+template <typename T, typename R>
+__device__ __forceinline__ void collide_t(T (&h)[Q], T drho, T rho, T psi_c, T fpx, T fpy,
+                                          const Phys<R>& p) {
+  typedef Num<T> N;
+  const T Fx = psi_c * fpx, Fy = psi_c * fpy;
+  const T d13 = h[1] - h[3], d24 = h[2] - h[4];
+  const T s13 = h[1] + h[3], s24 = h[2] + h[4];
+  const T s57 = h[5] + h[7], s68 = h[6] + h[8];
+  const T tx = (h[5] - h[6]) - (h[7] - h[8]);  // h5 - h6 - h7 + h8
+  const T ty = (h[5] + h[6]) - (h[7] + h[8]);  // h5 + h6 - h7 - h8
+  const T ir = N::rcp(rho);
+  const T ux = N::fma(N::k(0.5), Fx, d13 + tx) * ir;
+  const T uy = N::fma(N::k(0.5), Fy, d24 + ty) * ir;
+  const T sa = s13 + s24, sd = s57 + s68;
+  const T m1 = N::fma(N::k(-4), h[0], sd + (sd - sa));
+  const T m2 = N::fma(N::k(4), h[0], sd - (sa + sa));
+  const T m4 = N::fma(N::k(-2), d13, tx);
+  const T m6 = N::fma(N::k(-2), d24, ty);
+  const T m7 = s13 - s24;
+  const T m8 = s57 - s68;
+  const T rux = rho * ux, ruy = rho * uy;
+  const T ru2 = N::fma(rux, ux, ruy * uy);
+  const T e1 = N::fma(N::k(3), ru2, N::k(-2) * drho);
+  const T e2 = N::fma(N::k(-3), ru2, drho);
+  const T e7 = N::fma(rux, ux, N::k(0) - ruy * uy);
+  const T e8 = rux * uy;
+  const T vF = N::fma(ux, Fx, uy * Fy);
+  const T F2 = N::fma(fpx, fpx, fpy * fpy);
+  const T wxy = N::fma(ux, Fx, N::k(0) - uy * Fy), vxy = N::fma(ux, Fy, uy * Fx);
+  T k7s, k7v, k8s, k8v;
+  if (p.visc_mode == VISC_CONST) {
+    k7s = N::k(p.k7s);
+    k7v = N::k(p.k7v);
+    k8s = N::k(p.k8s);
+    k8v = N::k(p.k8v);
+  } else {
+    T tau;
+    if (p.visc_mode == VISC_STEP) {
+      tau = N::sel_ge(rho, p.rho_c, p.tau_l, p.tau_v);
+    } else {
+      const T fr = N::clamp01((rho - N::k(p.rho_v)) * N::k(p.inv_drho_lv));
+      tau = N::fma(fr, N::k(p.dtau), N::k(p.tau_v));
+    }
+    k7s = N::k(0.25) * N::rcp(tau);  // s_nu / 4 with s_nu = 1 / tau (Eq. 10)
+    k7v = N::k(0.5) - k7s;           // (1 - s_nu / 2) / 2
+    k8s = k7s;
+    k8v = N::k(0.5) * k7v;
+  }
+  const T a1 = N::fma(N::k(-p.k1s), m1 - e1, N::fma(N::k(p.k1v), vF, N::k(p.k1f) * F2));
+  const T a2 = N::fma(N::k(-p.k2s), m2 - e2, N::fma(N::k(-p.k2v), vF, N::k(-p.k2f) * F2));
+  const T a3 = N::k(1.0 / 6.0) * Fx, a5 = N::k(1.0 / 6.0) * Fy;
+  const T a4 = N::fma(N::k(-p.k4s), m4 + rux, N::k(-p.k4f) * Fx);
+  const T a6 = N::fma(N::k(-p.k6s), m6 + ruy, N::k(-p.k6f) * Fy);
+  const T a7 = N::fma(N::k(0) - k7s, m7 - e7, k7v * wxy);
+  const T a8 = N::fma(N::k(0) - k8s, m8 - e8, k8v * vxy);
+  const T A = N::fma(N::k(-2), a2, N::k(0) - a1), B = N::fma(N::k(2), a1, a2);
+  const T Px = N::fma(N::k(-2), a4, a3), Py = N::fma(N::k(-2), a6, a5);
+  const T X = a3 + a4, Y = a5 + a6;
+  const T XpY = X + Y, XmY = X - Y;
+  const T Ap = A + a7, Am = A - a7, Bp = B + a8, Bm = B - a8;
+  h[0] = N::fma(N::k(4), a2 - a1, h[0]);
+  h[1] = h[1] + (Ap + Px);
+  h[3] = h[3] + (Ap - Px);
+  h[2] = h[2] + (Am + Py);
+  h[4] = h[4] + (Am - Py);
+  h[5] = h[5] + (Bp + XpY);
+  h[7] = h[7] + (Bp - XpY);
+  h[6] = h[6] + (Bm - XmY);
+  h[8] = h[8] + (Bm + XmY);
 }
 
-// Shared-memory layout of the sweep kernel (dynamic), in bytes.
+// Force of Eq. 7 divided by psi(x) from the 3x3 psi stencil (c centre, n north = y + 1,
+// s south = y - 1; E, W = x +- 1), with g1 = -G/3 and g2 = -G/12.
+template <typename T, typename R>
+__device__ __forceinline__ void force_t(T pE, T pW, T pN, T pS, T pNE, T pNW, T pSE, T pSW,
+                                        const Phys<R>& p, T& fpx, T& fpy) {
+  typedef Num<T> N;
+  fpx = N::fma(N::k(p.g1), pE - pW, N::k(p.g2) * ((pNE - pNW) + (pSE - pSW)));
+  fpy = N::fma(N::k(p.g1), pN - pS, N::k(p.g2) * ((pNE + pNW) - (pSE + pSW)));
+}
+
+// Bulk asynchronous store shared -> global and its completion tracking.
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_addr(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// Configuration and shared-memory layout (dynamic, bytes) of one sweep instantiation.
+// Thread t handles CTA column c = t - 2: threads 1 and NT-2 evaluate psi of the halo
+// columns -1 and WO, threads 2 .. NT-3 own the WO = NT - 4 columns of the strip, thread 0
+// issues the bulk copies.
 template <typename S, int NT>
-struct SweepSmem {
-  static constexpr int SEG = NT + 2 * SEG_HALO;                    // columns per ring row
-  static constexpr size_t BARS = 128;                              // NSLOT mbarriers
+struct SweepCfg {
+  static constexpr int WO = NT - 4;          // owned columns per CTA (a multiple of 4)
+  static constexpr int SEG = NT + 4;         // ring row: columns x0-4 .. x0+WO+3
+  static constexpr int NSLOT = 8;            // ring rows (NSLOT - 3 rows in flight)
+  static constexpr size_t BARS = 128;        // mbarriers
   static constexpr size_t POP = (size_t)NSLOT * Q * SEG * sizeof(S);
-  static constexpr size_t PSI = (size_t)PSI_ROWS * (NT + 2) * sizeof(S);
-  static constexpr size_t BYTES = BARS + POP + PSI;
+  static constexpr size_t PSI = (size_t)PSI_ROWS * NT * sizeof(S);
+  static constexpr size_t OUT = (size_t)2 * Q * NT * sizeof(S);  // two staged output rows
+  static constexpr size_t BYTES = BARS + POP + PSI + OUT;
+};
+
+// FP32 instantiations are held to 128 registers per thread so that enough CTAs stay
+// resident; FP64 (a correctness mode) is left unconstrained.
+template <typename S, int NT>
+struct MinBlocks {
+  static constexpr int value = sizeof(S) == 4 ? (65536 / (NT * 128)) : 1;
 };
 
 // ---------------------------------------------------------------------------------------
-// The fused sweep kernel.  One CTA per work item, NT threads, thread t owns column x0 + t.
-// Threads 0 and 1 also evaluate psi of the halo columns x0 - 1 and x0 + NT.
+// The fused sweep kernel.  One CTA per work item (a strip of WO columns and a chunk of
+// rows).  MODE_STEP writes the post-collision populations (staged in shared memory, one
+// bulk store per plane and row); MODE_MOMENTS writes rho, v and/or reduces diagnostics.
 template <typename S, int NT, int MODE>
-__global__ void __launch_bounds__(NT) sweep_kernel(const S* __restrict__ fin,
-                                                   S* __restrict__ fout,
-                                                   const InstParams* __restrict__ insts,
-                                                   const WorkItem* __restrict__ items,
-                                                   int n_items, MomArgs<S> mo,
-                                                   int* __restrict__ status) {
+__global__ void __launch_bounds__(NT, MinBlocks<S, NT>::value) sweep_kernel(
+    const S* __restrict__ fin, S* __restrict__ fout, const InstParams* __restrict__ insts,
+    const WorkItem* __restrict__ items, int n_items, MomArgs<S> mo, int* __restrict__ status) {
   typedef S R;  // arithmetic type follows the storage type
-  typedef SweepSmem<S, NT> L;
-  constexpr int SEG = L::SEG;
+  typedef SweepCfg<S, NT> C;
+  constexpr int WO = C::WO, SEG = C::SEG, NS = C::NSLOT;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
-  S* ring = reinterpret_cast<S*>(smem_raw + L::BARS);
-  R* psis = reinterpret_cast<R*>(smem_raw + L::BARS + L::POP);
+  S* ring = reinterpret_cast<S*>(smem_raw + C::BARS);
+  R* psis = reinterpret_cast<R*>(smem_raw + C::BARS + C::POP);
+  S* outs = reinterpret_cast<S*>(smem_raw + C::BARS + C::POP + C::PSI);
   __shared__ int s_abort;
   __shared__ double red_d[NT / 32][3];
   __shared__ float red_f[NT / 32][2];
@@ -337,220 +459,554 @@ __global__ void __launch_bounds__(NT) sweep_kernel(const S* __restrict__ fin,
   const Phys<R> ph = load_phys<R>(P);
   const int tid = threadIdx.x;
   const int lane = tid & 31;
+  const bool issuer = tid == 0;
   const int nx = P.nx, ny = P.ny, pitch = P.pitch, walls = P.walls;
   const long long plane = P.plane;
   const int x0 = it.x0;
-  const int x = x0 + tid;
-  const int xend = min(x0 + NT, nx);
-  const bool owner = x < xend;
+  const int c = tid - 2;                  // CTA column of this thread
+  const int x = x0 + c;                   // its global column
+  const int xend = min(x0 + WO, nx);
+  const bool psi_thread = tid >= 1 && tid <= NT - 2;
+  const bool owner = c >= 0 && c < WO && x < xend;
+  const int n_bulk = ((xend - x0) / 4) * 4;  // columns written by the bulk store
   const int dir = it.dir < 0 ? -1 : 1;
   const int y0 = it.y0, y1 = it.y1;
-  const int nload = y1 - y0 + 4;              // population rows y0-2 .. y1+1
+  const int nload = y1 - y0 + 4;          // population rows y0-2 .. y1+1
   const int rstart = dir > 0 ? y0 - 2 : y1 + 1;
-  const int seg0 = GHOST + x0 - SEG_HALO;     // storage column of the ring's column 0
-  const int len = min(SEG, pitch - seg0);     // elements per copied plane-row
+  const int seg0 = GHOST + x0 - SEG_HALO; // storage column of ring column 0
+  const int len = min(SEG, pitch - seg0); // elements per copied plane-row
   const uint32_t plane_bytes = (uint32_t)len * (uint32_t)sizeof(S);
   const S* gsrc = fin + P.off + seg0;
 
-  // Physical row held by ring row j (walls: clamped, so every slot is filled uniformly;
-  // the clamped copies are never pulled from because bounce-back replaces those reads).
-  auto phys_load_row = [&](int j) -> int {
-    const int r = rstart + j * dir;
-    if (walls) return r < 0 ? 0 : (r >= ny ? ny - 1 : r);
-    return wrapi(r, ny);
-  };
+  // Ring row j holds physical row rstart + j*dir (walls: clamped, so every slot is filled
+  // the same way; those clamped copies are never read because bounce-back replaces them).
   auto issue_row = [&](int j) {
-    const int slot = j & (NSLOT - 1);
-    const S* src = gsrc + (long long)phys_load_row(j) * pitch;
+    const int slot = j % NS;
+    const int r = rstart + j * dir;
+    const int rp = walls ? (r < 0 ? 0 : (r >= ny ? ny - 1 : r)) : wrapi(r, ny);
+    const S* src = gsrc + (long long)rp * pitch;
     mbar_arrive_expect_tx(&bars[slot], plane_bytes * Q);
 #pragma unroll
     for (int q = 0; q < Q; ++q)
       bulk_g2s(ring + ((size_t)slot * Q + q) * SEG, src + (long long)q * plane, plane_bytes,
                &bars[slot]);
   };
+  // Bulk store of the staged output row of centre row yc (out slot k).
+  auto store_row = [&](int k, int yc) {
+    if (n_bulk <= 0) return;
+    S* dst = fout + P.off + (long long)yc * pitch + GHOST + x0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+      bulk_s2g(dst + (long long)q * plane, outs + ((size_t)k * Q + q) * NT,
+               (uint32_t)(n_bulk * sizeof(S)));
+    bulk_commit();
+  };
 
-  if (tid == 0) {
+  int issued = 0;  // rows issued (meaningful in the issuing thread)
+  if (issuer) {
     s_abort = 0;
-    for (int k = 0; k < NSLOT; ++k) mbar_init(&bars[k], 1);
+    for (int k = 0; k < NS; ++k) mbar_init(&bars[k], 1);
     mbar_fence_init();
   }
   __syncthreads();
-  int issued = 0;  // meaningful in thread 0 only
-  if (tid == 0) {
-    const int n0 = min(nload, NSLOT);
+  if (issuer) {
+    const int n0 = min(nload, NS);
     for (int j = 0; j < n0; ++j) issue_row(j);
     issued = n0;
   }
 
   S cur[Q], nxt[Q];
-  R cur_drho = 0, cur_rho = 1;
+  R cur_rho = 1, cur_dr = 0;
   bool flag_bad = false;
   double acc_m = 0.0, acc_x = 0.0, acc_y = 0.0;
   float mx_u = 0.f, mx_d = 0.f;
   int bad = 0;
-  int waited = 0;  // ring rows waited for so far (all threads)
-
-  for (int s = 1; s <= nload - 2; ++s) {
-    // Refill the slot freed by row s-2 (all threads left it at the previous barrier).
-    if (tid == 0 && s >= 2 && issued < nload) {
-      fence_proxy_async_smem();
-      issue_row(issued);
-      ++issued;
+  int waited = 0;  // ring rows waited for so far (same in every thread)
+  const int last = nload - 2;
+  int s = 1;
+  for (; s <= last; ++s) {
+    if (issuer) {
+      if (s >= 2 && issued < nload) {
+        fence_proxy_async_smem();  // our reads of the freed slot precede the new copy
+        issue_row(issued);
+        ++issued;
+      }
+      if (MODE == MODE_STEP) bulk_wait_read_all();  // the staged row about to be reused
     }
-    // Rows s-1, s, s+1 must be resident.
-    while (waited <= s + 1) {
-      if (!mbar_wait_bounded(&bars[waited & (NSLOT - 1)], (uint32_t)((waited / NSLOT) & 1)))
-        s_abort = 1;
+    while (waited <= s + 1) {  // rows s-1, s, s+1 must be resident
+      if (!mbar_wait_bounded(&bars[waited % NS], (uint32_t)((waited / NS) & 1))) s_abort = 1;
       ++waited;
     }
-    const int rpsi = rstart + s * dir;  // psi row of this iteration
+    const int rpsi = rstart + s * dir;
     const bool ghost = walls && (rpsi < 0 || rpsi >= ny);
-    R* ps_now = psis + (s & (PSI_ROWS - 1)) * (NT + 2);
-    R nrho = 1, ndrho = 0;
+    R* ps_now = psis + (s & (PSI_ROWS - 1)) * NT;
+    R nrho = 1, ndr = 0;
     if (!ghost) {
-      const int rp = walls ? rpsi : wrapi(rpsi, ny);
-      const bool bb_low = walls && rp == 0;          // e_y = +1 would come from row -1
-      const bool bb_high = walls && rp == ny - 1;    // e_y = -1 would come from row ny
-      // Pull for columns c (CTA-relative): own column, and the halo columns for t < 2.
-      auto pull = [&](int c, S (&v)[Q]) {
+      if (psi_thread) {
+        const bool bb_low = walls && rpsi == 0;        // e_y = +1 would come from row -1
+        const bool bb_high = walls && rpsi == ny - 1;  // e_y = -1 would come from row ny
+        const int j0 = s % NS, js = (s - dir) % NS, jn = (s + dir) % NS;
+        const S* rowC = ring + (size_t)j0 * Q * SEG + SEG_HALO + c;
+        const S* rowS = ring + (size_t)js * Q * SEG + SEG_HALO + c;  // row y - 1
+        const S* rowN = ring + (size_t)jn * Q * SEG + SEG_HALO + c;  // row y + 1
+        if (!(bb_low || bb_high)) {
 #pragma unroll
-        for (int q = 0; q < Q; ++q) {
-          const int eyq = ey_of(q), exq = ex_of(q);
-          const bool bb = (eyq > 0 && bb_low) || (eyq < 0 && bb_high);
-          const int j = bb ? s : s - eyq * dir;
-          const int qs = bb ? opp_of(q) : q;
-          const int col = SEG_HALO + c - (bb ? 0 : exq);
-          v[q] = ring[((size_t)(j & (NSLOT - 1)) * Q + qs) * SEG + col];
+          for (int q = 0; q < Q; ++q) {
+            const int eyq = ey_of(q);
+            nxt[q] = (eyq > 0 ? rowS : (eyq < 0 ? rowN : rowC))[q * SEG - ex_of(q)];
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < Q; ++q) {
+            const int eyq = ey_of(q);
+            const bool bb = (eyq > 0 && bb_low) || (eyq < 0 && bb_high);
+            nxt[q] = bb ? rowC[opp_of(q) * SEG]
+                        : (eyq > 0 ? rowS : (eyq < 0 ? rowN : rowC))[q * SEG - ex_of(q)];
+          }
         }
-      };
-      auto density = [&](const S (&v)[Q], R& d) {
-        d = ((R)v[0] + ((R)v[1] + (R)v[3])) +
-            (((R)v[2] + (R)v[4]) + (((R)v[5] + (R)v[7]) + ((R)v[6] + (R)v[8])));
-        return ph.rho_ref + d;
-      };
-      pull(tid, nxt);
-      nrho = density(nxt, ndrho);
-      ps_now[1 + tid] = psi_of<R>(nrho, ph);
-      if (tid < 2) {
-        S hv[Q];
-        const int c = tid == 0 ? -1 : NT;
-        pull(c, hv);
-        R hd;
-        ps_now[1 + c] = psi_of<R>(density(hv, hd), ph);
-      }
-      if (walls && s == 2) {
-        // The first psi row of a sweep that starts at a wall is the ghost row: it mirrors
-        // the row just computed.
-        const int rfirst = rstart + dir;
-        if (rfirst < 0 || rfirst >= ny) {
-          R* ps_g = psis + (1 & (PSI_ROWS - 1)) * (NT + 2);
-          ps_g[1 + tid] = ps_now[1 + tid];
-          if (tid < 2) ps_g[tid == 0 ? 0 : NT + 1] = ps_now[tid == 0 ? 0 : NT + 1];
+        ndr = ((R)nxt[0] + ((R)nxt[1] + (R)nxt[3])) +
+              (((R)nxt[2] + (R)nxt[4]) + (((R)nxt[5] + (R)nxt[7]) + ((R)nxt[6] + (R)nxt[8])));
+        nrho = ph.rho_ref + ndr;
+        ps_now[tid] = psi_t<R, R>(nrho, ph);
+        if (walls && s == 2) {
+          // A sweep that starts at a wall begins with the ghost row: it mirrors this row.
+          const int rfirst = rstart + dir;
+          if (rfirst < 0 || rfirst >= ny) psis[(1 & (PSI_ROWS - 1)) * NT + tid] = ps_now[tid];
         }
       }
-    } else if (s > 1) {
+    } else if (s > 1 && psi_thread) {
       // Ghost row at the end of a sweep: mirror the previous (wall) row.
-      const R* ps_prev = psis + ((s - 1) & (PSI_ROWS - 1)) * (NT + 2);
-      ps_now[1 + tid] = ps_prev[1 + tid];
-      if (tid < 2) ps_now[tid == 0 ? 0 : NT + 1] = ps_prev[tid == 0 ? 0 : NT + 1];
+      ps_now[tid] = psis[((s - 1) & (PSI_ROWS - 1)) * NT + tid];
     }
     __syncthreads();
     if (s_abort) break;
+    if (MODE == MODE_STEP && issuer && s >= 4)
+      store_row((s - 1) & 1, rstart + (s - 2) * dir);  // staged in the previous iteration
 
-    if (s >= 3) {
-      // Centre row rc = rstart + (s-1) dir; psi rows rc - dir and rc + dir around it.
+    if (s >= 3 && owner) {
+      // Collision of the centre row yc = rstart + (s-1) dir.
       const int yc = rstart + (s - 1) * dir;
-      const R* ps_c = psis + ((s - 1) & (PSI_ROWS - 1)) * (NT + 2);
-      const R* ps_a = psis + ((s - 2) & (PSI_ROWS - 1)) * (NT + 2);  // row yc - dir
-      const R* ps_b = ps_now;                                         // row yc + dir
-      const R* ps_n = dir > 0 ? ps_b : ps_a;  // north (y + 1)
-      const R* ps_s = dir > 0 ? ps_a : ps_b;  // south (y - 1)
-      if (owner) {
-        const int c = 1 + tid;
-        const R pE = ps_c[c + 1], pW = ps_c[c - 1];
-        const R pN = ps_n[c], pS = ps_s[c];
-        const R pNE = ps_n[c + 1], pNW = ps_n[c - 1];
-        const R pSW = ps_s[c - 1], pSE = ps_s[c + 1];
-        const R w1 = (R)(1.0 / 3.0), w2 = (R)(1.0 / 12.0);
-        const R fpx = -ph.G * (w1 * (pE - pW) + w2 * ((pNE - pNW) + (pSE - pSW)));
-        const R fpy = -ph.G * (w1 * (pN - pS) + w2 * ((pNE + pNW) - (pSE + pSW)));
-        const R pc = ps_c[c];
-        R h[Q];
+      const R* pa = psis + ((s - 2) & (PSI_ROWS - 1)) * NT + tid;  // row yc - dir
+      const R* pc = psis + ((s - 1) & (PSI_ROWS - 1)) * NT + tid;  // row yc
+      const R* pb = ps_now + tid;                                   // row yc + dir
+      const R* pn = dir > 0 ? pb : pa;   // north (y + 1)
+      const R* pso = dir > 0 ? pa : pb;  // south (y - 1)
+      const R pE = pc[1], pW = pc[-1], pN = pn[0], pS = pso[0];
+      const R pNE = pn[1], pNW = pn[-1], pSW = pso[-1], pSE = pso[1];
+      R fpx, fpy;
+      force_t<R, R>(pE, pW, pN, pS, pNE, pNW, pSE, pSW, ph, fpx, fpy);
+      R h[Q];
 #pragma unroll
-        for (int q = 0; q < Q; ++q) h[q] = (R)cur[q];
-        if (MODE == MODE_STEP) {
-          collide_node<R>(h, cur_drho, cur_rho, pc, fpx, fpy, ph);
-          if (!(cur_rho > (R)0) || !isfinite(cur_rho)) flag_bad = true;
+      for (int q = 0; q < Q; ++q) h[q] = (R)cur[q];
+      if (MODE == MODE_STEP) {
+        collide_t<R, R>(h, cur_dr, cur_rho, pc[0], fpx, fpy, ph);
+        flag_bad |= !(cur_rho > (R)0 && cur_rho < (R)INFINITY);
+        S* ost = outs + (size_t)(s & 1) * Q * NT + c;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) ost[q * NT] = (S)h[q];
+        fence_proxy_async_smem();  // the staged values are read by a bulk store
+        if (c >= n_bulk || x < 2 || x >= nx - 2) {
+          // Columns past the last full group of four, and the ghost copies -2, -1, nx,
+          // nx+1 of the columns they mirror, are written directly.
           S* dst = fout + P.off + (long long)yc * pitch + GHOST;
+          if (c >= n_bulk) {
 #pragma unroll
-          for (int q = 0; q < Q; ++q) dst[(long long)q * plane + x] = (S)h[q];
+            for (int q = 0; q < Q; ++q) dst[(long long)q * plane + x] = (S)h[q];
+          }
+          auto put = [&](int g) {
+            if (wrapi(g, nx) == x) {
+#pragma unroll
+              for (int q = 0; q < Q; ++q) dst[(long long)q * plane + g] = (S)h[q];
+            }
+          };
           if (x < 2 || x >= nx - 2) {
-            // Keep the ghost columns -2, -1, nx, nx+1 equal to the columns they mirror.
-            auto put = [&](int g) {
-              if (wrapi(g, nx) == x) {
-#pragma unroll
-                for (int q = 0; q < Q; ++q) dst[(long long)q * plane + g] = (S)h[q];
-              }
-            };
             put(-2);
             put(-1);
             put(nx);
             put(nx + 1);
           }
-        } else {
-          const R Fx = pc * fpx, Fy = pc * fpy;
-          const R jx = (h[1] - h[3]) + ((h[5] - h[6]) - (h[7] - h[8]));
-          const R jy = (h[2] - h[4]) + ((h[5] + h[6]) - (h[7] + h[8]));
-          const R px = jx + (R)0.5 * Fx, py = jy + (R)0.5 * Fy;
-          const R ir = (R)1 / cur_rho;
-          const R ux = px * ir, uy = py * ir;
-          const long long di = P.dense_off + (long long)yc * nx + x;
-          if (mo.flags & MOM_FIELDS) {
-            if (mo.rho) mo.rho[di] = (S)cur_rho;
-            if (mo.ux) mo.ux[di] = (S)ux;
-            if (mo.uy) mo.uy[di] = (S)uy;
-          }
-          if (mo.flags & MOM_DIAG) {
-            const bool ok = isfinite(cur_rho) && isfinite(ux) && isfinite(uy);
-            if (!ok) {
-              ++bad;
-            } else {
-              acc_m += (double)cur_rho;
-              acc_x += (double)px;
-              acc_y += (double)py;
-              mx_u = fmaxf(mx_u, (float)sqrt((double)ux * ux + (double)uy * uy));
-              if (mo.rho_prev)
-                mx_d = fmaxf(mx_d, (float)fabs((double)cur_rho - (double)mo.rho_prev[di]));
-            }
-          }
-          if ((mo.flags & MOM_UPDATE_PREV) && mo.rho_prev) mo.rho_prev[di] = (S)cur_rho;
         }
+      } else {
+        const R Fx = pc[0] * fpx, Fy = pc[0] * fpy;
+        const R jx = (h[1] - h[3]) + ((h[5] - h[6]) - (h[7] - h[8]));
+        const R jy = (h[2] - h[4]) + ((h[5] + h[6]) - (h[7] + h[8]));
+        const R px = jx + (R)0.5 * Fx, py = jy + (R)0.5 * Fy;
+        const R ir = (R)1 / cur_rho;
+        const R ux = px * ir, uy = py * ir;
+        const long long di = P.dense_off + (long long)yc * nx + x;
+        if (mo.flags & MOM_FIELDS) {
+          if (mo.rho) mo.rho[di] = (S)cur_rho;
+          if (mo.ux) mo.ux[di] = (S)ux;
+          if (mo.uy) mo.uy[di] = (S)uy;
+        }
+        if (mo.flags & MOM_DIAG) {
+          if (!(isfinite(cur_rho) && isfinite(ux) && isfinite(uy))) {
+            ++bad;
+          } else {
+            acc_m += (double)cur_rho;
+            acc_x += (double)px;
+            acc_y += (double)py;
+            mx_u = fmaxf(mx_u, (float)sqrt((double)ux * ux + (double)uy * uy));
+            if (mo.rho_prev)
+              mx_d = fmaxf(mx_d, (float)fabs((double)cur_rho - (double)mo.rho_prev[di]));
+          }
+        }
+        if ((mo.flags & MOM_UPDATE_PREV) && mo.rho_prev) mo.rho_prev[di] = (S)cur_rho;
       }
     }
 #pragma unroll
     for (int q = 0; q < Q; ++q) cur[q] = nxt[q];
-    cur_drho = ndrho;
     cur_rho = nrho;
+    cur_dr = ndr;
   }
 
-  if (s_abort) {
-    // A copy did not complete in time: wait (bounded) for the copies still in flight so
-    // no write lands in shared memory after this CTA has exited, then report.
-    if (tid == 0) {
-      // The newest row issued into each slot: once its phase completed, every earlier
-      // copy into that slot has too.
-      for (int k = 0; k < NSLOT && k < issued; ++k) {
-        const int j = issued - 1 - ((issued - 1 - k) & (NSLOT - 1));
-        mbar_wait_bounded(&bars[k], (uint32_t)((j / NSLOT) & 1));
+  if (s <= last) {
+    // A copy did not complete in time: wait (bounded) for the loads still in flight and
+    // for the stores, so nothing touches shared memory after this CTA has exited.
+    if (issuer) {
+      for (int k = 0; k < NS && k < issued; ++k) {
+        const int j = issued - 1 - ((issued - 1 - k) % NS);
+        mbar_wait_bounded(&bars[k], (uint32_t)((j / NS) & 1));
       }
+      if (MODE == MODE_STEP) bulk_wait_all();
       atomicOr(status, STATUS_TIMEOUT);
     }
     return;
   }
   if (MODE == MODE_STEP) {
+    __syncthreads();  // the last staged row is complete
+    if (issuer) {
+      if (last >= 3) store_row(last & 1, rstart + (last - 1) * dir);
+      bulk_wait_all();
+    }
     if (flag_bad) atomicOr(status, STATUS_NONFINITE);
   } else if (mo.flags & MOM_DIAG) {
     // Block reduction: warp shuffles, then one value per warp through shared memory.
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc_m += __shfl_down_sync(0xffffffffu, acc_m, o);
+      acc_x += __shfl_down_sync(0xffffffffu, acc_x, o);
+      acc_y += __shfl_down_sync(0xffffffffu, acc_y, o);
+      mx_u = fmaxf(mx_u, __shfl_down_sync(0xffffffffu, mx_u, o));
+      mx_d = fmaxf(mx_d, __shfl_down_sync(0xffffffffu, mx_d, o));
+      bad += __shfl_down_sync(0xffffffffu, bad, o);
+    }
+    const int wid = tid >> 5;
+    if (lane == 0) {
+      red_d[wid][0] = acc_m;
+      red_d[wid][1] = acc_x;
+      red_d[wid][2] = acc_y;
+      red_f[wid][0] = mx_u;
+      red_f[wid][1] = mx_d;
+      red_i[wid] = bad;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double s0 = 0, s1 = 0, s2 = 0;
+      float f0 = 0.f, f1 = 0.f;
+      int b = 0;
+      for (int w = 0; w < NT / 32; ++w) {
+        s0 += red_d[w][0];
+        s1 += red_d[w][1];
+        s2 += red_d[w][2];
+        f0 = fmaxf(f0, red_f[w][0]);
+        f1 = fmaxf(f1, red_f[w][1]);
+        b += red_i[w];
+      }
+      mo.part_sum[3 * blockIdx.x + 0] = s0;
+      mo.part_sum[3 * blockIdx.x + 1] = s1;
+      mo.part_sum[3 * blockIdx.x + 2] = s2;
+      mo.part_max[2 * blockIdx.x + 0] = f0;
+      mo.part_max[2 * blockIdx.x + 1] = f1;
+      mo.part_bad[blockIdx.x] = b;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// FP32 pair kernel: thread t handles the two adjacent CTA columns c0 = 2t - 2 and c0 + 1
+// and does their arithmetic with packed float2 instructions.  Threads 1 .. NT-2 own the
+// WO = 2 NT - 4 columns of the strip; threads 0 and NT-1 evaluate psi of the halo
+// columns -1 and WO (their other column is unused); thread 0 issues the bulk copies.
+template <int NT>
+struct Sweep2Cfg {
+  static constexpr int WO = 2 * NT - 4;      // owned columns per CTA (a multiple of 4)
+  static constexpr int SEG = WO + 8;         // ring row: columns x0-4 .. x0+WO+3
+  static constexpr int NSLOT = 6;            // ring rows (NSLOT - 3 rows in flight)
+  static constexpr int PSW = 2 * NT;         // psi ring row: CTA columns -2 .. WO+1
+  static constexpr size_t BARS = 128;
+  static constexpr size_t POP = (size_t)NSLOT * Q * SEG * sizeof(float);
+  static constexpr size_t PSI = (size_t)PSI_ROWS * PSW * sizeof(float);
+  static constexpr size_t OUT = (size_t)2 * Q * PSW * sizeof(float);
+  static constexpr size_t BYTES = BARS + POP + PSI + OUT;
+};
+
+template <int NT, int MODE>
+__global__ void __launch_bounds__(NT, 65536 / (NT * 128)) sweep2_kernel(
+    const float* __restrict__ fin, float* __restrict__ fout, const InstParams* __restrict__ insts,
+    const WorkItem* __restrict__ items, int n_items, MomArgs<float> mo,
+    int* __restrict__ status) {
+  typedef Sweep2Cfg<NT> C;
+  typedef Num<float2> N;
+  constexpr int WO = C::WO, SEG = C::SEG, NS = C::NSLOT, PSW = C::PSW;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+  float* ring = reinterpret_cast<float*>(smem_raw + C::BARS);
+  float* psis = reinterpret_cast<float*>(smem_raw + C::BARS + C::POP);
+  float* outs = reinterpret_cast<float*>(smem_raw + C::BARS + C::POP + C::PSI);
+  __shared__ int s_abort;
+  __shared__ double red_d[NT / 32][3];
+  __shared__ float red_f[NT / 32][2];
+  __shared__ int red_i[NT / 32];
+
+  if ((int)blockIdx.x >= n_items) return;
+  const WorkItem it = items[blockIdx.x];
+  const InstParams& P = insts[it.inst];
+  const Phys<float> ph = load_phys<float>(P);
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const bool issuer = tid == 0;
+  const int nx = P.nx, ny = P.ny, pitch = P.pitch, walls = P.walls;
+  const long long plane = P.plane;
+  const int x0 = it.x0;
+  const int c0 = 2 * tid - 2;             // first CTA column of this thread
+  const int xa = x0 + c0;                 // its global column (xa, xa + 1)
+  const int xend = min(x0 + WO, nx);
+  const bool owner = tid >= 1 && tid <= NT - 2 && xa < xend;
+  const int n_bulk = ((xend - x0) / 4) * 4;  // columns written by the bulk store
+  const int dir = it.dir < 0 ? -1 : 1;
+  const int y0 = it.y0, y1 = it.y1;
+  const int nload = y1 - y0 + 4;
+  const int rstart = dir > 0 ? y0 - 2 : y1 + 1;
+  const int seg0 = GHOST + x0 - SEG_HALO;
+  const int len = min(SEG, pitch - seg0);
+  const uint32_t plane_bytes = (uint32_t)len * (uint32_t)sizeof(float);
+  const float* gsrc = fin + P.off + seg0;
+  const float2 rho_ref2 = N::k(ph.rho_ref);
+
+  auto issue_row = [&](int j) {
+    const int slot = j % NS;
+    const int r = rstart + j * dir;
+    const int rp = walls ? (r < 0 ? 0 : (r >= ny ? ny - 1 : r)) : wrapi(r, ny);
+    const float* src = gsrc + (long long)rp * pitch;
+    mbar_arrive_expect_tx(&bars[slot], plane_bytes * Q);
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+      bulk_g2s(ring + ((size_t)slot * Q + q) * SEG, src + (long long)q * plane, plane_bytes,
+               &bars[slot]);
+  };
+  auto store_row = [&](int k, int yc) {
+    if (n_bulk <= 0) return;
+    float* dst = fout + P.off + (long long)yc * pitch + GHOST + x0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+      bulk_s2g(dst + (long long)q * plane, outs + ((size_t)k * Q + q) * PSW,
+               (uint32_t)(n_bulk * sizeof(float)));
+    bulk_commit();
+  };
+
+  int issued = 0;
+  if (issuer) {
+    s_abort = 0;
+    for (int k = 0; k < NS; ++k) mbar_init(&bars[k], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (issuer) {
+    const int n0 = min(nload, NS);
+    for (int j = 0; j < n0; ++j) issue_row(j);
+    issued = n0;
+  }
+
+  float2 cur[Q], nxt[Q];
+  float2 cur_rho = N::k(1.f), cur_dr = N::k(0.f);
+  bool flag_bad = false;
+  double acc_m = 0.0, acc_x = 0.0, acc_y = 0.0;
+  float mx_u = 0.f, mx_d = 0.f;
+  int bad = 0;
+  int waited = 0;
+  const int last = nload - 2;
+  int s = 1;
+  for (; s <= last; ++s) {
+    if (issuer) {
+      if (s >= 2 && issued < nload) {
+        fence_proxy_async_smem();
+        issue_row(issued);
+        ++issued;
+      }
+      if (MODE == MODE_STEP) bulk_wait_read_all();
+    }
+    while (waited <= s + 1) {
+      if (!mbar_wait_bounded(&bars[waited % NS], (uint32_t)((waited / NS) & 1))) s_abort = 1;
+      ++waited;
+    }
+    const int rpsi = rstart + s * dir;
+    const bool ghost = walls && (rpsi < 0 || rpsi >= ny);
+    float* ps_now = psis + (s & (PSI_ROWS - 1)) * PSW;
+    float2 nrho = N::k(1.f), ndr = N::k(0.f);
+    if (!ghost) {
+      const bool bb_low = walls && rpsi == 0;
+      const bool bb_high = walls && rpsi == ny - 1;
+      const float* rowC = ring + (size_t)(s % NS) * Q * SEG + SEG_HALO + c0;
+      const float* rowS = ring + (size_t)((s - dir) % NS) * Q * SEG + SEG_HALO + c0;
+      const float* rowN = ring + (size_t)((s + dir) % NS) * Q * SEG + SEG_HALO + c0;
+      auto pair_at = [&](const float* p) -> float2 {  // columns c0, c0+1 (8-byte aligned)
+        return *reinterpret_cast<const float2*>(p);
+      };
+      if (!(bb_low || bb_high)) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const int eyq = ey_of(q), exq = ex_of(q);
+          const float* src = (eyq > 0 ? rowS : (eyq < 0 ? rowN : rowC)) + q * SEG - exq;
+          nxt[q] = exq == 0 ? pair_at(src) : make_float2(src[0], src[1]);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+          const int eyq = ey_of(q), exq = ex_of(q);
+          const bool bb = (eyq > 0 && bb_low) || (eyq < 0 && bb_high);
+          if (bb) {
+            nxt[q] = pair_at(rowC + opp_of(q) * SEG);
+          } else {
+            const float* src = (eyq > 0 ? rowS : (eyq < 0 ? rowN : rowC)) + q * SEG - exq;
+            nxt[q] = exq == 0 ? pair_at(src) : make_float2(src[0], src[1]);
+          }
+        }
+      }
+      ndr = (nxt[0] + (nxt[1] + nxt[3])) + ((nxt[2] + nxt[4]) + ((nxt[5] + nxt[7]) + (nxt[6] + nxt[8])));
+      nrho = rho_ref2 + ndr;
+      *reinterpret_cast<float2*>(ps_now + 2 + c0) = psi_t<float2, float>(nrho, ph);
+      if (walls && s == 2) {
+        const int rfirst = rstart + dir;
+        if (rfirst < 0 || rfirst >= ny)
+          *reinterpret_cast<float2*>(psis + (1 & (PSI_ROWS - 1)) * PSW + 2 + c0) =
+              *reinterpret_cast<const float2*>(ps_now + 2 + c0);
+      }
+    } else if (s > 1) {
+      *reinterpret_cast<float2*>(ps_now + 2 + c0) =
+          *reinterpret_cast<const float2*>(psis + ((s - 1) & (PSI_ROWS - 1)) * PSW + 2 + c0);
+    }
+    __syncthreads();
+    if (s_abort) break;
+    if (MODE == MODE_STEP && issuer && s >= 4) store_row((s - 1) & 1, rstart + (s - 2) * dir);
+
+    if (s >= 3 && owner) {
+      const int yc = rstart + (s - 1) * dir;
+      const float* pa = psis + ((s - 2) & (PSI_ROWS - 1)) * PSW + 2 + c0;  // row yc - dir
+      const float* pc = psis + ((s - 1) & (PSI_ROWS - 1)) * PSW + 2 + c0;  // row yc
+      const float* pb = ps_now + 2 + c0;                                    // row yc + dir
+      const float* pn = dir > 0 ? pb : pa;
+      const float* pso = dir > 0 ? pa : pb;
+      // psi at columns c0-1 .. c0+2 of the three rows, as pairs for columns (c0, c0+1)
+      const float2 cC = *reinterpret_cast<const float2*>(pc);
+      const float2 cN = *reinterpret_cast<const float2*>(pn);
+      const float2 cS = *reinterpret_cast<const float2*>(pso);
+      const float cWm = pc[-1], cEp = pc[2], nWm = pn[-1], nEp = pn[2], sWm = pso[-1], sEp = pso[2];
+      const float2 pE = make_float2(cC.y, cEp), pW = make_float2(cWm, cC.x);
+      const float2 pNE = make_float2(cN.y, nEp), pNW = make_float2(nWm, cN.x);
+      const float2 pSE = make_float2(cS.y, sEp), pSW = make_float2(sWm, cS.x);
+      float2 fpx, fpy;
+      force_t<float2, float>(pE, pW, cN, cS, pNE, pNW, pSE, pSW, ph, fpx, fpy);
+      float2 h[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) h[q] = cur[q];
+      if (MODE == MODE_STEP) {
+        collide_t<float2, float>(h, cur_dr, cur_rho, cC, fpx, fpy, ph);
+        const bool ok0 = cur_rho.x > 0.f && cur_rho.x < INFINITY;
+        const bool ok1 = cur_rho.y > 0.f && cur_rho.y < INFINITY;
+        flag_bad |= !ok0 || (xa + 1 < xend && !ok1);
+        float* ost = outs + (size_t)(s & 1) * Q * PSW + c0;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) *reinterpret_cast<float2*>(ost + q * PSW) = h[q];
+        fence_proxy_async_smem();
+        if (c0 + 2 > n_bulk || xa < 2 || xa + 1 >= nx - 2) {
+          // Columns past the last full group of four, and the ghost copies -2, -1, nx,
+          // nx+1 of the columns they mirror, are written directly.
+          float* dst = fout + P.off + (long long)yc * pitch + GHOST;
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const int x = xa + k;
+            if (x >= xend) continue;
+            float v[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) v[q] = k == 0 ? h[q].x : h[q].y;
+            if (c0 + k >= n_bulk) {
+#pragma unroll
+              for (int q = 0; q < Q; ++q) dst[(long long)q * plane + x] = v[q];
+            }
+            if (x < 2 || x >= nx - 2) {
+              auto put = [&](int g) {
+                if (wrapi(g, nx) == x) {
+#pragma unroll
+                  for (int q = 0; q < Q; ++q) dst[(long long)q * plane + g] = v[q];
+                }
+              };
+              put(-2);
+              put(-1);
+              put(nx);
+              put(nx + 1);
+            }
+          }
+        }
+      } else {
+        const float2 Fx = cC * fpx, Fy = cC * fpy;
+        const float2 jx = (h[1] - h[3]) + ((h[5] - h[6]) - (h[7] - h[8]));
+        const float2 jy = (h[2] - h[4]) + ((h[5] + h[6]) - (h[7] + h[8]));
+        const float2 px = N::fma(N::k(0.5f), Fx, jx), py = N::fma(N::k(0.5f), Fy, jy);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int x = xa + k;
+          if (x >= xend) continue;
+          const float r = k == 0 ? cur_rho.x : cur_rho.y;
+          const float mx = k == 0 ? px.x : px.y, my = k == 0 ? py.x : py.y;
+          const float ux = mx / r, uy = my / r;
+          const long long di = P.dense_off + (long long)yc * nx + x;
+          if (mo.flags & MOM_FIELDS) {
+            if (mo.rho) mo.rho[di] = r;
+            if (mo.ux) mo.ux[di] = ux;
+            if (mo.uy) mo.uy[di] = uy;
+          }
+          if (mo.flags & MOM_DIAG) {
+            if (!(isfinite(r) && isfinite(ux) && isfinite(uy))) {
+              ++bad;
+            } else {
+              acc_m += (double)r;
+              acc_x += (double)mx;
+              acc_y += (double)my;
+              mx_u = fmaxf(mx_u, (float)sqrt((double)ux * ux + (double)uy * uy));
+              if (mo.rho_prev)
+                mx_d = fmaxf(mx_d, (float)fabs((double)r - (double)mo.rho_prev[di]));
+            }
+          }
+          if ((mo.flags & MOM_UPDATE_PREV) && mo.rho_prev) mo.rho_prev[di] = r;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) cur[q] = nxt[q];
+    cur_rho = nrho;
+    cur_dr = ndr;
+  }
+
+  if (s <= last) {
+    if (issuer) {
+      for (int k = 0; k < NS && k < issued; ++k) {
+        const int j = issued - 1 - ((issued - 1 - k) % NS);
+        mbar_wait_bounded(&bars[k], (uint32_t)((j / NS) & 1));
+      }
+      if (MODE == MODE_STEP) bulk_wait_all();
+      atomicOr(status, STATUS_TIMEOUT);
+    }
+    return;
+  }
+  if (MODE == MODE_STEP) {
+    __syncthreads();
+    if (issuer) {
+      if (last >= 3) store_row(last & 1, rstart + (last - 1) * dir);
+      bulk_wait_all();
+    }
+    if (flag_bad) atomicOr(status, STATUS_NONFINITE);
+  } else if (mo.flags & MOM_DIAG) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       acc_m += __shfl_down_sync(0xffffffffu, acc_m, o);

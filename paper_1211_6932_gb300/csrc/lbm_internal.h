@@ -7,9 +7,10 @@
 namespace lbm {
 
 // Launch the fused sweep (MODE_STEP) or the moments/diagnostics pass (MODE_MOMENTS) over
-// n_items work items; nt (threads = columns per CTA) selects the instantiation.
+// n_items work items; nt (threads per CTA) and vec (columns per thread) select the
+// instantiation.
 template <typename S>
-cudaError_t launch_sweep(int nt, int mode, const S* fin, S* fout, const InstParams* d_inst,
+cudaError_t launch_sweep(int nt, int vec, int mode, const S* fin, S* fout, const InstParams* d_inst,
                          const WorkItem* d_items, int n_items, const MomArgs<S>& mo,
                          int* d_status, cudaStream_t st);
 template <typename S>
@@ -30,11 +31,16 @@ cudaError_t launch_diag_finalize(const double* part_sum, const float* part_max,
 
 // Resident CTAs per SM of the step kernel instantiation (at least 1).
 template <typename S>
-int sweep_occupancy(int nt);
+int sweep_occupancy(int nt, int vec);
 
-// Whether a (storage type, threads per CTA) pair has a kernel.
-inline bool nt_supported(bool fp64, int nt) {
+// Whether a (storage type, threads per CTA, columns per thread) triple has a kernel.
+inline bool cfg_supported(bool fp64, int nt, int vec) {
+  if (vec == 2) return !fp64 && (nt == 64 || nt == 128);
+  if (vec != 1) return false;
   return nt == 64 || nt == 128 || (nt == 256 && !fp64);
 }
+
+// Columns owned by one CTA of a configuration.
+inline int strip_width(int nt, int vec) { return vec == 2 ? 2 * nt - 4 : nt - 4; }
 
 }  // namespace lbm

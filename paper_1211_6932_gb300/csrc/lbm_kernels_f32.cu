@@ -33,15 +33,15 @@ __global__ void diag_finalize_kernel(const double* __restrict__ part_sum,
 
 
 template <>
-cudaError_t launch_sweep<float>(int nt, int mode, const float* fin, float* fout,
+cudaError_t launch_sweep<float>(int nt, int vec, int mode, const float* fin, float* fout,
                              const InstParams* d_inst, const WorkItem* d_items, int n_items,
                              const MomArgs<float>& mo, int* d_status, cudaStream_t st) {
-  switch (nt) {
-    case 64: return launch_sweep_mode<float, 64>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
-    case 128: return launch_sweep_mode<float, 128>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
-    case 256: return launch_sweep_mode<float, 256>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
-    default: return cudaErrorInvalidValue;
-  }
+  if (nt == 64 && vec == 1) return launch_sweep_mode<float, 64>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
+  if (nt == 128 && vec == 1) return launch_sweep_mode<float, 128>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
+  if (nt == 256 && vec == 1) return launch_sweep_mode<float, 256>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
+  if (nt == 64 && vec == 2) return launch_sweep2_mode<64>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
+  if (nt == 128 && vec == 2) return launch_sweep2_mode<128>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_diag_finalize(const double* part_sum, const float* part_max,
@@ -53,13 +53,13 @@ cudaError_t launch_diag_finalize(const double* part_sum, const float* part_max,
 }
 
 template <>
-int sweep_occupancy<float>(int nt) {
-  switch (nt) {
-    case 64: return occupancy_nt<float, 64>();
-    case 128: return occupancy_nt<float, 128>();
-    case 256: return occupancy_nt<float, 256>();
-    default: return 1;
-  }
+int sweep_occupancy<float>(int nt, int vec) {
+  if (nt == 64 && vec == 1) return occupancy_cfg<float, 64>();
+  if (nt == 128 && vec == 1) return occupancy_cfg<float, 128>();
+  if (nt == 256 && vec == 1) return occupancy_cfg<float, 256>();
+  if (nt == 64 && vec == 2) return occupancy2_cfg<64>();
+  if (nt == 128 && vec == 2) return occupancy2_cfg<128>();
+  return 1;
 }
 
 }  // namespace lbm

@@ -4,23 +4,19 @@
 namespace lbm {
 
 template <>
-cudaError_t launch_sweep<double>(int nt, int mode, const double* fin, double* fout,
+cudaError_t launch_sweep<double>(int nt, int vec, int mode, const double* fin, double* fout,
                              const InstParams* d_inst, const WorkItem* d_items, int n_items,
                              const MomArgs<double>& mo, int* d_status, cudaStream_t st) {
-  switch (nt) {
-    case 64: return launch_sweep_mode<double, 64>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
-    case 128: return launch_sweep_mode<double, 128>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
-    default: return cudaErrorInvalidValue;
-  }
+  if (nt == 64 && vec == 1) return launch_sweep_mode<double, 64>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
+  if (nt == 128 && vec == 1) return launch_sweep_mode<double, 128>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
+  return cudaErrorInvalidValue;
 }
 
 template <>
-int sweep_occupancy<double>(int nt) {
-  switch (nt) {
-    case 64: return occupancy_nt<double, 64>();
-    case 128: return occupancy_nt<double, 128>();
-    default: return 1;
-  }
+int sweep_occupancy<double>(int nt, int vec) {
+  if (nt == 64 && vec == 1) return occupancy_cfg<double, 64>();
+  if (nt == 128 && vec == 1) return occupancy_cfg<double, 128>();
+  return 1;
 }
 
 }  // namespace lbm

@@ -6,10 +6,10 @@
 namespace lbm {
 
 template <typename S, int NT, int MODE>
-static cudaError_t launch_sweep_nt(const S* fin, S* fout, const InstParams* d_inst,
-                                   const WorkItem* d_items, int n_items, const MomArgs<S>& mo,
-                                   int* d_status, cudaStream_t st) {
-  constexpr size_t smem = SweepSmem<S, NT>::BYTES;
+static cudaError_t launch_sweep_cfg(const S* fin, S* fout, const InstParams* d_inst,
+                                    const WorkItem* d_items, int n_items, const MomArgs<S>& mo,
+                                    int* d_status, cudaStream_t st) {
+  constexpr size_t smem = SweepCfg<S, NT>::BYTES;
   static bool configured = false;  // one attribute call per instantiation and process
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel<S, NT, MODE>,
@@ -29,15 +29,58 @@ static cudaError_t launch_sweep_mode(int mode, const S* fin, S* fout, const Inst
                                      const WorkItem* d_items, int n_items,
                                      const MomArgs<S>& mo, int* d_status, cudaStream_t st) {
   if (mode == MODE_STEP)
-    return launch_sweep_nt<S, NT, MODE_STEP>(fin, fout, d_inst, d_items, n_items, mo,
-                                             d_status, st);
-  return launch_sweep_nt<S, NT, MODE_MOMENTS>(fin, fout, d_inst, d_items, n_items, mo,
+    return launch_sweep_cfg<S, NT, MODE_STEP>(fin, fout, d_inst, d_items, n_items, mo,
                                               d_status, st);
+  return launch_sweep_cfg<S, NT, MODE_MOMENTS>(fin, fout, d_inst, d_items, n_items, mo,
+                                               d_status, st);
+}
+
+// FP32 pair kernel (two columns per thread, packed float2 arithmetic).
+template <int NT, int MODE>
+static cudaError_t launch_sweep2_cfg(const float* fin, float* fout, const InstParams* d_inst,
+                                     const WorkItem* d_items, int n_items,
+                                     const MomArgs<float>& mo, int* d_status, cudaStream_t st) {
+  constexpr size_t smem = Sweep2Cfg<NT>::BYTES;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(sweep2_kernel<NT, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (n_items <= 0) return cudaSuccess;
+  sweep2_kernel<NT, MODE><<<n_items, NT, smem, st>>>(fin, fout, d_inst, d_items, n_items, mo,
+                                                     d_status);
+  return cudaGetLastError();
+}
+
+template <int NT>
+static cudaError_t launch_sweep2_mode(int mode, const float* fin, float* fout,
+                                      const InstParams* d_inst, const WorkItem* d_items,
+                                      int n_items, const MomArgs<float>& mo, int* d_status,
+                                      cudaStream_t st) {
+  if (mode == MODE_STEP)
+    return launch_sweep2_cfg<NT, MODE_STEP>(fin, fout, d_inst, d_items, n_items, mo, d_status,
+                                            st);
+  return launch_sweep2_cfg<NT, MODE_MOMENTS>(fin, fout, d_inst, d_items, n_items, mo,
+                                             d_status, st);
+}
+
+template <int NT>
+static int occupancy2_cfg() {
+  constexpr size_t smem = Sweep2Cfg<NT>::BYTES;
+  cudaFuncSetAttribute(sweep2_kernel<NT, MODE_STEP>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &occ, sweep2_kernel<NT, MODE_STEP>, NT, smem);
+  return (e == cudaSuccess && occ > 0) ? occ : 1;
 }
 
 template <typename S, int NT>
-static int occupancy_nt() {
-  constexpr size_t smem = SweepSmem<S, NT>::BYTES;
+static int occupancy_cfg() {
+  constexpr size_t smem = SweepCfg<S, NT>::BYTES;
   cudaFuncSetAttribute(sweep_kernel<S, NT, MODE_STEP>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int occ = 0;

@@ -82,7 +82,7 @@ class Lattice:
     def __init__(self, nx, ny, eos: Eos, G=-1.0, sigma=0.0, s=None, nu_l=0.0, nu_v=0.0,
                  precision="fp32", visc_mode=None, bc="periodic", psi_fp64=False,
                  rho_ref=None, rho_c=None, rho_l=None, rho_v=None, stream=None, tile_threads=0,
-                 tile_rows=0, device=None):
+                 tile_rows=0, device=None, tile_vec=0):
         self._L = C.lib()
         self.nx, self.ny = int(nx), int(ny)
         self.precision = precision
@@ -106,6 +106,7 @@ class Lattice:
         o.stream = sp.value if sp is not None else None
         o.device = _device_of(stream, device)
         o.tile_threads = int(tile_threads)
+        o.tile_vec = int(tile_vec)
         o.tile_rows = int(tile_rows)
         h = ctypes.c_void_p()
         rc = self._L.lbm_create(ctypes.byref(h), self.nx, self.ny, eos.c(), float(G),
@@ -212,13 +213,14 @@ class Lattice:
 
     @property
     def tiling(self):
-        """(threads per CTA, rows per CTA sweep) of the step kernel."""
-        v, r = ctypes.c_int(), ctypes.c_int()
-        self._check(self._L.lbm_get_tiling(self._h, ctypes.byref(v), ctypes.byref(r)))
-        return v.value, r.value
+        """(threads per CTA, columns per thread, rows per CTA sweep) of the step kernel."""
+        t, v, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self._L.lbm_get_tiling(self._h, ctypes.byref(t), ctypes.byref(v),
+                                           ctypes.byref(r)))
+        return t.value, v.value, r.value
 
-    def set_tiling(self, threads=0, rows=0):
-        self._check(self._L.lbm_set_tiling(self._h, int(threads), int(rows)))
+    def set_tiling(self, threads=0, vec=0, rows=0):
+        self._check(self._L.lbm_set_tiling(self._h, int(threads), int(vec), int(rows)))
 
     @property
     def stream(self):
@@ -262,7 +264,7 @@ class Batch:
     """Many independent lattices advanced by one launch per step (lbm_batch_*)."""
 
     def __init__(self, instances, precision="fp32", stream=None, tile_threads=0, tile_rows=0,
-                 device=None):
+                 device=None, tile_vec=0):
         self._L = C.lib()
         self.instances = list(instances)
         arr = (C.lbm_instance * len(self.instances))(*[i.c() for i in self.instances])
@@ -270,7 +272,7 @@ class Batch:
         sp = _stream_ptr(stream)
         rc = self._L.lbm_batch_create(ctypes.byref(h), len(self.instances), arr,
                                       _PREC[precision], sp, _device_of(stream, device),
-                                      int(tile_threads), int(tile_rows))
+                                      int(tile_threads), int(tile_vec), int(tile_rows))
         if rc != 0:
             raise LbmError(rc, self._L.lbm_batch_last_error(None).decode())
         self._h = h
