@@ -27,7 +27,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-NX = NY = 4096
+NX = NY = 4096  # default grid; --grid changes it (smaller grids are for profiling only)
 A, B, R = 0.25, 4.0, 1.0
 TR = 0.6
 SIGMA = 0.114
@@ -35,9 +35,16 @@ NU_L, NU_V = 0.05, 0.5
 RATES = (1.0, 1.1, 1.1, 1.0, 1.1, 1.0, 1.1, 1.0, 1.0)
 DIAG_EVERY = 100
 BYTES_PER_LU = 72  # 9 float populations read + 9 written per lattice update
-WORKLOAD = "droplets64_4096x4096_fp32"
 REF_WINDOW = 1024
 METRIC = "MLUPS (D2Q9 MRT-pseudopotential step, 4096^2, FP32)"
+
+
+def n_droplets():
+    return max(1, 64 * NX * NY // (4096 * 4096))
+
+
+def workload_name():
+    return "droplets%d_%dx%d_fp32" % (n_droplets(), NX, NY)
 
 
 def eos_T():
@@ -45,10 +52,12 @@ def eos_T():
     return TR * wl.t_crit(A, B, R)
 
 
-def field(rho_l, rho_v, n=NX, droplets=64):
+def field(rho_l, rho_v, n=None, droplets=None):
     """The workload's density field: `droplets` non-overlapping droplets, radii uniform
     in [40, 200], on an n x n periodic lattice (seed 5)."""
     from paper_1211_6932_gb300 import workloads as wl
+    n = NX if n is None else n
+    droplets = n_droplets() if droplets is None else droplets
     rho, _, _ = wl.multi_droplets(n, n, rho_l, rho_v, 4.0, droplets, 40.0, 200.0, seed=5)
     return rho
 
@@ -60,9 +69,11 @@ def ref_field(rho_l, rho_v):
 
 
 def config(extra=None):
-    c = {"workload": WORKLOAD, "grid": [NX, NY], "droplets": 64, "a": A, "T_over_Tc": TR,
+    c = {"workload": workload_name(), "grid": [NX, NY], "droplets": n_droplets(), "a": A,
+         "T_over_Tc": TR,
          "sigma": SIGMA, "nu_l": NU_L, "nu_v": NU_V, "visc_mode": "linear",
-         "diag_every": DIAG_EVERY, "l2": "state 1.21 GB > 129 MB L2, no flush",
+         "diag_every": DIAG_EVERY,
+         "l2": "state %.2f GB > 129 MB L2, no flush" % (2 * 36 * NX * NY / 1e9),
          "parallelism": "replicas"}
     if extra:
         c.update(extra)
@@ -132,23 +143,30 @@ def load_peak():
 
 
 def kernel_source_hash():
+    """Hash of the sources that define the step kernel."""
     h = hashlib.sha256()
-    for f in ("lbm_device.cuh",):
+    for f in ("lbm_device.cuh", "lbm_kernels_impl.cuh", "lbm_kernels_f32.cu"):
         with open(os.path.join(ROOT, "paper_1211_6932_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def load_traffic(n_nodes):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the kernel."""
+    """DRAM bytes per launch from the committed ncu summary of the step kernel, scaled to
+    n_nodes, or None when the kernel source has changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "sweep2_kernel_fp32.md")
+    vals = {}
     try:
-        with open(os.path.join(ROOT, "profiles", "sweep_traffic.json")) as fh:
-            t = json.load(fh)
-    except (OSError, ValueError):
+        with open(path) as fh:
+            for line in fh:
+                for key in ("kernel_hash", "dram_bytes_per_node"):
+                    if line.strip().startswith(key + ":"):
+                        vals[key] = line.split(":", 1)[1].strip().strip("`")
+    except OSError:
         return None
-    if t.get("kernel_hash") != kernel_source_hash():
+    if vals.get("kernel_hash") != kernel_source_hash() or "dram_bytes_per_node" not in vals:
         return None
-    return float(t["dram_bytes_per_node"]) * n_nodes
+    return float(vals["dram_bytes_per_node"]) * n_nodes
 
 
 def dist_setup():
@@ -383,7 +401,11 @@ def main():
     ap.add_argument("--tile-vec", type=int, default=0)
     ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=4096,
+                    help="square grid side (default 4096; smaller grids for profiling)")
     args = ap.parse_args()
+    global NX, NY
+    NX = NY = args.grid
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

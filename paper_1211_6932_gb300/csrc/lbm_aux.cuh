@@ -82,27 +82,32 @@ template <typename S>
 __global__ void init_eq_kernel(const double* __restrict__ rho, const double* __restrict__ ux,
                                const double* __restrict__ uy, S* __restrict__ buf,
                                InstParams P, int* __restrict__ bad) {
+  // Arithmetic in the storage type; only the deviation rho - rho_ref is formed in double.
+  typedef S R;
+  const PhysParams<R>& pp = phys_params<R>(P);
   const long long N = (long long)P.nx * P.ny;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
        n += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(n % P.nx), y = (int)(n / P.nx);
-    const double r = rho[n];
-    const double u = ux ? ux[n] : 0.0, v = uy ? uy[n] : 0.0;
-    const double xb = P.b4 * r;
-    const double psi2 = P.two_over_G * r *
-                        (P.RT * (1.0 + xb * (1.0 + xb * (1.0 - xb))) /
-                             ((1.0 - xb) * (1.0 - xb) * (1.0 - xb)) -
-                         P.a * r - 1.0 / 3.0);
-    if (!(r > 0.0) || !(xb < 1.0) || !(psi2 >= 0.0) || !isfinite(u) || !isfinite(v))
+    const double rd = rho[n];
+    const R r = (R)rd, dr = (R)(rd - P.rho_ref);
+    const R u = ux ? (R)ux[n] : (R)0, v = uy ? (R)uy[n] : (R)0;
+    const R xb = pp.b4 * r;
+    const R brk = pp.RT * (((R)1 + xb * ((R)1 + xb * ((R)1 - xb))) /
+                           (((R)1 - xb) * ((R)1 - xb) * ((R)1 - xb))) -
+                  pp.a * r - (R)(1.0 / 3.0);
+    const R psi2 = pp.two_over_G * r * brk;
+    if (!(r > (R)0) || !(xb < (R)1) || !(psi2 >= (R)0) || !isfinite(u) || !isfinite(v))
       atomicAdd(bad, 1);
-    const double u2 = u * u + v * v;
+    const R u2 = u * u + v * v;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      const double eu = ex_of(q) * u + ey_of(q) * v;
-      const double feq = tw_of(q) * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * u2);
+      const R eu = (R)ex_of(q) * u + (R)ey_of(q) * v;
+      // t_q rho [1 + 3 e.v + 9/2 (e.v)^2 - 3/2 v^2] - t_q rho_ref
+      const R h = (R)tw_of(q) * (dr + r * ((R)3 * eu + (R)4.5 * eu * eu - (R)1.5 * u2));
       int qs;
       const long long s = slot_of(P, q, x, y, qs);
-      buf[s] = (S)(feq - tw_of(q) * P.rho_ref);
+      buf[s] = (S)h;
     }
   }
 }

@@ -217,6 +217,20 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
+// Compensated (Kahan) running sum: per-thread diagnostics sums stay accurate to the last
+// bits of the storage type without per-node double-precision arithmetic.
+template <typename R>
+struct CompSum {
+  R s = 0, c = 0;
+  __device__ __forceinline__ void add(R v) {
+    const R y = v - c;
+    const R t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 // ---------------------------------------------------------------------------------------
 // Arithmetic used by the collision, written once for three number types: float and
 // double (one node per value) and float2 (two nodes per value, Blackwell's packed FP32
@@ -518,8 +532,8 @@ __global__ void __launch_bounds__(NT, MinBlocks<S, NT>::value) sweep_kernel(
   S cur[Q], nxt[Q];
   R cur_rho = 1, cur_dr = 0;
   bool flag_bad = false;
-  double acc_m = 0.0, acc_x = 0.0, acc_y = 0.0;
-  float mx_u = 0.f, mx_d = 0.f;
+  CompSum<R> acc_m, acc_x, acc_y;  // per-thread compensated sums (diagnostics)
+  float mx_u = 0.f, mx_d = 0.f;    // max |v|^2, max |rho - rho_prev|
   int bad = 0;
   int waited = 0;  // ring rows waited for so far (same in every thread)
   const int last = nload - 2;
@@ -643,12 +657,11 @@ __global__ void __launch_bounds__(NT, MinBlocks<S, NT>::value) sweep_kernel(
           if (!(isfinite(cur_rho) && isfinite(ux) && isfinite(uy))) {
             ++bad;
           } else {
-            acc_m += (double)cur_rho;
-            acc_x += (double)px;
-            acc_y += (double)py;
-            mx_u = fmaxf(mx_u, (float)sqrt((double)ux * ux + (double)uy * uy));
-            if (mo.rho_prev)
-              mx_d = fmaxf(mx_d, (float)fabs((double)cur_rho - (double)mo.rho_prev[di]));
+            acc_m.add(cur_rho);
+            acc_x.add(px);
+            acc_y.add(py);
+            mx_u = fmaxf(mx_u, (float)(ux * ux + uy * uy));
+            if (mo.rho_prev) mx_d = fmaxf(mx_d, (float)fabs(cur_rho - mo.rho_prev[di]));
           }
         }
         if ((mo.flags & MOM_UPDATE_PREV) && mo.rho_prev) mo.rho_prev[di] = (S)cur_rho;
@@ -681,22 +694,24 @@ __global__ void __launch_bounds__(NT, MinBlocks<S, NT>::value) sweep_kernel(
     }
     if (flag_bad) atomicOr(status, STATUS_NONFINITE);
   } else if (mo.flags & MOM_DIAG) {
-    // Block reduction: warp shuffles, then one value per warp through shared memory.
+    // Block reduction in double: warp shuffles, then one value per warp through shared
+    // memory.  max |v| is taken from the max of |v|^2.
+    double sm = acc_m.value(), sx = acc_x.value(), sy = acc_y.value();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      acc_m += __shfl_down_sync(0xffffffffu, acc_m, o);
-      acc_x += __shfl_down_sync(0xffffffffu, acc_x, o);
-      acc_y += __shfl_down_sync(0xffffffffu, acc_y, o);
+      sm += __shfl_down_sync(0xffffffffu, sm, o);
+      sx += __shfl_down_sync(0xffffffffu, sx, o);
+      sy += __shfl_down_sync(0xffffffffu, sy, o);
       mx_u = fmaxf(mx_u, __shfl_down_sync(0xffffffffu, mx_u, o));
       mx_d = fmaxf(mx_d, __shfl_down_sync(0xffffffffu, mx_d, o));
       bad += __shfl_down_sync(0xffffffffu, bad, o);
     }
     const int wid = tid >> 5;
     if (lane == 0) {
-      red_d[wid][0] = acc_m;
-      red_d[wid][1] = acc_x;
-      red_d[wid][2] = acc_y;
-      red_f[wid][0] = mx_u;
+      red_d[wid][0] = sm;
+      red_d[wid][1] = sx;
+      red_d[wid][2] = sy;
+      red_f[wid][0] = sqrtf(mx_u);
       red_f[wid][1] = mx_d;
       red_i[wid] = bad;
     }
@@ -821,8 +836,8 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) sweep2_kernel(
   float2 cur[Q], nxt[Q];
   float2 cur_rho = N::k(1.f), cur_dr = N::k(0.f);
   bool flag_bad = false;
-  double acc_m = 0.0, acc_x = 0.0, acc_y = 0.0;
-  float mx_u = 0.f, mx_d = 0.f;
+  CompSum<float> acc_m, acc_x, acc_y;  // per-thread compensated sums (diagnostics)
+  float mx_u = 0.f, mx_d = 0.f;        // max |v|^2, max |rho - rho_prev|
   int bad = 0;
   int waited = 0;
   const int last = nload - 2;
@@ -970,12 +985,11 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) sweep2_kernel(
             if (!(isfinite(r) && isfinite(ux) && isfinite(uy))) {
               ++bad;
             } else {
-              acc_m += (double)r;
-              acc_x += (double)mx;
-              acc_y += (double)my;
-              mx_u = fmaxf(mx_u, (float)sqrt((double)ux * ux + (double)uy * uy));
-              if (mo.rho_prev)
-                mx_d = fmaxf(mx_d, (float)fabs((double)r - (double)mo.rho_prev[di]));
+              acc_m.add(r);
+              acc_x.add(mx);
+              acc_y.add(my);
+              mx_u = fmaxf(mx_u, ux * ux + uy * uy);
+              if (mo.rho_prev) mx_d = fmaxf(mx_d, fabsf(r - mo.rho_prev[di]));
             }
           }
           if ((mo.flags & MOM_UPDATE_PREV) && mo.rho_prev) mo.rho_prev[di] = r;
@@ -1007,21 +1021,22 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) sweep2_kernel(
     }
     if (flag_bad) atomicOr(status, STATUS_NONFINITE);
   } else if (mo.flags & MOM_DIAG) {
+    double sm = acc_m.value(), sx = acc_x.value(), sy = acc_y.value();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      acc_m += __shfl_down_sync(0xffffffffu, acc_m, o);
-      acc_x += __shfl_down_sync(0xffffffffu, acc_x, o);
-      acc_y += __shfl_down_sync(0xffffffffu, acc_y, o);
+      sm += __shfl_down_sync(0xffffffffu, sm, o);
+      sx += __shfl_down_sync(0xffffffffu, sx, o);
+      sy += __shfl_down_sync(0xffffffffu, sy, o);
       mx_u = fmaxf(mx_u, __shfl_down_sync(0xffffffffu, mx_u, o));
       mx_d = fmaxf(mx_d, __shfl_down_sync(0xffffffffu, mx_d, o));
       bad += __shfl_down_sync(0xffffffffu, bad, o);
     }
     const int wid = tid >> 5;
     if (lane == 0) {
-      red_d[wid][0] = acc_m;
-      red_d[wid][1] = acc_x;
-      red_d[wid][2] = acc_y;
-      red_f[wid][0] = mx_u;
+      red_d[wid][0] = sm;
+      red_d[wid][1] = sx;
+      red_d[wid][2] = sy;
+      red_f[wid][0] = sqrtf(mx_u);
       red_f[wid][1] = mx_d;
       red_i[wid] = bad;
     }

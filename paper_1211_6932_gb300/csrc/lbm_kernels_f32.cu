@@ -3,19 +3,24 @@
 
 namespace lbm {
 
-// Per-instance totals from the per-work-item partials, in a fixed order (deterministic).
+// Per-instance totals from the per-work-item partials.  One block per instance; thread t
+// takes items t, t + 256, ... and the block combines them in a fixed tree order, so the
+// result does not depend on scheduling.
 // out: 6 doubles per instance (mass, mom_x, mom_y, max_u, dinf, nonfinite).
-__global__ void diag_finalize_kernel(const double* __restrict__ part_sum,
-                                     const float* __restrict__ part_max,
-                                     const int* __restrict__ part_bad,
-                                     const int* __restrict__ item_begin, int n_inst,
-                                     double* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) diag_finalize_kernel(const double* __restrict__ part_sum,
+                                                            const float* __restrict__ part_max,
+                                                            const int* __restrict__ part_bad,
+                                                            const int* __restrict__ item_begin,
+                                                            int n_inst, double* __restrict__ out) {
+  __shared__ double sd[3][256];
+  __shared__ float sf[2][256];
+  __shared__ long long sb[256];
+  const int i = blockIdx.x, t = threadIdx.x;
   if (i >= n_inst) return;
   double m = 0, x = 0, y = 0;
   float mu = 0.f, md = 0.f;
   long long b = 0;
-  for (int k = item_begin[i]; k < item_begin[i + 1]; ++k) {
+  for (int k = item_begin[i] + t; k < item_begin[i + 1]; k += 256) {
     m += part_sum[3 * k];
     x += part_sum[3 * k + 1];
     y += part_sum[3 * k + 2];
@@ -23,14 +28,33 @@ __global__ void diag_finalize_kernel(const double* __restrict__ part_sum,
     md = fmaxf(md, part_max[2 * k + 1]);
     b += part_bad[k];
   }
-  out[6 * i + 0] = m;
-  out[6 * i + 1] = x;
-  out[6 * i + 2] = y;
-  out[6 * i + 3] = mu;
-  out[6 * i + 4] = md;
-  out[6 * i + 5] = (double)b;
+  sd[0][t] = m;
+  sd[1][t] = x;
+  sd[2][t] = y;
+  sf[0][t] = mu;
+  sf[1][t] = md;
+  sb[t] = b;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (t < w) {
+      sd[0][t] += sd[0][t + w];
+      sd[1][t] += sd[1][t + w];
+      sd[2][t] += sd[2][t + w];
+      sf[0][t] = fmaxf(sf[0][t], sf[0][t + w]);
+      sf[1][t] = fmaxf(sf[1][t], sf[1][t + w]);
+      sb[t] += sb[t + w];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    out[6 * i + 0] = sd[0][0];
+    out[6 * i + 1] = sd[1][0];
+    out[6 * i + 2] = sd[2][0];
+    out[6 * i + 3] = sf[0][0];
+    out[6 * i + 4] = sf[1][0];
+    out[6 * i + 5] = (double)sb[0];
+  }
 }
-
 
 template <>
 cudaError_t launch_sweep<float>(int nt, int vec, int mode, const float* fin, float* fout,
@@ -47,8 +71,8 @@ cudaError_t launch_sweep<float>(int nt, int vec, int mode, const float* fin, flo
 cudaError_t launch_diag_finalize(const double* part_sum, const float* part_max,
                                  const int* part_bad, const int* item_begin, int n_inst,
                                  double* out, cudaStream_t st) {
-  diag_finalize_kernel<<<(n_inst + 127) / 128, 128, 0, st>>>(part_sum, part_max, part_bad,
-                                                              item_begin, n_inst, out);
+  diag_finalize_kernel<<<n_inst, 256, 0, st>>>(part_sum, part_max, part_bad, item_begin,
+                                                n_inst, out);
   return cudaGetLastError();
 }
 
