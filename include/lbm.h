@@ -173,6 +173,28 @@ int lbm_moments_device(lbm_handle* h, void* rho, void* ux, void* uy);
  * the reference of the next call's dinf.  Synchronous. */
 int lbm_diagnostics(lbm_handle* h, lbm_diag* out);
 
+/*
+ * Diagnostics for callers that must not allocate device memory: code that runs while a
+ * CUDA graph is being captured (cudaMalloc is not allowed there), or code that lives
+ * inside a fixed device-memory budget where allocation is forbidden or would fail.  The
+ * paper has no counterpart; this is the lbm_diagnostics reduction with its per-CTA
+ * partial sums held in one fixed device array compiled into the library (room for
+ * LBM_NOALLOC_MAX_ITEMS work items, 36 bytes each, about 0.6 MB per GPU that loads the
+ * library, kept until the process exits) instead of buffers owned by the handle.
+ *   out_dev  caller-owned device memory for 6 doubles per instance: mass, mom_x, mom_y,
+ *            max_u, 0 (dinf is not computed: the reference density of lbm_diagnostics
+ *            is neither read nor updated), count of non-finite nodes.
+ * Queued on the handle's stream and not synchronised; nothing is allocated, neither on
+ * the device nor on the host.  The first call on a device looks up the array's device
+ * address, so make that first call before any stream capture.  All calls in the process
+ * share the one array and each call overwrites it (the part it uses is cleared first):
+ * calls whose work can overlap on the GPU (other streams, other handles) race and must
+ * be serialised by the caller.  Returns LBM_EINVAL if the lattice needs more work items
+ * than the array holds (see lbm_get_tiling; larger tiles need fewer items).
+ */
+#define LBM_NOALLOC_MAX_ITEMS 16384
+int lbm_diagnostics_noalloc(lbm_handle* h, double* out_dev);
+
 /* Number of steps since the last init/set/load. */
 long long lbm_step_count(const lbm_handle* h);
 

@@ -58,6 +58,7 @@ SIGNATURES = {
     "lbm_moments": (c_int, [c_void_p, dptr, dptr, dptr]),
     "lbm_moments_device": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_diagnostics": (c_int, [c_void_p, ctypes.POINTER(lbm_diag)]),
+    "lbm_diagnostics_noalloc": (c_int, [c_void_p, c_void_p]),
     "lbm_step_count": (c_longlong, [c_void_p]),
     "lbm_eval_psi": (c_int, [c_void_p, dptr, dptr, c_size_t]),
     "lbm_save": (c_int, [c_void_p, ctypes.c_char_p]),

@@ -12,6 +12,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -738,6 +739,55 @@ struct FileHeader {
 }  // namespace
 
 // ---------------------------------------------------------------------------------------
+// Allocation-free diagnostics: the per-work-item partials live in this fixed device array
+// instead of handle-owned buffers.  Layout: 3 doubles (sums) per item, then 2 floats
+// (maxima) per item, then 1 int (non-finite count) per item.
+namespace {
+
+constexpr size_t kNoAllocItemBytes = 3 * sizeof(double) + 2 * sizeof(float) + sizeof(int);
+static __device__ __align__(256) unsigned char
+    g_noalloc_partials[(size_t)LBM_NOALLOC_MAX_ITEMS * kNoAllocItemBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the array on the current device, looked up once per device.  Host
+// code must never use the symbol's name as a device pointer: it is a host-side stand-in.
+int noalloc_partials(Batch* b, unsigned char** out) {
+  int dev = 0;
+  CK(b, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices)
+    return set_err(b->err, LBM_EINVAL, "device %d beyond the %d supported", dev, kMaxDevices);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    CK(b, cudaGetSymbolAddress(&p, g_noalloc_partials));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = (unsigned char*)g_noalloc_addr[dev];
+  return LBM_OK;
+}
+
+template <typename S>
+int noalloc_diag_pass(Batch* b, double* part_sum, float* part_max, int* part_bad) {
+  MomArgs<S> mo{};
+  mo.part_sum = part_sum;
+  mo.part_max = part_max;
+  mo.part_bad = part_bad;
+  mo.flags = lbm::MOM_DIAG;  // no fields, no reference density
+  cudaError_t e = lbm::launch_sweep<S>(b->nt, b->vec, lbm::MODE_MOMENTS,
+                                       (const S*)b->slab[b->cur], nullptr, b->d_inst,
+                                       b->d_all_items, b->n_all, mo, b->d_status, b->stream);
+  if (e != cudaSuccess)
+    return set_err(b->err, LBM_ECUDA, "diagnostics pass launch failed: %s",
+                   cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
 // Single-lattice handle
 
 struct lbm_handle {
@@ -875,6 +925,40 @@ int lbm_diagnostics(lbm_handle* h, lbm_diag* out) {
   DeviceGuard g_(h ? &h->b : nullptr);
   if (!h || !out) return h ? set_err(h->b.err, LBM_EINVAL, "out must not be NULL") : LBM_EINVAL;
   return diagnostics(&h->b, out);
+}
+
+int lbm_diagnostics_noalloc(lbm_handle* h, double* out_dev) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  Batch* b = &h->b;
+  if (!out_dev) return set_err(b->err, LBM_EINVAL, "out_dev must not be NULL");
+  if (b->n_all > LBM_NOALLOC_MAX_ITEMS)
+    return set_err(b->err, LBM_EINVAL,
+                   "lbm_diagnostics_noalloc: this lattice needs %d work items, the fixed "
+                   "array holds %d; use lbm_diagnostics or larger tiles",
+                   b->n_all, LBM_NOALLOC_MAX_ITEMS);
+  unsigned char* base = nullptr;
+  int rc = noalloc_partials(b, &base);
+  if (rc) return rc;
+  const size_t cap = LBM_NOALLOC_MAX_ITEMS;
+  double* part_sum = (double*)base;
+  float* part_max = (float*)(base + 3 * sizeof(double) * cap);
+  int* part_bad = (int*)(base + (3 * sizeof(double) + 2 * sizeof(float)) * cap);
+  const size_t n = (size_t)b->n_all;
+  // Clear the part this call uses: an item that returned early must not leave an earlier
+  // call's partials behind.
+  CK(b, cudaMemsetAsync(part_sum, 0, 3 * sizeof(double) * n, b->stream));
+  CK(b, cudaMemsetAsync(part_max, 0, 2 * sizeof(float) * n, b->stream));
+  CK(b, cudaMemsetAsync(part_bad, 0, sizeof(int) * n, b->stream));
+  rc = b->fp64 ? noalloc_diag_pass<double>(b, part_sum, part_max, part_bad)
+               : noalloc_diag_pass<float>(b, part_sum, part_max, part_bad);
+  if (rc) return rc;
+  cudaError_t e = lbm::launch_diag_finalize(part_sum, part_max, part_bad, b->d_item_begin,
+                                            b->n_inst, out_dev, b->stream);
+  if (e != cudaSuccess)
+    return set_err(b->err, LBM_ECUDA, "diagnostics reduction failed: %s",
+                   cudaGetErrorString(e));
+  return LBM_OK;
 }
 
 long long lbm_step_count(const lbm_handle* h) { return h ? h->b.steps[0] : -1; }

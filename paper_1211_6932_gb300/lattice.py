@@ -195,6 +195,13 @@ class Lattice:
         self._check(self._L.lbm_diagnostics(self._h, ctypes.byref(d)))
         return _diag_dict(d)
 
+    def diagnostics_noalloc(self, out_dev):
+        """Allocation-free diagnostics into caller-owned device memory (6 doubles: mass,
+        mom_x, mom_y, max_u, 0, nonfinite); queued on the lattice's stream.  out_dev is a
+        device pointer (int) or an object with data_ptr() (e.g. a CUDA tensor)."""
+        ptr = out_dev.data_ptr() if hasattr(out_dev, "data_ptr") else int(out_dev)
+        self._check(self._L.lbm_diagnostics_noalloc(self._h, ctypes.c_void_p(ptr)))
+
     @property
     def step_count(self):
         return self._L.lbm_step_count(self._h)
