@@ -1,0 +1,136 @@
+"""Batches of ragged instances (one launch per step over every instance)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import thermo
+from paper_1211_6932_gb300 import workloads as wl
+from tests import pairs
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    pairs.case(70, 45, a=0.25, tr=0.7, sigma=0.114),
+    pairs.case(130, 67, a=0.5, tr=0.8, sigma=0.11, walls=True, visc="step", nu_l=0.05,
+               nu_v=0.3),
+    pairs.case(5, 3, a=1.0, tr=0.9, sigma=0.11),
+    pairs.case(257, 31, a=0.125, tr=0.6, sigma=0.114, visc="linear", nu_l=0.04, nu_v=0.4),
+    pairs.case(64, 200, a=0.75, tr=0.85, sigma=0.1),
+]
+
+
+def instance(c):
+    from paper_1211_6932_gb300 import Eos, Instance
+    rl, rv = pairs.maxwell(c)
+    return Instance(nx=c["nx"], ny=c["ny"], eos=Eos(a=c["a"], T=c["T"]), G=c["G"],
+                    sigma=c["sigma"], s=c["s"], nu_l=c["nu_l"], nu_v=c["nu_v"],
+                    visc_mode=c["visc"], bc="walls" if c["walls"] else "periodic",
+                    rho_c=0.5218 / 4.0, rho_l=rl, rho_v=rv)
+
+
+def start_fields(c, seed):
+    rl, rv = pairs.maxwell(c)
+    rho = wl.droplet(c["nx"], c["ny"], rl, rv, 0.3 * min(c["nx"], c["ny"]), 4.0)
+    rng = np.random.default_rng(seed)
+    return rho, 0.01 * rng.uniform(-1, 1, rho.shape), 0.01 * rng.uniform(-1, 1, rho.shape)
+
+
+def test_fp64_batch_matches_oracle_per_instance():
+    from paper_1211_6932_gb300 import Batch
+    b = Batch([instance(c) for c in CASES], precision="fp64", tile_rows=16)
+    starts = []
+    for i, c in enumerate(CASES):
+        rho, ux, uy = start_fields(c, i)
+        b.init_fields(i, rho, ux, uy)
+        starts.append(oracle.equilibrium(rho, ux, uy))
+    b.step(5)
+    for i, c in enumerate(CASES):
+        ref = oracle.run(pairs.oracle_params(c), starts[i], 5)
+        assert pairs.rel_err(b.get_populations(i), ref) <= 5e-12, i
+    b.close()
+
+
+def test_fp32_batch_equals_single_lattices_bitwise():
+    """Same kernel instantiation, so the batch and one-lattice runs are bitwise equal."""
+    from paper_1211_6932_gb300 import Batch
+    b = Batch([instance(c) for c in CASES], precision="fp32")
+    fields = [start_fields(c, 10 + i) for i, c in enumerate(CASES)]
+    for i, fl in enumerate(fields):
+        b.init_fields(i, *fl)
+    b.step(70)
+    diags = b.diagnostics()
+    for i, c in enumerate(CASES):
+        with pairs.gpu_lattice(c, "fp32") as L:
+            L.init_fields(*fields[i])
+            L.step(70)
+            assert np.array_equal(b.get_populations(i), L.get_populations()), i
+            d = L.diagnostics()
+            assert diags[i]["mass"] == d["mass"] and diags[i]["max_u"] == d["max_u"], i
+            assert diags[i]["step"] == 70
+    b.close()
+
+
+def test_run_to_equilibrium_freezes_converged_instances():
+    """Flat films converge; a converged instance is no longer stepped (its state and step
+    count stay fixed) while the others continue."""
+    from paper_1211_6932_gb300 import Batch
+    cs = [pairs.case(3, 64, a=0.5, tr=0.85, sigma=0.11),
+          pairs.case(4, 96, a=0.25, tr=0.8, sigma=0.114),
+          pairs.case(130, 67, a=0.5, tr=0.8, sigma=0.11)]
+    b = Batch([instance(c) for c in cs], precision="fp32")
+    for i, c in enumerate(cs):
+        rl, rv = pairs.maxwell(c)
+        if c["nx"] <= 4:
+            rho = wl.flat_film(c["nx"], c["ny"], rl, rv, 4.0, c["ny"] / 2)
+        else:
+            rho = wl.droplet(c["nx"], c["ny"], rl, rv, 20.0, 4.0)
+        b.init_fields(i, rho)
+    left, steps = b.run_to_equilibrium(tol=2e-6, check_every=100, max_steps=20000)
+    assert left == 0, steps
+    assert (steps > 0).all() and (steps % 100 == 0).all()
+    frozen = [b.get_populations(i) for i in range(3)]
+    b.step(50)  # nothing is active any more
+    for i in range(3):
+        assert np.array_equal(b.get_populations(i), frozen[i])
+    d = b.diagnostics()
+    assert [di["step"] for di in d] == list(steps)
+    b.close()
+
+
+def test_batch_rejects_bad_instance():
+    from paper_1211_6932_gb300 import Batch, LbmError
+    bad = instance(CASES[0])
+    bad.s = (1.0,) * 8 + (2.5,)
+    with pytest.raises(LbmError) as ei:
+        Batch([instance(CASES[1]), bad])
+    assert ei.value.code == -1
+
+
+def test_batch_of_256_workload_draws_runs():
+    """The batched-equilibria recipe (256 instances, sides 64..512) builds and steps; every
+    instance stays finite and conserves mass over 200 steps."""
+    from paper_1211_6932_gb300 import Batch, Eos, Instance
+    draws = wl.batch_draws(256, seed=4)
+    insts, fields = [], []
+    for d in draws:
+        T = d["T_over_Tc"] * wl.t_crit(d["a"])
+        rl, rv, _ = thermo.maxwell(d["a"], 4.0, 1.0, T)
+        nu_l = 0.1
+        insts.append(Instance(nx=d["nx"], ny=d["ny"], eos=Eos(a=d["a"], T=T),
+                              sigma=d["sigma"], s=oracle.rates_for(0.8), nu_l=nu_l,
+                              nu_v=nu_l * d["visc_ratio"], visc_mode="linear", rho_l=rl,
+                              rho_v=rv))
+        if d["kind"] == "film":
+            fields.append(wl.flat_film(d["nx"], d["ny"], rl, rv, 4.0, d["ny"] / 2))
+        else:
+            fields.append(wl.droplet(d["nx"], d["ny"], rl, rv, min(d["nx"], d["ny"]) / 4, 4.0))
+    b = Batch(insts, precision="fp32")
+    for i, rho in enumerate(fields):
+        b.init_fields(i, rho)
+    d0 = b.diagnostics()
+    b.step(200)
+    d1 = b.diagnostics()
+    for i in range(256):
+        assert d1[i]["nonfinite"] == 0, i
+        assert abs(d1[i]["mass"] - d0[i]["mass"]) <= 1e-5 * d0[i]["mass"], i
+    b.close()
