@@ -265,6 +265,101 @@ def run_reference(args):
     return 0
 
 
+def batch256_instances():
+    from paper_1211_6932_gb300 import Eos, Instance, maxwell, workloads as wl
+    insts, fields, nodes = [], [], 0
+    for d in wl.batch_draws(256, seed=4):
+        T = d["T_over_Tc"] * wl.t_crit(d["a"])
+        eos = Eos(a=d["a"], T=T)
+        rl, rv = maxwell(eos)
+        nu_l = 0.1
+        insts.append(Instance(nx=d["nx"], ny=d["ny"], eos=eos, sigma=d["sigma"],
+                              s=(1.0, 1.1, 1.1, 1.0, 1.1, 1.0, 1.1, 1.25, 1.25), nu_l=nu_l,
+                              nu_v=nu_l * d["visc_ratio"], visc_mode="linear", rho_l=rl,
+                              rho_v=rv))
+        if d["kind"] == "film":
+            fields.append(wl.flat_film(d["nx"], d["ny"], rl, rv, 4.0, d["ny"] / 2))
+        else:
+            fields.append(wl.droplet(d["nx"], d["ny"], rl, rv, min(d["nx"], d["ny"]) / 4, 4.0))
+        nodes += d["nx"] * d["ny"]
+    return insts, fields, nodes
+
+
+def run_batch(args):
+    """--workload batch256: every instance advances one step per launch."""
+    import torch
+
+    from paper_1211_6932_gb300 import Batch
+
+    world, rank, local = dist_setup()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    insts, fields, n_nodes = batch256_instances()
+    stream = torch.cuda.Stream(device=dev)
+    b = Batch(insts, precision="fp32", stream=stream)
+    for i, rho in enumerate(fields):
+        b.init_fields(i, rho)
+    nt, vec, rows, tuned_ms = b.autotune(steps=20)
+    for _ in range(args.warmup):
+        b.step(1)
+    b.step(64)
+    b.diagnostics()
+    K = args.steps
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    step_ms = 0.0
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    k = 0
+    launches = 0
+    while k < K:
+        n = min(DIAG_EVERY, K - k)
+        e0.record(stream)
+        b.step(n)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms += e0.elapsed_time(e1)
+        launches += n
+        if n == DIAG_EVERY:
+            b.diagnostics()
+            launches += 2
+        k += n
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    total_ms = max_over_ranks(t0.elapsed_time(t1), world)
+    peak, peak_kind = load_peak()
+    avg = step_ms / K
+    achieved = BYTES_PER_LU * n_nodes / (avg * 1e-3) / 1e9
+    if rank == 0:
+        line = {"metric": "MLUPS (D2Q9 MRT-pseudopotential step, 256-instance batch, FP32)",
+                "value": world * n_nodes * K / (total_ms * 1e-3) / 1e6, "unit": "MLUPS",
+                "n_gpus": world, "steps": K, "warmup": args.warmup,
+                "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "batch256_64to512_fp32", "instances": 256,
+                           "nodes": n_nodes, "tile_threads": nt, "tile_vec": vec,
+                           "tile_rows": rows, "autotuned_ms": tuned_ms,
+                           "diag_every": DIAG_EVERY,
+                           "l2": "state %.2f GB > 129 MB L2, no flush" % (72 * n_nodes / 1e9),
+                           "parallelism": "replicas"},
+                "gpu_launches": launches,
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                             "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                             "peak_source": peak_kind, "avg_launch_ms": avg},
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    b.close()
+    return 0
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -401,6 +496,9 @@ def main():
     ap.add_argument("--tile-vec", type=int, default=0)
     ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="field4096", choices=["field4096", "batch256"],
+                    help="field4096 (default): the 4096^2 droplet field; batch256: the "
+                         "256-instance batched-equilibria recipe")
     ap.add_argument("--grid", type=int, default=4096,
                     help="square grid side (default 4096; smaller grids for profiling)")
     args = ap.parse_args()
@@ -410,6 +508,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch256":
+        return run_batch(args)
     return run_gpu(args)
 
 

@@ -213,6 +213,19 @@ int lbm_get_tiling(const lbm_handle* h, int* threads, int* vec, int* rows);
 /* Change it (same meaning as the lbm_options fields; 0 picks the default). */
 int lbm_set_tiling(lbm_handle* h, int threads, int vec, int rows);
 
+/*
+ * Pick the step kernel's tiling by measurement: every available (threads, vec) pair with
+ * chunk heights of 8, 16, 32 and 64 rows is timed over `steps` steps (CUDA events on the
+ * handle's stream) on a saved copy of the state, which is restored afterwards (state and
+ * step count are unchanged).  The fastest is kept.  cache_path (may be NULL) names a text
+ * file of earlier choices keyed by precision, lattice sizes and GPU; a hit skips the
+ * timing, a miss appends the new choice.  The chosen values are returned through the
+ * optional out pointers (ms_per_step: the measured time of the choice, or the cached one).
+ * The environment variable LBM_TILE="threads,vec,rows", when set, overrides everything.
+ */
+int lbm_autotune(lbm_handle* h, int steps, const char* cache_path, int* threads, int* vec,
+                 int* rows, double* ms_per_step);
+
 /* The CUDA stream the handle queues work on (a cudaStream_t). */
 void* lbm_stream(const lbm_handle* h);
 
@@ -278,6 +291,12 @@ int lbm_batch_run_to_equilibrium(lbm_batch* b, double tol, int check_every,
 
 /* Number of instances still being stepped. */
 int lbm_batch_active(const lbm_batch* b);
+
+/* lbm_autotune for a batch (all active instances are stepped together). */
+int lbm_batch_autotune(lbm_batch* b, int steps, const char* cache_path, int* threads,
+                       int* vec, int* rows, double* ms_per_step);
+/* Tiling in use by a batch. */
+int lbm_batch_get_tiling(const lbm_batch* b, int* threads, int* vec, int* rows);
 
 #ifdef __cplusplus
 }

@@ -67,6 +67,8 @@ SIGNATURES = {
                                ctypes.POINTER(c_int)]),
     "lbm_set_tiling": (c_int, [c_void_p, c_int, c_int, c_int]),
     "lbm_stream": (c_void_p, [c_void_p]),
+    "lbm_autotune": (c_int, [c_void_p, c_int, ctypes.c_char_p, ctypes.POINTER(c_int),
+                             ctypes.POINTER(c_int), ctypes.POINTER(c_int), dptr]),
     "lbm_maxwell": (c_int, [lbm_eos, dptr, dptr]),
     "lbm_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(lbm_instance),
                                  c_int, c_void_p, c_int, c_int, c_int, c_int]),
@@ -79,6 +81,10 @@ SIGNATURES = {
     "lbm_batch_diagnostics": (c_int, [c_void_p, ctypes.POINTER(lbm_diag)]),
     "lbm_batch_run_to_equilibrium": (c_int, [c_void_p, c_double, c_int, c_longlong, llptr]),
     "lbm_batch_active": (c_int, [c_void_p]),
+    "lbm_batch_autotune": (c_int, [c_void_p, c_int, ctypes.c_char_p, ctypes.POINTER(c_int),
+                                   ctypes.POINTER(c_int), ctypes.POINTER(c_int), dptr]),
+    "lbm_batch_get_tiling": (c_int, [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                     ctypes.POINTER(c_int)]),
 }
 
 _LIB = None

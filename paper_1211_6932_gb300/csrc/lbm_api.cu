@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -736,6 +737,147 @@ struct FileHeader {
   InstParams params;
 };
 
+// ---------------------------------------------------------------------------------------
+// Autotuner
+
+struct TileChoice {
+  int nt = 0, vec = 0, rows = 0;
+  double ms = -1.0;
+};
+
+std::string tune_key(const Batch* b) {
+  cudaDeviceProp prop{};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaGetDeviceProperties(&prop, dev);
+  unsigned long long hsh = 1469598103934665603ULL;  // FNV-1a over the instance sizes/walls
+  long long nodes = 0;
+  for (int i = 0; i < b->n_inst; ++i) {
+    if (!b->active[i]) continue;
+    const long long v[3] = {b->inst[i].nx, b->inst[i].ny, b->inst[i].walls};
+    for (long long x : v)
+      for (int k = 0; k < 8; ++k) hsh = (hsh ^ ((x >> (8 * k)) & 0xff)) * 1099511628211ULL;
+    nodes += (long long)b->inst[i].nx * b->inst[i].ny;
+  }
+  std::string name = prop.name;
+  for (char& ch : name)
+    if (ch == ' ') ch = '_';
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s|%d|%s|%d|%lld|%016llx", b->fp64 ? "fp64" : "fp32", b->n_inst,
+           name.c_str(), prop.multiProcessorCount, nodes, hsh);
+  return buf;
+}
+
+bool cache_lookup(const char* path, const std::string& key, TileChoice& c) {
+  if (!path) return false;
+  FILE* fp = std::fopen(path, "r");
+  if (!fp) return false;
+  char line[512], k[300];
+  bool found = false;
+  while (std::fgets(line, sizeof line, fp)) {
+    TileChoice t;
+    if (std::sscanf(line, "%299s %d %d %d %lf", k, &t.nt, &t.vec, &t.rows, &t.ms) == 5 &&
+        key == k) {
+      c = t;  // the last entry for a key wins
+      found = true;
+    }
+  }
+  std::fclose(fp);
+  return found;
+}
+
+void cache_store(const char* path, const std::string& key, const TileChoice& c) {
+  if (!path) return;
+  FILE* fp = std::fopen(path, "a");
+  if (!fp) return;
+  std::fprintf(fp, "%s %d %d %d %.6f\n", key.c_str(), c.nt, c.vec, c.rows, c.ms);
+  std::fclose(fp);
+}
+
+int apply_tiling(Batch* b, int nt, int vec, int rows) {
+  if (!lbm::cfg_supported(b->fp64, nt, vec))
+    return set_err(b->err, LBM_EINVAL, "tiling %d threads x %d columns not available", nt, vec);
+  b->nt = nt;
+  b->vec = vec;
+  b->rows_req = rows;
+  return rebuild_items(b);
+}
+
+int autotune(Batch* b, int steps, const char* cache_path, TileChoice& best) {
+  if (steps < 2) return set_err(b->err, LBM_EINVAL, "autotune needs steps >= 2");
+  if (const char* env = std::getenv("LBM_TILE")) {
+    TileChoice t;
+    if (std::sscanf(env, "%d,%d,%d", &t.nt, &t.vec, &t.rows) != 3)
+      return set_err(b->err, LBM_EINVAL, "LBM_TILE must be threads,vec,rows");
+    int rc = apply_tiling(b, t.nt, t.vec, t.rows);
+    if (rc) return rc;
+    best = t;
+    return LBM_OK;
+  }
+  const std::string key = tune_key(b);
+  TileChoice hit;
+  if (cache_lookup(cache_path, key, hit) && lbm::cfg_supported(b->fp64, hit.nt, hit.vec)) {
+    best = hit;
+    return apply_tiling(b, hit.nt, hit.vec, hit.rows);
+  }
+  if (b->n_items == 0) return set_err(b->err, LBM_ESTATE, "no active instance to tune on");
+  // Save the state (both slabs agree for frozen instances; the current one for the rest).
+  void* backup = nullptr;
+  const size_t bytes = b->slab_elems * b->esz;
+  CK(b, cudaMalloc(&backup, bytes));
+  CK(b, cudaMemcpyAsync(backup, b->slab[b->cur], bytes, cudaMemcpyDeviceToDevice, b->stream));
+  const int saved_cur = b->cur;
+  const std::vector<long long> saved_steps = b->steps;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(b, cudaEventCreate(&e0));
+  CK(b, cudaEventCreate(&e1));
+  const int nts[] = {64, 128, 256};
+  const int vecs[] = {1, 2};
+  const int rows_c[] = {8, 16, 32, 64};
+  best = TileChoice();
+  int rc = LBM_OK;
+  for (int vec : vecs)
+    for (int nt : nts) {
+      if (!lbm::cfg_supported(b->fp64, nt, vec)) continue;
+      for (int rows : rows_c) {
+        rc = apply_tiling(b, nt, vec, rows);
+        if (rc) break;
+        for (int k = 0; k < 2 && rc == LBM_OK; ++k) rc = launch_step(b, b->stream);  // warm
+        if (rc) break;
+        CK(b, cudaEventRecord(e0, b->stream));
+        for (int k = 0; k < steps && rc == LBM_OK; ++k) rc = launch_step(b, b->stream);
+        if (rc) break;
+        CK(b, cudaEventRecord(e1, b->stream));
+        CK(b, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(b, cudaEventElapsedTime(&ms, e0, e1));
+        const double per = ms / steps;
+        if (best.ms < 0 || per < best.ms) {
+          best.nt = nt;
+          best.vec = vec;
+          best.rows = rows;
+          best.ms = per;
+        }
+      }
+      if (rc) break;
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // Restore the state into both slabs and the bookkeeping.
+  cudaMemcpyAsync(b->slab[0], backup, bytes, cudaMemcpyDeviceToDevice, b->stream);
+  cudaMemcpyAsync(b->slab[1], backup, bytes, cudaMemcpyDeviceToDevice, b->stream);
+  cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream);
+  cudaStreamSynchronize(b->stream);
+  cudaFree(backup);
+  b->cur = saved_cur;
+  b->steps = saved_steps;
+  if (rc) return rc;
+  rc = apply_tiling(b, best.nt, best.vec, best.rows);
+  if (rc) return rc;
+  cache_store(cache_path, key, best);
+  return LBM_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------
@@ -997,6 +1139,20 @@ int lbm_set_tiling(lbm_handle* h, int threads, int vec, int rows) {
 
 void* lbm_stream(const lbm_handle* h) { return h ? (void*)h->b.stream : nullptr; }
 
+int lbm_autotune(lbm_handle* h, int steps, const char* cache_path, int* threads, int* vec,
+                 int* rows, double* ms_per_step) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  TileChoice c;
+  int rc = autotune(&h->b, steps, cache_path, c);
+  if (rc) return rc;
+  if (threads) *threads = h->b.nt;
+  if (vec) *vec = h->b.vec;
+  if (rows) *rows = h->b.rows;
+  if (ms_per_step) *ms_per_step = c.ms;
+  return LBM_OK;
+}
+
 int lbm_save(lbm_handle* h, const char* path) {
   DeviceGuard g_(h ? &h->b : nullptr);
   if (!h || !path) return LBM_EINVAL;
@@ -1141,6 +1297,28 @@ int lbm_batch_active(const lbm_batch* b) {
   int n = 0;
   for (int a : b->b.active) n += a;
   return n;
+}
+
+int lbm_batch_autotune(lbm_batch* b, int steps, const char* cache_path, int* threads,
+                       int* vec, int* rows, double* ms_per_step) {
+  DeviceGuard g_(b ? &b->b : nullptr);
+  if (!b) return LBM_EINVAL;
+  TileChoice c;
+  int rc = autotune(&b->b, steps, cache_path, c);
+  if (rc) return rc;
+  if (threads) *threads = b->b.nt;
+  if (vec) *vec = b->b.vec;
+  if (rows) *rows = b->b.rows;
+  if (ms_per_step) *ms_per_step = c.ms;
+  return LBM_OK;
+}
+
+int lbm_batch_get_tiling(const lbm_batch* b, int* threads, int* vec, int* rows) {
+  if (!b) return LBM_EINVAL;
+  if (threads) *threads = b->b.nt;
+  if (vec) *vec = b->b.vec;
+  if (rows) *rows = b->b.rows;
+  return LBM_OK;
 }
 
 int lbm_batch_run_to_equilibrium(lbm_batch* bb, double tol, int check_every,

@@ -233,6 +233,16 @@ class Lattice:
     def stream(self):
         return self._L.lbm_stream(self._h)
 
+    def autotune(self, steps=20, cache=None):
+        """Time the available tilings on a saved copy of the state and keep the fastest;
+        returns (threads, vec, rows, ms_per_step)."""
+        t, v, r, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        self._check(self._L.lbm_autotune(self._h, int(steps),
+                                         None if cache is None else str(cache).encode(),
+                                         ctypes.byref(t), ctypes.byref(v), ctypes.byref(r),
+                                         ctypes.byref(ms)))
+        return t.value, v.value, r.value, ms.value
+
 
 @dataclasses.dataclass
 class Instance:
@@ -340,3 +350,19 @@ class Batch:
     @property
     def active(self):
         return self._check(self._L.lbm_batch_active(self._h))
+
+    def autotune(self, steps=20, cache=None):
+        """As Lattice.autotune, for all active instances together."""
+        t, v, r, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        self._check(self._L.lbm_batch_autotune(self._h, int(steps),
+                                               None if cache is None else str(cache).encode(),
+                                               ctypes.byref(t), ctypes.byref(v),
+                                               ctypes.byref(r), ctypes.byref(ms)))
+        return t.value, v.value, r.value, ms.value
+
+    @property
+    def tiling(self):
+        t, v, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self._L.lbm_batch_get_tiling(self._h, ctypes.byref(t), ctypes.byref(v),
+                                                 ctypes.byref(r)))
+        return t.value, v.value, r.value

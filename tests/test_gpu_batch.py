@@ -134,3 +134,27 @@ def test_batch_of_256_workload_draws_runs():
         assert d1[i]["nonfinite"] == 0, i
         assert abs(d1[i]["mass"] - d0[i]["mass"]) <= 1e-5 * d0[i]["mass"], i
     b.close()
+
+
+def test_autotune_keeps_state_and_uses_cache(tmp_path):
+    """The autotuner times tilings on a saved copy: populations and step count are
+    unchanged, the choice is valid, and a second call is served from the cache."""
+    import os
+    c = pairs.case(300, 200, tr=0.7, sigma=0.114)
+    f = pairs.droplet_state(c, vel=0.01)
+    cache = os.path.join(tmp_path, "tiles.txt")
+    with pairs.gpu_lattice(c, "fp32") as L:
+        L.set_populations(f)
+        L.step(3)
+        before = L.get_populations()
+        t, v, r, ms = L.autotune(steps=6, cache=cache)
+        assert (t, v) in ((64, 1), (128, 1), (256, 1), (64, 2), (128, 2)) and r in (8, 16, 32, 64)
+        assert ms > 0 and L.tiling == (t, v, r)
+        assert L.step_count == 3
+        assert np.array_equal(L.get_populations(), before)
+        L.step(2)  # stepping after tuning works with the chosen tiling
+    with pairs.gpu_lattice(c, "fp32") as L2:
+        L2.set_populations(f)
+        t2, v2, r2, ms2 = L2.autotune(steps=6, cache=cache)
+        assert (t2, v2, r2) == (t, v, r) and abs(ms2 - ms) < 1e-5
+    assert len(open(cache).read().strip().splitlines()) == 1
