@@ -151,20 +151,23 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def load_traffic(n_nodes):
+def load_traffic(n_nodes, block_size):
     """DRAM bytes per launch from the committed ncu summary of the step kernel, scaled to
-    n_nodes, or None when the kernel source has changed since that capture."""
+    n_nodes, or None when the kernel source or its block size has changed since that
+    capture."""
     path = os.path.join(ROOT, "profiles", "sweep2_kernel_fp32.md")
     vals = {}
     try:
         with open(path) as fh:
             for line in fh:
-                for key in ("kernel_hash", "dram_bytes_per_node"):
+                for key in ("kernel_hash", "block_size", "dram_bytes_per_node"):
                     if line.strip().startswith(key + ":"):
                         vals[key] = line.split(":", 1)[1].strip().strip("`")
     except OSError:
         return None
     if vals.get("kernel_hash") != kernel_source_hash() or "dram_bytes_per_node" not in vals:
+        return None
+    if vals.get("block_size") != str(block_size):
         return None
     return float(vals["dram_bytes_per_node"]) * n_nodes
 
@@ -451,8 +454,8 @@ def run_gpu(args):
 
     peak, peak_kind = load_peak()
     achieved = BYTES_PER_LU * n_nodes / (avg_launch_ms * 1e-3) / 1e9
-    traffic = load_traffic(n_nodes)
     nt, vec, rows = L.tiling
+    traffic = load_traffic(n_nodes, nt) if vec == 2 else None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K,
@@ -463,7 +466,8 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_kind,
-                         "kernel": "sweep_kernel<float,%d,%d,STEP>" % (nt, vec),
+                         "kernel": ("sweep2_kernel<%d,STEP>" % nt if vec == 2
+                                    else "sweep_kernel<float,%d,STEP>" % nt),
                          "algorithmic_bytes_per_launch": BYTES_PER_LU * n_nodes,
                          "avg_launch_ms": avg_launch_ms},
             "e2e": {"value": e2e_value, "unit": "MLUPS",

@@ -95,7 +95,7 @@ int set_err(std::string& dst, int code, const char* fmt, ...) {
 size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
 // Default kernel configuration per precision (threads per CTA, columns per thread).
-int default_threads(bool fp64) { return fp64 ? 128 : 64; }
+int default_threads(bool fp64) { return fp64 ? 128 : 96; }
 int default_vec(bool fp64) { return fp64 ? 1 : 2; }
 
 template <typename R>
@@ -831,7 +831,7 @@ int autotune(Batch* b, int steps, const char* cache_path, TileChoice& best) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CK(b, cudaEventCreate(&e0));
   CK(b, cudaEventCreate(&e1));
-  const int nts[] = {64, 128, 256};
+  const int nts[] = {32, 64, 96, 128, 256};
   const int vecs[] = {1, 2};
   const int rows_c[] = {8, 16, 32, 64};
   best = TileChoice();

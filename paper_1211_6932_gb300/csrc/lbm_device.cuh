@@ -743,11 +743,11 @@ __global__ void __launch_bounds__(NT, MinBlocks<S, NT>::value) sweep_kernel(
 // and does their arithmetic with packed float2 instructions.  Threads 1 .. NT-2 own the
 // WO = 2 NT - 4 columns of the strip; threads 0 and NT-1 evaluate psi of the halo
 // columns -1 and WO (their other column is unused); thread 0 issues the bulk copies.
-template <int NT>
+template <int NT, int NS_ = 4>
 struct Sweep2Cfg {
   static constexpr int WO = 2 * NT - 4;      // owned columns per CTA (a multiple of 4)
   static constexpr int SEG = WO + 8;         // ring row: columns x0-4 .. x0+WO+3
-  static constexpr int NSLOT = 6;            // ring rows (NSLOT - 3 rows in flight)
+  static constexpr int NSLOT = NS_;          // ring rows (NSLOT - 3 rows in flight)
   static constexpr int PSW = 2 * NT;         // psi ring row: CTA columns -2 .. WO+1
   static constexpr size_t BARS = 128;
   static constexpr size_t POP = (size_t)NSLOT * Q * SEG * sizeof(float);
@@ -756,12 +756,12 @@ struct Sweep2Cfg {
   static constexpr size_t BYTES = BARS + POP + PSI + OUT;
 };
 
-template <int NT, int MODE>
+template <int NT, int MODE, int NS_ = 4>
 __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) sweep2_kernel(
     const float* __restrict__ fin, float* __restrict__ fout, const InstParams* __restrict__ insts,
     const WorkItem* __restrict__ items, int n_items, MomArgs<float> mo,
     int* __restrict__ status) {
-  typedef Sweep2Cfg<NT> C;
+  typedef Sweep2Cfg<NT, NS_> C;
   typedef Num<float2> N;
   constexpr int WO = C::WO, SEG = C::SEG, NS = C::NSLOT, PSW = C::PSW;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -799,8 +799,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) sweep2_kernel(
   const float* gsrc = fin + P.off + seg0;
   const float2 rho_ref2 = N::k(ph.rho_ref);
 
-  auto issue_row = [&](int j) {
-    const int slot = j % NS;
+  auto issue_row = [&](int j, int slot) {
     const int r = rstart + j * dir;
     const int rp = walls ? (r < 0 ? 0 : (r >= ny ? ny - 1 : r)) : wrapi(r, ny);
     const float* src = gsrc + (long long)rp * pitch;
@@ -820,7 +819,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) sweep2_kernel(
     bulk_commit();
   };
 
-  int issued = 0;
+  int issued = 0, islot = 0;  // rows issued and the slot of the next one (issuer only)
   if (issuer) {
     s_abort = 0;
     for (int k = 0; k < NS; ++k) mbar_init(&bars[k], 1);
@@ -829,8 +828,9 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) sweep2_kernel(
   __syncthreads();
   if (issuer) {
     const int n0 = min(nload, NS);
-    for (int j = 0; j < n0; ++j) issue_row(j);
+    for (int j = 0; j < n0; ++j) issue_row(j, j);
     issued = n0;
+    islot = n0 == NS ? 0 : n0;
   }
 
   float2 cur[Q], nxt[Q];
@@ -839,22 +839,33 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) sweep2_kernel(
   CompSum<float> acc_m, acc_x, acc_y;  // per-thread compensated sums (diagnostics)
   float mx_u = 0.f, mx_d = 0.f;        // max |v|^2, max |rho - rho_prev|
   int bad = 0;
-  int waited = 0;
+  // Ring bookkeeping without division: slot of row s, and the slot/phase of the next row
+  // to wait for (rows are waited for in order, one per iteration after the first).
+  int waited = 0, wslot = 0;
+  uint32_t wphase = 0;
+  int slot_s = 1;  // s % NS for s = 1
   const int last = nload - 2;
   int s = 1;
   for (; s <= last; ++s) {
     if (issuer) {
       if (s >= 2 && issued < nload) {
         fence_proxy_async_smem();
-        issue_row(issued);
+        issue_row(issued, islot);
         ++issued;
+        islot = islot + 1 == NS ? 0 : islot + 1;
       }
       if (MODE == MODE_STEP) bulk_wait_read_all();
     }
     while (waited <= s + 1) {
-      if (!mbar_wait_bounded(&bars[waited % NS], (uint32_t)((waited / NS) & 1))) s_abort = 1;
+      if (!mbar_wait_bounded(&bars[wslot], wphase)) s_abort = 1;
       ++waited;
+      if (++wslot == NS) {
+        wslot = 0;
+        wphase ^= 1u;
+      }
     }
+    const int slot_p = slot_s == 0 ? NS - 1 : slot_s - 1;  // row s - 1
+    const int slot_n = slot_s + 1 == NS ? 0 : slot_s + 1;  // row s + 1
     const int rpsi = rstart + s * dir;
     const bool ghost = walls && (rpsi < 0 || rpsi >= ny);
     float* ps_now = psis + (s & (PSI_ROWS - 1)) * PSW;
@@ -862,9 +873,9 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) sweep2_kernel(
     if (!ghost) {
       const bool bb_low = walls && rpsi == 0;
       const bool bb_high = walls && rpsi == ny - 1;
-      const float* rowC = ring + (size_t)(s % NS) * Q * SEG + SEG_HALO + c0;
-      const float* rowS = ring + (size_t)((s - dir) % NS) * Q * SEG + SEG_HALO + c0;
-      const float* rowN = ring + (size_t)((s + dir) % NS) * Q * SEG + SEG_HALO + c0;
+      const float* rowC = ring + slot_s * (Q * SEG) + SEG_HALO + c0;
+      const float* rowS = ring + (dir > 0 ? slot_p : slot_n) * (Q * SEG) + SEG_HALO + c0;
+      const float* rowN = ring + (dir > 0 ? slot_n : slot_p) * (Q * SEG) + SEG_HALO + c0;
       auto pair_at = [&](const float* p) -> float2 {  // columns c0, c0+1 (8-byte aligned)
         return *reinterpret_cast<const float2*>(p);
       };
@@ -1000,10 +1011,13 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) sweep2_kernel(
     for (int q = 0; q < Q; ++q) cur[q] = nxt[q];
     cur_rho = nrho;
     cur_dr = ndr;
+    slot_s = slot_n;
   }
 
   if (s <= last) {
     if (issuer) {
+      // The newest row issued into each slot: once its phase completed, every earlier
+      // copy into that slot has too.
       for (int k = 0; k < NS && k < issued; ++k) {
         const int j = issued - 1 - ((issued - 1 - k) % NS);
         mbar_wait_bounded(&bars[k], (uint32_t)((j / NS) & 1));

@@ -35,7 +35,7 @@ int sweep_occupancy(int nt, int vec);
 
 // Whether a (storage type, threads per CTA, columns per thread) triple has a kernel.
 inline bool cfg_supported(bool fp64, int nt, int vec) {
-  if (vec == 2) return !fp64 && (nt == 64 || nt == 128);
+  if (vec == 2) return !fp64 && (nt == 32 || nt == 64 || nt == 96 || nt == 128);
   if (vec != 1) return false;
   return nt == 64 || nt == 128 || (nt == 256 && !fp64);
 }

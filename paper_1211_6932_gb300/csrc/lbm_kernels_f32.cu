@@ -63,7 +63,9 @@ cudaError_t launch_sweep<float>(int nt, int vec, int mode, const float* fin, flo
   if (nt == 64 && vec == 1) return launch_sweep_mode<float, 64>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
   if (nt == 128 && vec == 1) return launch_sweep_mode<float, 128>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
   if (nt == 256 && vec == 1) return launch_sweep_mode<float, 256>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
+  if (nt == 32 && vec == 2) return launch_sweep2_mode<32>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
   if (nt == 64 && vec == 2) return launch_sweep2_mode<64>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
+  if (nt == 96 && vec == 2) return launch_sweep2_mode<96>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
   if (nt == 128 && vec == 2) return launch_sweep2_mode<128>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
   return cudaErrorInvalidValue;
 }
@@ -81,7 +83,9 @@ int sweep_occupancy<float>(int nt, int vec) {
   if (nt == 64 && vec == 1) return occupancy_cfg<float, 64>();
   if (nt == 128 && vec == 1) return occupancy_cfg<float, 128>();
   if (nt == 256 && vec == 1) return occupancy_cfg<float, 256>();
+  if (nt == 32 && vec == 2) return occupancy2_cfg<32>();
   if (nt == 64 && vec == 2) return occupancy2_cfg<64>();
+  if (nt == 96 && vec == 2) return occupancy2_cfg<96>();
   if (nt == 128 && vec == 2) return occupancy2_cfg<128>();
   return 1;
 }
