@@ -34,6 +34,7 @@ SIGMA = 0.114
 NU_L, NU_V = 0.05, 0.5
 RATES = (1.0, 1.1, 1.1, 1.0, 1.1, 1.0, 1.1, 1.0, 1.0)
 DIAG_EVERY = 100
+WARM_HORIZON = 60000  # steps each initialisation of the warm-start comparison runs
 BYTES_PER_LU = 72  # 9 float populations read + 9 written per lattice update
 REF_WINDOW = 1024
 METRIC = "MLUPS (D2Q9 MRT-pseudopotential step, 4096^2, FP32)"
@@ -477,6 +478,12 @@ def run_gpu(args):
             "diagnostics": diag_last,
         }
         print("gpu part: %s" % json.dumps(line), file=sys.stderr, flush=True)
+        if not args.no_warm_start and world == 1 and NX == 4096:
+            try:
+                line["warm_start"] = warm_start_ab(stream)
+            except Exception as exc:  # reported, never hidden
+                line["warm_start"] = {"error": repr(exc)}
+            print("warm start: %s" % json.dumps(line["warm_start"]), file=sys.stderr, flush=True)
         if not args.no_cpu_baseline:
             try:
                 line["cpu_baseline"] = cpu_baseline()[0]
@@ -490,6 +497,61 @@ def run_gpu(args):
     return 0
 
 
+def warm_start_ab(stream):
+    """Learned warm start against Eq. 31 on the 4096^2 field: the training set from the
+    batched equilibria (256 draws, one film and two droplets each), the network trained on
+    the GPU, then both initialisations relaxed for WARM_HORIZON steps with the phase
+    densities recorded every 100 steps.  Steps-to-equilibrium: the first check after
+    which the vapour and liquid phase densities stay within the tolerances of the plain
+    run's final values (mean over its last 20 % of checks)."""
+    from paper_1211_6932_gb300 import Lattice, workloads as wl
+    from paper_1211_6932_gb300 import warmstart as ws
+    t0 = time.perf_counter()
+    draws = wl.warm_draws(256, seed=6)
+    ds = ws.equilibria(draws, max_steps=60000, stream=stream)
+    t_data = time.perf_counter() - t0
+    sur = ws.Surrogate(seed=0, stream=stream)
+    t1 = time.perf_counter()
+    losses = sur.fit(ds, steps=4000, lr=3e-3)
+    t_train = time.perf_counter() - t1
+    eos = ws.eos_of(A, TR)
+    plain = ws.plain_params(eos)
+    warm = sur.predict(A, TR, SIGMA, NU_V / NU_L)
+    sur.close()
+    cs, rs = wl.droplet_layout(NX, NY, n_droplets(), 40.0, 200.0, seed=5, gap=4 * ws.W_PLAIN)
+    drops = ws.drops_array(cs, rs)
+    thr = ws.phase_thresholds(plain)
+    with Lattice(NX, NY, eos, sigma=SIGMA, s=RATES, nu_l=NU_L, nu_v=NU_V, precision="fp32",
+                 visc_mode="linear", stream=stream) as L:
+        rp = ws.relax(L, drops, plain, False, thr, 100, WARM_HORIZON)
+        rw = ws.relax(L, drops, warm, True, thr, 100, WARM_HORIZON)
+    ref_v, ref_l = ws.tail_mean(rp.vap), ws.tail_mean(rp.liq)
+    tols = [(0.01, 0.002), (0.005, 0.002), (0.02, 0.005)]
+    settle = []
+    for tv, tl in tols:
+        a, b = ws.settling_step(rp, ref_v, ref_l, tv, tl), ws.settling_step(rw, ref_v, ref_l, tv, tl)
+        settle.append({"tol_vapour": tv, "tol_liquid": tl, "plain": a, "warm": b,
+                       "saved": (a - b) if a is not None and b is not None else None})
+    return {
+        "metric": "warm-start steps saved (4096^2, 64 droplets, phase densities within "
+                  "1 % vapour / 0.2 % liquid)",
+        "value": settle[0]["saved"], "unit": "steps",
+        "settling": settle,
+        "start_error": {"plain_vapour": rp.vap[0] / ref_v - 1, "warm_vapour": rw.vap[0] / ref_v - 1},
+        "final": {"plain_vapour": ref_v, "plain_liquid": ref_l,
+                  "warm_vapour": ws.tail_mean(rw.vap), "warm_liquid": ws.tail_mean(rw.liq),
+                  "rel_diff_vapour": ws.tail_mean(rw.vap) / ref_v - 1,
+                  "rel_diff_liquid": ws.tail_mean(rw.liq) / ref_l - 1},
+        "horizon": WARM_HORIZON, "thresholds": list(thr),
+        "params": {"plain": plain.__dict__, "warm": warm.__dict__},
+        "network": {"updates": int(len(losses)), "loss_first": float(losses[0]),
+                    "loss_last": float(losses[-1]), "train_s": t_train},
+        "dataset": {"draws": len(draws), "rows": int(len(ds.x)), "dropped": len(ds.dropped),
+                    "unconverged": [int(v) for v in (ds.steps < 0).sum(axis=0)],
+                    "seconds": t_data},
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -500,6 +562,8 @@ def main():
     ap.add_argument("--tile-vec", type=int, default=0)
     ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-warm-start", action="store_true",
+                    help="skip the learned warm-start comparison (4096^2, 1 GPU only)")
     ap.add_argument("--workload", default="field4096", choices=["field4096", "batch256"],
                     help="field4096 (default): the 4096^2 droplet field; batch256: the "
                          "256-instance batched-equilibria recipe")

@@ -5,13 +5,16 @@ this package only marshals arguments to it.  Import is lazy: the library is load
 first use of ``Lattice``/``Batch`` and loading fails loudly if it has not been built.
 """
 
-__all__ = ["Lattice", "Batch", "Eos", "maxwell", "lib", "LbmError"]
+__all__ = ["Lattice", "Batch", "Eos", "maxwell", "lib", "LbmError", "Mlp"]
 
 
 def __getattr__(name):
     if name in ("Lattice", "Batch", "Eos", "maxwell", "LbmError", "Options", "Instance"):
         from . import lattice
         return getattr(lattice, name)
+    if name == "Mlp":
+        from . import mlp
+        return mlp.Mlp
     if name == "lib":
         from . import _lib
         return _lib.lib

@@ -1,4 +1,4 @@
-"""ctypes declarations of the C ABI in include/lbm.h (argument marshalling only)."""
+"""ctypes declarations of the C ABI in include/*.h (argument marshalling only)."""
 import ctypes
 import os
 
@@ -42,7 +42,24 @@ class lbm_instance(ctypes.Structure):
                 ("rho_l", c_double), ("rho_v", c_double), ("rho_ref", c_double)]
 
 
-# name -> (restype, argtypes); every symbol include/lbm.h declares.
+class lbm_adam(ctypes.Structure):
+    _fields_ = [("lr", c_double), ("beta1", c_double), ("beta2", c_double), ("eps", c_double)]
+
+
+class lbm_warm_params(ctypes.Structure):
+    _fields_ = [("rho_l", c_double), ("rho_v", c_double), ("width", c_double),
+                ("shift", c_double), ("curvature", c_double)]
+
+
+class lbm_droplet(ctypes.Structure):
+    _fields_ = [("cx", c_double), ("cy", c_double), ("radius", c_double)]
+
+
+LBM_WARM_CURVATURE = 1
+fptr = ctypes.POINTER(ctypes.c_float)
+LBM_MLP_NPARAMS = 4805
+
+# name -> (restype, argtypes); every symbol include/*.h declares.
 SIGNATURES = {
     "lbm_options_default": (None, [ctypes.POINTER(lbm_options)]),
     "lbm_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_int, lbm_eos, c_double, c_double,
@@ -85,6 +102,30 @@ SIGNATURES = {
                                    ctypes.POINTER(c_int), ctypes.POINTER(c_int), dptr]),
     "lbm_batch_get_tiling": (c_int, [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                                      ctypes.POINTER(c_int)]),
+    # include/lbm_mlp.h
+    "lbm_mlp_create": (c_int, [ctypes.POINTER(c_void_p), fptr, c_int, c_void_p, c_int]),
+    "lbm_mlp_destroy": (None, [c_void_p]),
+    "lbm_mlp_last_error": (ctypes.c_char_p, [c_void_p]),
+    "lbm_mlp_set_scaling": (c_int, [c_void_p, dptr, dptr, dptr, dptr]),
+    "lbm_mlp_fit_scaling": (c_int, [c_void_p, dptr, dptr, c_int]),
+    "lbm_mlp_set_data": (c_int, [c_void_p, dptr, dptr, c_int]),
+    "lbm_mlp_train": (c_int, [c_void_p, c_int, ctypes.POINTER(lbm_adam), fptr]),
+    "lbm_mlp_gradient": (c_int, [c_void_p, fptr, fptr]),
+    "lbm_mlp_predict": (c_int, [c_void_p, dptr, c_int, dptr]),
+    "lbm_mlp_get_params": (c_int, [c_void_p, c_int, fptr]),
+    "lbm_mlp_set_params": (c_int, [c_void_p, c_int, fptr]),
+    "lbm_mlp_update_count": (c_longlong, [c_void_p]),
+    # include/lbm_warm.h
+    "lbm_measure_film": (c_int, [dptr, c_int, c_int, ctypes.POINTER(lbm_warm_params)]),
+    "lbm_measure_droplet": (c_int, [dptr, c_int, c_int, lbm_eos, dptr, dptr, dptr, dptr]),
+    "lbm_warm_encode": (c_int, [lbm_eos, ctypes.POINTER(lbm_warm_params), dptr]),
+    "lbm_warm_decode": (c_int, [lbm_eos, dptr, ctypes.POINTER(lbm_warm_params)]),
+    "lbm_vapour_law": (c_int, [c_double, c_double, c_double, c_double, dptr, dptr]),
+    "lbm_curved_densities": (c_int, [lbm_eos, ctypes.POINTER(lbm_warm_params), c_double, dptr,
+                                     dptr]),
+    "lbm_init_droplets": (c_int, [c_void_p, ctypes.POINTER(lbm_droplet), c_int,
+                                  ctypes.POINTER(lbm_warm_params), c_int]),
+    "lbm_phase_stats": (c_int, [c_void_p, c_double, c_double, dptr]),
 }
 
 _LIB = None

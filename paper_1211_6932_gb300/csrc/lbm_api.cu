@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "../../include/lbm.h"
+#include "../../include/lbm_warm.h"
 #include "lbm_internal.h"
 
 using lbm::InstParams;
@@ -1067,6 +1068,94 @@ int lbm_diagnostics(lbm_handle* h, lbm_diag* out) {
   DeviceGuard g_(h ? &h->b : nullptr);
   if (!h || !out) return h ? set_err(h->b.err, LBM_EINVAL, "out must not be NULL") : LBM_EINVAL;
   return diagnostics(&h->b, out);
+}
+
+int lbm_init_droplets(lbm_handle* h, const lbm_droplet* drops, int n, const lbm_warm_params* p,
+                      int flags) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  Batch* b = &h->b;
+  if (!drops || !p) return set_err(b->err, LBM_EINVAL, "drops and params must not be NULL");
+  if (n < 1 || n > 65536) return set_err(b->err, LBM_EINVAL, "droplet count %d not in [1, 65536]", n);
+  if (flags & ~LBM_WARM_CURVATURE) return set_err(b->err, LBM_EINVAL, "unknown flags %d", flags);
+  if (!(p->width > 0.0) || !std::isfinite(p->width) || !(p->rho_v > 0.0) ||
+      !(p->rho_l > p->rho_v) || !std::isfinite(p->rho_l) || !std::isfinite(p->shift))
+    return set_err(b->err, LBM_EINVAL, "warm-start parameters out of range");
+  const InstParams& P = b->inst[0];
+  const lbm_eos eos{P.a, 4.0 * P.b4, 1.0, P.RT};  // p depends on R and T through R T only
+  double kappa = 0.0;
+  for (int k = 0; k < n; ++k) {
+    const lbm_droplet& d = drops[k];
+    if (!std::isfinite(d.cx) || !std::isfinite(d.cy) || !(d.radius > 0.0))
+      return set_err(b->err, LBM_EINVAL, "droplet %d: bad centre or radius", k);
+    kappa += 1.0 / d.radius;
+  }
+  kappa /= n;
+  double rin = p->rho_l, rout = p->rho_v;
+  if ((flags & LBM_WARM_CURVATURE) && lbm_curved_densities(eos, p, kappa, &rin, &rout) != LBM_OK)
+    return set_err(b->err, LBM_EINVAL, "no curved-interface densities for these parameters");
+  if (!(rin > rout)) return set_err(b->err, LBM_EINVAL, "liquid density not above the vapour's");
+  std::vector<double4> recs(n);
+  for (int k = 0; k < n; ++k)
+    recs[k] = make_double4(drops[k].cx, drops[k].cy, drops[k].radius + p->shift, rin);
+  const size_t N = (size_t)P.nx * P.ny;
+  double* d_rho = nullptr;
+  double4* d_drops = nullptr;
+  int rc = dev_alloc(b, (void**)&d_rho, N * sizeof(double));
+  if (!rc) rc = dev_alloc(b, (void**)&d_drops, n * sizeof(double4));
+  if (!rc) {
+    cudaError_t e = cudaMemcpyAsync(d_drops, recs.data(), n * sizeof(double4),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+      e = lbm::launch_fill_droplets(d_rho, P.nx, P.ny, d_drops, n, rout, p->width, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess)
+      rc = set_err(b->err, LBM_ECUDA, "droplet fill failed: %s", cudaGetErrorString(e));
+  }
+  if (!rc) rc = init_instance(b, 0, d_rho, nullptr, nullptr, true);
+  if (d_rho) cudaFree(d_rho);
+  if (d_drops) cudaFree(d_drops);
+  return rc;
+}
+
+int lbm_phase_stats(lbm_handle* h, double rho_vap_max, double rho_liq_min, double out[4]) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  Batch* b = &h->b;
+  if (!out) return set_err(b->err, LBM_EINVAL, "out must not be NULL");
+  int rc = ensure_fields(b);
+  if (!rc) rc = moments_device(b, 0, b->fields[0], nullptr, nullptr, false);
+  if (rc) return rc;
+  const InstParams& P = b->inst[0];
+  const long long N = (long long)P.nx * P.ny;
+  double* d_part = nullptr;
+  rc = dev_alloc(b, (void**)&d_part, lbm::kPhaseBlocks * 4 * sizeof(double));
+  if (rc) return rc;
+  std::vector<double> part(lbm::kPhaseBlocks * 4);
+  cudaError_t e =
+      b->fp64 ? lbm::launch_phase_sums<double>((const double*)b->fields[0] + P.dense_off, N,
+                                               rho_vap_max, rho_liq_min, d_part, b->stream)
+              : lbm::launch_phase_sums<float>((const float*)b->fields[0] + P.dense_off, N,
+                                              rho_vap_max, rho_liq_min, d_part, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(part.data(), d_part, part.size() * sizeof(double),
+                        cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  cudaFree(d_part);
+  if (e != cudaSuccess)
+    return set_err(b->err, LBM_ECUDA, "phase sums failed: %s", cudaGetErrorString(e));
+  double sv = 0.0, cv = 0.0, sl = 0.0, cl = 0.0;
+  for (int k = 0; k < lbm::kPhaseBlocks; ++k) {
+    sv += part[4 * k];
+    cv += part[4 * k + 1];
+    sl += part[4 * k + 2];
+    cl += part[4 * k + 3];
+  }
+  out[0] = cv > 0 ? sv / cv : 0.0;
+  out[1] = cv;
+  out[2] = cl > 0 ? sl / cl : 0.0;
+  out[3] = cl;
+  return LBM_OK;
 }
 
 int lbm_diagnostics_noalloc(lbm_handle* h, double* out_dev) {

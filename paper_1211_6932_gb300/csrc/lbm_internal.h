@@ -29,6 +29,19 @@ cudaError_t launch_diag_finalize(const double* part_sum, const float* part_max,
                                  const int* part_bad, const int* item_begin, int n_inst,
                                  double* out, cudaStream_t st);
 
+// Droplet fill of lbm_init_droplets: rho (ny, nx) doubles on the device; drops holds n
+// records (cx, cy, r_half, rho_in) with r_half the radius of the half-density circle.
+cudaError_t launch_fill_droplets(double* rho, int nx, int ny, const double4* drops, int n,
+                                 double rho_v, double width, cudaStream_t st);
+
+// Phase sums of a dense density array (n values of type S): per block, the sum and count
+// of values below vmax and above lmin, written to part[4 * block]; returns the number of
+// blocks used (at most kPhaseBlocks).
+constexpr int kPhaseBlocks = 152 * 4;
+template <typename S>
+cudaError_t launch_phase_sums(const S* rho, long long n, double vmax, double lmin, double* part,
+                              cudaStream_t st);
+
 // Resident CTAs per SM of the step kernel instantiation (at least 1).
 template <typename S>
 int sweep_occupancy(int nt, int vec);

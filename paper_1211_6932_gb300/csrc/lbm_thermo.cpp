@@ -10,28 +10,11 @@
 #include <cmath>
 
 #include "../../include/lbm.h"
+#include "lbm_cs_host.h"
 
 namespace {
 
-struct Cs {
-  double a, b, R, T;
-  double p(double r) const {
-    const double x = b * r / 4.0;
-    return r * R * T * (1.0 + x + x * x - x * x * x) / ((1.0 - x) * (1.0 - x) * (1.0 - x)) -
-           a * r * r;
-  }
-  double dp(double r) const {
-    // d/drho of rho R T Z(x) - a rho^2 = R T (Z + x Z') - 2 a rho
-    const double x = b * r / 4.0, u = 1.0 - x;
-    const double N = 1.0 + x + x * x - x * x * x, N1 = 1.0 + 2.0 * x - 3.0 * x * x;
-    const double Z = N / (u * u * u), Z1 = N1 / (u * u * u) + 3.0 * N / (u * u * u * u);
-    return R * T * (Z + x * Z1) - 2.0 * a * r;
-  }
-  double phi(double r) const {
-    const double x = b * r / 4.0, u = 1.0 - x;
-    return R * T * (std::log(r) + (4.0 * x - 3.0 * x * x) / (u * u)) - a * r;
-  }
-};
+using lbm_host::Cs;
 
 template <typename F>
 double bisect(F f, double lo, double hi, int iters = 200) {

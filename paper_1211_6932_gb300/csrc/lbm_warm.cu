@@ -1,0 +1,102 @@
+// Device side of the warm start (include/lbm_warm.h): the droplet-field fill and the
+// phase-averaged density sums.
+#include <cuda_runtime.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+namespace {
+
+constexpr int kFillThreads = 256;
+constexpr int kDropTile = 256;  // droplets staged in shared memory per pass
+
+// One thread per node: the largest tanh profile over the droplets within reach (8
+// widths beyond the half-density circle), else rho_v.
+__global__ void __launch_bounds__(kFillThreads) fill_droplets_kernel(
+    double* __restrict__ rho, int nx, int ny, const double4* __restrict__ drops, int n,
+    double rho_v, double width) {
+  __shared__ double4 sd[kDropTile];
+  const long long N = (long long)nx * ny;
+  const long long node = (long long)blockIdx.x * kFillThreads + threadIdx.x;
+  const bool live = node < N;
+  const int x = live ? (int)(node % nx) : 0, y = live ? (int)(node / nx) : 0;
+  const double reach = 8.0 * width;
+  double best = rho_v;
+  for (int base = 0; base < n; base += kDropTile) {
+    const int m = min(kDropTile, n - base);
+    __syncthreads();
+    if ((int)threadIdx.x < m) sd[threadIdx.x] = drops[base + threadIdx.x];
+    __syncthreads();
+    if (!live) continue;
+    for (int k = 0; k < m; ++k) {
+      const double4 d = sd[k];
+      double dx = fabs((double)x - d.x);
+      dx = fmin(dx, (double)nx - dx);
+      double dy = fabs((double)y - d.y);
+      dy = fmin(dy, (double)ny - dy);
+      const double s = sqrt(dx * dx + dy * dy) - d.z;
+      if (s > reach) continue;
+      const double v = 0.5 * (d.w + rho_v) - 0.5 * (d.w - rho_v) * tanh(2.0 * s / width);
+      best = fmax(best, v);
+    }
+  }
+  if (live) rho[node] = best;
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) phase_sums_kernel(const S* __restrict__ rho, long long n,
+                                                         double vmax, double lmin,
+                                                         double* __restrict__ part) {
+  __shared__ double red[4][256];
+  double sv = 0.0, cv = 0.0, sl = 0.0, cl = 0.0;
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n;
+       i += (long long)gridDim.x * 256) {
+    const double r = (double)rho[i];
+    if (r < vmax) {
+      sv += r;
+      cv += 1.0;
+    }
+    if (r > lmin) {
+      sl += r;
+      cl += 1.0;
+    }
+  }
+  const int t = threadIdx.x;
+  red[0][t] = sv;
+  red[1][t] = cv;
+  red[2][t] = sl;
+  red[3][t] = cl;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (t < h)
+      for (int k = 0; k < 4; ++k) red[k][t] += red[k][t + h];
+    __syncthreads();
+  }
+  if (t < 4) part[4 * blockIdx.x + t] = red[t][0];
+}
+
+}  // namespace
+
+cudaError_t launch_fill_droplets(double* rho, int nx, int ny, const double4* drops, int n,
+                                 double rho_v, double width, cudaStream_t st) {
+  const long long N = (long long)nx * ny;
+  const long long blocks = (N + kFillThreads - 1) / kFillThreads;
+  fill_droplets_kernel<<<(unsigned)blocks, kFillThreads, 0, st>>>(rho, nx, ny, drops, n, rho_v,
+                                                                  width);
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_phase_sums(const S* rho, long long n, double vmax, double lmin, double* part,
+                              cudaStream_t st) {
+  phase_sums_kernel<S><<<kPhaseBlocks, 256, 0, st>>>(rho, n, vmax, lmin, part);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_phase_sums<float>(const float*, long long, double, double, double*,
+                                              cudaStream_t);
+template cudaError_t launch_phase_sums<double>(const double*, long long, double, double, double*,
+                                               cudaStream_t);
+
+}  // namespace lbm

@@ -202,6 +202,23 @@ class Lattice:
         ptr = out_dev.data_ptr() if hasattr(out_dev, "data_ptr") else int(out_dev)
         self._check(self._L.lbm_diagnostics_noalloc(self._h, ctypes.c_void_p(ptr)))
 
+    def init_droplets(self, drops, params, curvature=False):
+        """Droplet field from (n, 3) rows (cx, cy, radius) and a warm.WarmParams
+        (lbm_init_droplets; curvature=True applies LBM_WARM_CURVATURE)."""
+        d = np.ascontiguousarray(drops, dtype=np.float64)
+        if d.ndim != 2 or d.shape[1] != 3:
+            raise ValueError("drops must be an (n, 3) array of (cx, cy, radius)")
+        arr = (C.lbm_droplet * len(d))(*[C.lbm_droplet(*row) for row in d])
+        self._check(self._L.lbm_init_droplets(self._h, arr, len(d), ctypes.byref(params.c()),
+                                              C.LBM_WARM_CURVATURE if curvature else 0))
+
+    def phase_stats(self, rho_vap_max, rho_liq_min):
+        """(mean vapour density, vapour nodes, mean liquid density, liquid nodes)."""
+        out = np.empty(4)
+        self._check(self._L.lbm_phase_stats(self._h, float(rho_vap_max), float(rho_liq_min),
+                                            _d(out)))
+        return out[0], int(out[1]), out[2], int(out[3])
+
     @property
     def step_count(self):
         return self._L.lbm_step_count(self._h)
@@ -329,6 +346,13 @@ class Batch:
         self._check(self._L.lbm_batch_moments(self._h, int(i), _d(out["rho"]), _d(out["ux"]),
                                               _d(out["uy"])))
         return out
+
+    def density(self, i):
+        """rho of instance i alone (lbm_batch_moments with no velocity outputs)."""
+        inst = self.instances[i]
+        rho = np.empty((inst.ny, inst.nx))
+        self._check(self._L.lbm_batch_moments(self._h, int(i), _d(rho), None, None))
+        return rho
 
     def get_populations(self, i):
         inst = self.instances[i]

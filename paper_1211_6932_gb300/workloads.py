@@ -81,10 +81,9 @@ def splash(nx, ny, rho_l, rho_v, W, film_h, D, U):
     return rho, ux, uy
 
 
-def multi_droplets(nx, ny, rho_l, rho_v, W, n, rmin, rmax, seed, gap=None, max_tries=200000):
+def droplet_layout(nx, ny, n, rmin, rmax, seed, gap, max_tries=200000):
     """n non-overlapping droplets with radii uniform in [rmin, rmax] (rejection sampling,
-    periodic distances, surface gap >= gap, default 4 W).  Returns rho, centres, radii."""
-    gap = 4.0 * W if gap is None else gap
+    periodic distances, surface gap >= gap).  Returns centres (n, 2) and radii (n,)."""
     rng = np.random.default_rng(seed)
     cs, rs = [], []
     tries = 0
@@ -106,8 +105,15 @@ def multi_droplets(nx, ny, rho_l, rho_v, W, n, rmin, rmax, seed, gap=None, max_t
         if ok:
             cs.append(c)
             rs.append(r)
+    return np.array(cs), np.array(rs)
+
+
+def multi_droplets(nx, ny, rho_l, rho_v, W, n, rmin, rmax, seed, gap=None, max_tries=200000):
+    """n non-overlapping droplets with radii uniform in [rmin, rmax] (rejection sampling,
+    periodic distances, surface gap >= gap, default 4 W).  Returns rho, centres, radii."""
+    gap = 4.0 * W if gap is None else gap
+    cs, rs = droplet_layout(nx, ny, n, rmin, rmax, seed, gap, max_tries)
     rho = np.full((ny, nx), rho_v, dtype=np.float64)
-    x, y = grid(nx, ny)
     for (cx, cy), r in zip(cs, rs):
         # Only the bounding box of each droplet (plus its tail) is touched.
         R = int(r + 4 * W) + 2
@@ -120,7 +126,7 @@ def multi_droplets(nx, ny, rho_l, rho_v, W, n, rmin, rmax, seed, gap=None, max_t
         dy = np.minimum(dy, ny - dy)
         prof = tanh_profile(np.hypot(dx, dy) - r, rho_l, rho_v, W)
         rho[Y, X] = np.maximum(rho[Y, X], prof)
-    return rho, np.array(cs), np.array(rs)
+    return rho, cs, rs
 
 
 def sigma0(a):
@@ -151,3 +157,32 @@ def batch_draws(n=256, seed=4, lo=64, hi=512):
         out.append({"nx": nx, "ny": ny, "a": a, "T_over_Tc": tr, "sigma": sig,
                     "visc_ratio": ratio, "kind": "film" if i % 2 == 0 else "droplet"})
     return out
+
+
+def warm_draws(n=256, seed=6, lo=64, hi=512, a=(0.125, 1.0), tr=(0.5, 0.9),
+               sig=(0.8, 1.2), ratio=(1.0, 20.0)):
+    """Parameter draws of the warm-start training set: per draw one flat film and one
+    droplet of the same parameters.  Grid sides log-uniform in [lo, hi] (independently),
+    a, T/Tc, sigma / sigma0(a) and the viscosity ratio uniform in the given ranges."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        nx = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+        ny = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+        av = rng.uniform(*a)
+        out.append({"nx": nx, "ny": ny, "a": av, "T_over_Tc": rng.uniform(*tr),
+                    "sigma": sigma0(av) * rng.uniform(*sig), "visc_ratio": rng.uniform(*ratio)})
+    return out
+
+
+def mlp_init(seed, n_in=4, n_hid=64, n_out=5):
+    """Initial weights of the warm-start network, packed W1, b1, W2, b2, W3, b3 (each W
+    (out, in) row-major): every entry of a layer uniform in [-1/sqrt(fan_in),
+    1/sqrt(fan_in)] (seeded).  float32."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fi, fo in ((n_in, n_hid), (n_hid, n_hid), (n_hid, n_out)):
+        k = 1.0 / math.sqrt(fi)
+        parts.append(rng.uniform(-k, k, fo * fi))
+        parts.append(rng.uniform(-k, k, fo))
+    return np.concatenate(parts).astype(np.float32)
