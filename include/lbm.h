@@ -160,6 +160,18 @@ int lbm_step(lbm_handle* h, int n);
  * density since the last init. */
 int lbm_sync(lbm_handle* h);
 
+/*
+ * Failure-detection check (no counterpart in the paper).  Every wait of the step kernels
+ * on a shared-memory copy is bounded: after a fixed number of polls the kernel gives up,
+ * sets a status bit and returns, and the host reports LBM_ETIMEOUT.  This call exercises
+ * that path without any device fault: a one-block kernel waits, with the same bounded-wait
+ * helper, on an mbarrier that nothing arrives at, gives up after `polls` polls (1 to
+ * 2^20) and sets the same status bit in the handle.  Returns LBM_ETIMEOUT; so does every
+ * later lbm_sync until the state is replaced (lbm_init_fields, lbm_init_fields_device,
+ * lbm_set_populations, lbm_load), after which the handle works normally.  Synchronous.
+ */
+int lbm_selftest_timeout(lbm_handle* h, long long polls);
+
 /* Density and velocity of Eq. 6 (rho v = sum e f + F/2) into host (ny, nx) doubles;
  * any pointer may be NULL.  Synchronous. */
 int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy);

@@ -72,6 +72,7 @@ SIGNATURES = {
     "lbm_get_populations": (c_int, [c_void_p, dptr]),
     "lbm_step": (c_int, [c_void_p, c_int]),
     "lbm_sync": (c_int, [c_void_p]),
+    "lbm_selftest_timeout": (c_int, [c_void_p, c_longlong]),
     "lbm_moments": (c_int, [c_void_p, dptr, dptr, dptr]),
     "lbm_moments_device": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_diagnostics": (c_int, [c_void_p, ctypes.POINTER(lbm_diag)]),

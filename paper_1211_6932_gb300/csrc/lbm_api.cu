@@ -96,7 +96,7 @@ int set_err(std::string& dst, int code, const char* fmt, ...) {
 size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
 // Default kernel configuration per precision (threads per CTA, columns per thread).
-int default_threads(bool fp64) { return fp64 ? 128 : 96; }
+int default_threads(bool fp64) { return fp64 ? 128 : 128; }
 int default_vec(bool fp64) { return fp64 ? 1 : 2; }
 
 template <typename R>
@@ -1068,6 +1068,17 @@ int lbm_diagnostics(lbm_handle* h, lbm_diag* out) {
   DeviceGuard g_(h ? &h->b : nullptr);
   if (!h || !out) return h ? set_err(h->b.err, LBM_EINVAL, "out must not be NULL") : LBM_EINVAL;
   return diagnostics(&h->b, out);
+}
+
+int lbm_selftest_timeout(lbm_handle* h, long long polls) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  if (polls < 1 || polls > (1LL << 20))
+    return set_err(h->b.err, LBM_EINVAL, "polls must be in [1, 2^20]");
+  cudaError_t e = lbm::launch_wait_selftest(h->b.d_status, polls, h->b.stream);
+  if (e != cudaSuccess)
+    return set_err(h->b.err, LBM_ECUDA, "self-test launch failed: %s", cudaGetErrorString(e));
+  return sync_status(&h->b);
 }
 
 int lbm_init_droplets(lbm_handle* h, const lbm_droplet* drops, int n, const lbm_warm_params* p,

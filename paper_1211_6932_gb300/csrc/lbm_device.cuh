@@ -210,11 +210,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Wait for the completion of phase `parity` of bar; false after WAIT_LIMIT polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (long long i = 0; i < WAIT_LIMIT; ++i)
+// Wait for the completion of phase `parity` of bar; false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait_polls(uint64_t* bar, uint32_t parity, long long limit) {
+  for (long long i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
+}
+
+// The step kernels' wait: false after WAIT_LIMIT polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  return mbar_wait_polls(bar, parity, WAIT_LIMIT);
 }
 
 // Compensated (Kahan) running sum: per-thread diagnostics sums stay accurate to the last
@@ -743,7 +748,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<S, NT>::value) sweep_kernel(
 // and does their arithmetic with packed float2 instructions.  Threads 1 .. NT-2 own the
 // WO = 2 NT - 4 columns of the strip; threads 0 and NT-1 evaluate psi of the halo
 // columns -1 and WO (their other column is unused); thread 0 issues the bulk copies.
-template <int NT, int NS_ = 4>
+template <int NT, int NS_ = 4, int ST = 0>
 struct Sweep2Cfg {
   static constexpr int WO = 2 * NT - 4;      // owned columns per CTA (a multiple of 4)
   static constexpr int SEG = WO + 8;         // ring row: columns x0-4 .. x0+WO+3
@@ -752,16 +757,23 @@ struct Sweep2Cfg {
   static constexpr size_t BARS = 128;
   static constexpr size_t POP = (size_t)NSLOT * Q * SEG * sizeof(float);
   static constexpr size_t PSI = (size_t)PSI_ROWS * PSW * sizeof(float);
-  static constexpr size_t OUT = (size_t)2 * Q * PSW * sizeof(float);
+  static constexpr size_t OUT = ST ? (size_t)2 * Q * PSW * sizeof(float) : 0;  // staged rows
   static constexpr size_t BYTES = BARS + POP + PSI + OUT;
 };
 
-template <int NT, int MODE, int NS_ = 4>
-__global__ void __launch_bounds__(NT, 65536 / (NT * 128)) sweep2_kernel(
+// Resident CTAs per SM the pair kernel is compiled for (the register cap follows): with
+// direct stores shared memory allows 10 / 7 / 5 CTAs of 64 / 96 / 128 threads, and these
+// targets are the largest that compile without spills (92-96 registers).
+constexpr int sweep2_min_blocks(int nt) {
+  return nt == 64 ? 10 : nt == 96 ? 6 : nt == 128 ? 5 : 65536 / (nt * 128);
+}
+
+template <int NT, int MODE, int NS_ = 4, int ST = 0>
+__global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
     const float* __restrict__ fin, float* __restrict__ fout, const InstParams* __restrict__ insts,
     const WorkItem* __restrict__ items, int n_items, MomArgs<float> mo,
     int* __restrict__ status) {
-  typedef Sweep2Cfg<NT, NS_> C;
+  typedef Sweep2Cfg<NT, NS_, ST> C;
   typedef Num<float2> N;
   constexpr int WO = C::WO, SEG = C::SEG, NS = C::NSLOT, PSW = C::PSW;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -854,7 +866,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) sweep2_kernel(
         ++issued;
         islot = islot + 1 == NS ? 0 : islot + 1;
       }
-      if (MODE == MODE_STEP) bulk_wait_read_all();
+      if (MODE == MODE_STEP && ST) bulk_wait_read_all();
     }
     while (waited <= s + 1) {
       if (!mbar_wait_bounded(&bars[wslot], wphase)) s_abort = 1;
@@ -914,7 +926,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) sweep2_kernel(
     }
     __syncthreads();
     if (s_abort) break;
-    if (MODE == MODE_STEP && issuer && s >= 4) store_row((s - 1) & 1, rstart + (s - 2) * dir);
+    if (MODE == MODE_STEP && ST && issuer && s >= 4) store_row((s - 1) & 1, rstart + (s - 2) * dir);
 
     if (s >= 3 && owner) {
       const int yc = rstart + (s - 1) * dir;
@@ -941,14 +953,23 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) sweep2_kernel(
         const bool ok0 = cur_rho.x > 0.f && cur_rho.x < INFINITY;
         const bool ok1 = cur_rho.y > 0.f && cur_rho.y < INFINITY;
         flag_bad |= !ok0 || (xa + 1 < xend && !ok1);
-        float* ost = outs + (size_t)(s & 1) * Q * PSW + c0;
+        float* dst = fout + P.off + (long long)yc * pitch + GHOST;
+        if (ST) {
+          float* ost = outs + (size_t)(s & 1) * Q * PSW + c0;
 #pragma unroll
-        for (int q = 0; q < Q; ++q) *reinterpret_cast<float2*>(ost + q * PSW) = h[q];
-        fence_proxy_async_smem();
-        if (c0 + 2 > n_bulk || xa < 2 || xa + 1 >= nx - 2) {
-          // Columns past the last full group of four, and the ghost copies -2, -1, nx,
-          // nx+1 of the columns they mirror, are written directly.
-          float* dst = fout + P.off + (long long)yc * pitch + GHOST;
+          for (int q = 0; q < Q; ++q) *reinterpret_cast<float2*>(ost + q * PSW) = h[q];
+          fence_proxy_async_smem();
+        } else if (xa + 1 < xend) {
+          // both columns from registers: xa is even, so the pair is 8-byte aligned
+#pragma unroll
+          for (int q = 0; q < Q; ++q)
+            *reinterpret_cast<float2*>(dst + (long long)q * plane + xa) = h[q];
+        }
+        const bool tail = ST ? c0 + 2 > n_bulk : xa + 1 >= xend;
+        if (tail || xa < 2 || xa + 1 >= nx - 2) {
+          // Columns not covered above (past the last full group of four when staged, the
+          // odd last column otherwise), and the ghost copies -2, -1, nx, nx+1 of the
+          // columns they mirror, are written directly.
 #pragma unroll
           for (int k = 0; k < 2; ++k) {
             const int x = xa + k;
@@ -956,7 +977,7 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) sweep2_kernel(
             float v[Q];
 #pragma unroll
             for (int q = 0; q < Q; ++q) v[q] = k == 0 ? h[q].x : h[q].y;
-            if (c0 + k >= n_bulk) {
+            if (ST ? c0 + k >= n_bulk : tail) {
 #pragma unroll
               for (int q = 0; q < Q; ++q) dst[(long long)q * plane + x] = v[q];
             }
@@ -1022,16 +1043,18 @@ __global__ void __launch_bounds__(NT, 65536 / (NT * 128)) sweep2_kernel(
         const int j = issued - 1 - ((issued - 1 - k) % NS);
         mbar_wait_bounded(&bars[k], (uint32_t)((j / NS) & 1));
       }
-      if (MODE == MODE_STEP) bulk_wait_all();
+      if (MODE == MODE_STEP && ST) bulk_wait_all();
       atomicOr(status, STATUS_TIMEOUT);
     }
     return;
   }
   if (MODE == MODE_STEP) {
-    __syncthreads();
-    if (issuer) {
-      if (last >= 3) store_row(last & 1, rstart + (last - 1) * dir);
-      bulk_wait_all();
+    if (ST) {
+      __syncthreads();
+      if (issuer) {
+        if (last >= 3) store_row(last & 1, rstart + (last - 1) * dir);
+        bulk_wait_all();
+      }
     }
     if (flag_bad) atomicOr(status, STATUS_NONFINITE);
   } else if (mo.flags & MOM_DIAG) {

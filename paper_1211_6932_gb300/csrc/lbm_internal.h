@@ -42,6 +42,10 @@ template <typename S>
 cudaError_t launch_phase_sums(const S* rho, long long n, double vmax, double lmin, double* part,
                               cudaStream_t st);
 
+// One-block kernel whose bounded mbarrier wait runs out after `polls` polls and sets
+// STATUS_TIMEOUT in *status (lbm_selftest_timeout).
+cudaError_t launch_wait_selftest(int* status, long long polls, cudaStream_t st);
+
 // Resident CTAs per SM of the step kernel instantiation (at least 1).
 template <typename S>
 int sweep_occupancy(int nt, int vec);

@@ -70,6 +70,24 @@ cudaError_t launch_sweep<float>(int nt, int vec, int mode, const float* fin, flo
   return cudaErrorInvalidValue;
 }
 
+// Failure-detection check: thread 0 waits on an mbarrier that nothing arrives at, with
+// the step kernels' bounded-wait helper and a caller-given poll limit, and reports the
+// timeout through the same status word.  No copy is in flight, so giving up is clean.
+__global__ void wait_selftest_kernel(int* __restrict__ status, long long polls) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait_polls(&bar, 0u, polls)) atomicOr(status, STATUS_TIMEOUT);
+}
+
+cudaError_t launch_wait_selftest(int* status, long long polls, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 32, 0, st>>>(status, polls);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_diag_finalize(const double* part_sum, const float* part_max,
                                  const int* part_bad, const int* item_begin, int n_inst,
                                  double* out, cudaStream_t st) {

@@ -174,6 +174,11 @@ class Lattice:
     def sync(self):
         self._check(self._L.lbm_sync(self._h))
 
+    def selftest_timeout(self, polls=1000):
+        """Run the bounded-wait failure check (lbm_selftest_timeout); raises LbmError with
+        code LBM_ETIMEOUT when the timeout is detected and reported."""
+        self._check(self._L.lbm_selftest_timeout(self._h, int(polls)))
+
     def moments(self, out=None):
         """rho, ux, uy of Eq. 6 as host arrays.  With out= (a float64 (ny, nx) array, e.g.
         a pinned buffer) only the density is copied, into out."""
