@@ -36,6 +36,8 @@ RATES = (1.0, 1.1, 1.1, 1.0, 1.1, 1.0, 1.1, 1.0, 1.0)
 DIAG_EVERY = 100
 WARM_HORIZON = 60000  # steps each initialisation of the warm-start comparison runs
 BYTES_PER_LU = 72  # 9 float populations read + 9 written per lattice update
+PREC = "fp32"      # --precision: fp32 (deviation storage, the headline) or fp64 (parity mode)
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, nominal
 REF_WINDOW = 1024
 METRIC = "MLUPS (D2Q9 MRT-pseudopotential step, 4096^2, FP32)"
 
@@ -45,7 +47,7 @@ def n_droplets():
 
 
 def workload_name():
-    return "droplets%d_%dx%d_fp32" % (n_droplets(), NX, NY)
+    return "droplets%d_%dx%d_%s" % (n_droplets(), NX, NY, PREC)
 
 
 def eos_T():
@@ -74,7 +76,8 @@ def config(extra=None):
          "T_over_Tc": TR,
          "sigma": SIGMA, "nu_l": NU_L, "nu_v": NU_V, "visc_mode": "linear",
          "diag_every": DIAG_EVERY,
-         "l2": "state %.2f GB > 129 MB L2, no flush" % (2 * 36 * NX * NY / 1e9),
+         "l2": "state %.2f GB > 129 MB L2, no flush" % (2 * (36 if PREC == "fp32" else 72)
+                                                         * NX * NY / 1e9),
          "parallelism": "replicas"}
     if extra:
         c.update(extra)
@@ -143,10 +146,10 @@ def load_peak():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash():
-    """Hash of the sources that define the step kernel."""
+def kernel_source_hash(precision="fp32"):
+    """Hash of the sources that define the step kernel of a precision."""
     h = hashlib.sha256()
-    for f in ("lbm_device.cuh", "lbm_kernels_impl.cuh", "lbm_kernels_f32.cu"):
+    for f in ("lbm_device.cuh", "lbm_kernels_impl.cuh", "lbm_kernels_f%s.cu" % precision[2:]):
         with open(os.path.join(ROOT, "paper_1211_6932_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -171,6 +174,24 @@ def load_traffic(n_nodes, block_size):
     if vals.get("block_size") != str(block_size):
         return None
     return float(vals["dram_bytes_per_node"]) * n_nodes
+
+
+def load_fp64_flops():
+    """FP64 flops per lattice update of the FP64 step kernel from the committed ncu
+    summary (dadd + dmul + 2 dfma), or None when the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", "sweep_kernel_fp64.md")
+    vals = {}
+    try:
+        with open(path) as fh:
+            for line in fh:
+                for key in ("kernel_hash", "fp64_flops_per_lu"):
+                    if line.strip().startswith(key + ":"):
+                        vals[key] = line.split(":", 1)[1].strip().strip("`")
+    except OSError:
+        return None
+    if vals.get("kernel_hash") != kernel_source_hash("fp64") or "fp64_flops_per_lu" not in vals:
+        return None
+    return float(vals["fp64_flops_per_lu"])
 
 
 def dist_setup():
@@ -379,7 +400,7 @@ def run_gpu(args):
     rho = field(rl, rv)
     stream = torch.cuda.Stream(device=dev)
     L = Lattice(NX, NY, eos, G=-1.0, sigma=SIGMA, s=RATES, nu_l=NU_L, nu_v=NU_V,
-                precision="fp32", visc_mode="linear", stream=stream,
+                precision=PREC, visc_mode="linear", stream=stream,
                 tile_threads=args.tile_threads, tile_vec=args.tile_vec,
                 tile_rows=args.tile_rows)
     L.init_fields(rho)
@@ -454,22 +475,25 @@ def run_gpu(args):
     e2e_value = world * n_nodes * DIAG_EVERY * e2e_steps / e2e_s / 1e6
 
     peak, peak_kind = load_peak()
-    achieved = BYTES_PER_LU * n_nodes / (avg_launch_ms * 1e-3) / 1e9
+    bytes_lu = BYTES_PER_LU * (2 if PREC == "fp64" else 1)
+    achieved = bytes_lu * n_nodes / (avg_launch_ms * 1e-3) / 1e9
     nt, vec, rows = L.tiling
-    traffic = load_traffic(n_nodes, nt) if vec == 2 else None
+    traffic = load_traffic(n_nodes, nt) if vec == 2 and PREC == "fp32" else None
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": total_ms_max / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if PREC == "fp32" else "f64",
+            "data": "synthetic",
             "config": config({"tile_threads": nt, "tile_vec": vec, "tile_rows": rows}),
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_kind,
                          "kernel": ("sweep2_kernel<%d,STEP>" % nt if vec == 2
-                                    else "sweep_kernel<float,%d,STEP>" % nt),
-                         "algorithmic_bytes_per_launch": BYTES_PER_LU * n_nodes,
+                                    else "sweep_kernel<%s,%d,STEP>"
+                                    % ("float" if PREC == "fp32" else "double", nt)),
+                         "algorithmic_bytes_per_launch": bytes_lu * n_nodes,
                          "avg_launch_ms": avg_launch_ms},
             "e2e": {"value": e2e_value, "unit": "MLUPS",
                     "h2d_bytes_per_step": n_nodes * 8, "d2h_bytes_per_step": n_nodes * 4,
@@ -477,7 +501,28 @@ def run_gpu(args):
             "clocks": clocks,
             "diagnostics": diag_last,
         }
+        if PREC == "fp64":
+            flops = load_fp64_flops()
+            if flops is not None:
+                tf = flops * n_nodes / (avg_launch_ms * 1e-3) / 1e12
+                line["roofline_fp64"] = {"bound": "alu", "achieved": tf,
+                                         "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                                         "frac": tf / FP64_NOMINAL_TFLOPS,
+                                         "peak_source": "nominal FP64 rate",
+                                         "fp64_flops_per_lu": flops}
         print("gpu part: %s" % json.dumps(line), file=sys.stderr, flush=True)
+        if not args.no_other_workloads and world == 1 and NX == 4096:
+            try:
+                line["other_workloads"] = other_workloads(stream)
+            except Exception as exc:  # reported, never hidden
+                line["other_workloads"] = {"error": repr(exc)}
+            print("other workloads: %s" % json.dumps(line["other_workloads"]), file=sys.stderr,
+                  flush=True)
+        if not args.no_other_workloads and world == 1 and NX == 4096:
+            try:
+                line["coexistence"] = coexistence_summary(stream)
+            except Exception as exc:  # reported, never hidden
+                line["coexistence"] = {"error": repr(exc)}
         if not args.no_warm_start and world == 1 and NX == 4096:
             try:
                 line["warm_start"] = warm_start_ab(stream)
@@ -495,6 +540,98 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def other_workloads(stream):
+    """MLUPS of the other configurations, reported beside the headline (not roofline
+    evidence: c1 is latency-bound, c2 and c3 fit in L2), and of the FP64 parity mode on the
+    4096^2 field (144 B per lattice update).  Each: 3 warm-up steps and a 64-step graph
+    capture, then `steps` steps timed with CUDA events on the lattice's stream."""
+    import torch
+
+    from paper_1211_6932_gb300 import Eos, Lattice, maxwell
+    from paper_1211_6932_gb300 import workloads as wl
+    out = []
+
+    def timed(name, L, steps, n_nodes, dtype, bytes_per_lu, note):
+        L.step(3)
+        L.step(64)
+        L.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        L.sync()
+        ms = e0.elapsed_time(e1) / steps
+        peak, kind = load_peak()
+        rec = {"workload": name, "nodes": n_nodes, "dtype": dtype, "steps": steps,
+               "ms_per_step": ms, "mlups": n_nodes / (ms * 1e-3) / 1e6,
+               "hbm_frac": bytes_per_lu * n_nodes / (ms * 1e-3) / 1e9 / peak,
+               "peak_source": kind, "note": note, "tiling": list(L.tiling)}
+        flops = load_fp64_flops() if dtype == "f64" else None
+        if flops is not None:
+            tf = flops * n_nodes / (ms * 1e-3) / 1e12
+            rec["fp64_tflops"] = tf
+            rec["fp64_frac_of_nominal"] = tf / FP64_NOMINAL_TFLOPS
+        out.append(rec)
+
+    tau8 = (1.0, 1.1, 1.1, 1.0, 1.1, 1.0, 1.1, 1.25, 1.25)  # Sec. IV A, tau_nu = 0.8
+    # c1: 128^2 droplet, FP64
+    e = Eos(a=0.25, T=0.7 * wl.t_crit(0.25))
+    rl, rv = maxwell(e)
+    with Lattice(128, 128, e, sigma=0.114, s=tau8, precision="fp64", stream=stream) as L:
+        L.init_fields(wl.droplet(128, 128, rl, rv, 30.0, 4.0))
+        timed("c1_droplet_128x128_fp64", L, 5000, 128 * 128, "f64", 144,
+              "1.2 MB of state: latency-bound")
+    # c2: 1024^2 oscillating ellipse, linear viscosity
+    e = Eos(a=0.25, T=0.6 * wl.t_crit(0.25))
+    rl, rv = maxwell(e)
+    with Lattice(1024, 1024, e, sigma=0.114, s=RATES, nu_l=0.05, nu_v=0.5,
+                 visc_mode="linear", precision="fp32", stream=stream) as L:
+        L.init_fields(wl.ellipse(1024, 1024, rl, rv, 240, 160, 4.0, noise=1e-4, seed=2))
+        timed("c2_ellipse_1024x1024_fp32", L, 2000, 1024 * 1024, "f32", 72,
+              "75 MB of state: L2-resident")
+    # c3: 2048 x 512 splash with walls, step viscosity, Re = 200, ratio 15
+    e = Eos(a=0.25, T=0.5 * wl.t_crit(0.25))
+    rl, rv = maxwell(e)
+    nu_l = 0.05 * 160 / 200
+    with Lattice(2048, 512, e, sigma=0.114, s=(1.0, 0.8, 0.8, 1.0, 1.1, 1.0, 1.1, 1.0, 1.0),
+                 nu_l=nu_l, nu_v=15 * nu_l, visc_mode="step", bc="walls", precision="fp32",
+                 stream=stream) as L:
+        rho, ux, uy = wl.splash(2048, 512, rl, rv, 4.0, 32, 160, 0.05)
+        L.init_fields(rho, ux, uy)
+        timed("c3_splash_2048x512_walls_fp32", L, 2000, 2048 * 512, "f32", 72,
+              "75 MB of state: L2-resident")
+    # c5 field in the FP64 parity mode
+    e = Eos(a=A, T=eos_T(), b=B, R=R)
+    rl, rv = maxwell(e)
+    with Lattice(NX, NY, e, sigma=SIGMA, s=RATES, nu_l=NU_L, nu_v=NU_V, visc_mode="linear",
+                 precision="fp64", stream=stream) as L:
+        L.init_fields(field(rl, rv))
+        timed("c5_droplets64_%dx%d_fp64" % (NX, NY), L, 200, NX * NY, "f64", 144,
+              "FP64 populations and arithmetic (the 1e-12 parity mode)")
+    return out
+
+
+def coexistence_summary(stream):
+    """Fig. 1 of the paper as one batch of flat films (a = 0.5; sigma 0 and 0.11; tau_nu
+    0.6 and 0.8; T/Tc 0.49 .. 0.95; 40000 steps): lowest stable reduced temperature and
+    largest deviation from the Maxwell densities per scheme."""
+    from paper_1211_6932_gb300 import coexistence as cx
+    t0 = time.perf_counter()
+    pts = cx.sweep(a=0.5, steps=40000, stream=stream)
+    secs = time.perf_counter() - t0
+    out = {"films": len(pts), "seconds": secs, "schemes": []}
+    for sig in (0.0, 0.11):
+        for tau in (0.6, 0.8):
+            ok = [p for p in pts if p.sigma == sig and p.tau_nu == tau and p.stable]
+            out["schemes"].append({
+                "sigma": sig, "tau_nu": tau, "lowest_stable_T_over_Tc": cx.lowest_stable(pts, sig, tau),
+                "max_rel_dev_liquid": max(abs(p.rho_l / p.maxwell_l - 1) for p in ok) if ok else None,
+                "max_rel_dev_vapour": max(abs(p.rho_v / p.maxwell_v - 1) for p in ok) if ok else None})
+    return out
 
 
 def warm_start_ab(stream):
@@ -562,16 +699,21 @@ def main():
     ap.add_argument("--tile-vec", type=int, default=0)
     ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the MLUPS of configurations c1-c3 and of the FP64 mode")
     ap.add_argument("--no-warm-start", action="store_true",
                     help="skip the learned warm-start comparison (4096^2, 1 GPU only)")
     ap.add_argument("--workload", default="field4096", choices=["field4096", "batch256"],
                     help="field4096 (default): the 4096^2 droplet field; batch256: the "
                          "256-instance batched-equilibria recipe")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="fp32 (default; the headline) or fp64 (the parity mode)")
     ap.add_argument("--grid", type=int, default=4096,
                     help="square grid side (default 4096; smaller grids for profiling)")
     args = ap.parse_args()
-    global NX, NY
+    global NX, NY, PREC
     NX = NY = args.grid
+    PREC = args.precision
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
