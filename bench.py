@@ -523,6 +523,10 @@ def run_gpu(args):
                 line["coexistence"] = coexistence_summary(stream)
             except Exception as exc:  # reported, never hidden
                 line["coexistence"] = {"error": repr(exc)}
+            try:
+                line["interface"] = interface_summary(stream)
+            except Exception as exc:  # reported, never hidden
+                line["interface"] = {"error": repr(exc)}
         if not args.no_warm_start and world == 1 and NX == 4096:
             try:
                 line["warm_start"] = warm_start_ab(stream)
@@ -632,6 +636,17 @@ def coexistence_summary(stream):
                 "max_rel_dev_liquid": max(abs(p.rho_l / p.maxwell_l - 1) for p in ok) if ok else None,
                 "max_rel_dev_vapour": max(abs(p.rho_v / p.maxwell_v - 1) for p in ok) if ok else None})
     return out
+
+
+def interface_summary(stream):
+    """Sec. IV B as one batch (films and 200^2 droplets for a = 1, 0.5, 0.25 at T/Tc 0.5 and
+    0.55, 30000 steps): integral widths and the droplets' largest spurious velocity."""
+    from paper_1211_6932_gb300 import interface as itf
+    t0 = time.perf_counter()
+    rows = itf.study(t_over_tc=(0.5, 0.55), steps=30000, stream=stream)
+    return {"seconds": time.perf_counter() - t0,
+            "rows": [{"a": r.a, "T_over_Tc": r.t_over_tc, "width": r.width, "max_u": r.max_u,
+                      "density_ratio": r.density_ratio, "stable": r.stable} for r in rows]}
 
 
 def warm_start_ab(stream):
