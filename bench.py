@@ -527,6 +527,10 @@ def run_gpu(args):
                 line["interface"] = interface_summary(stream)
             except Exception as exc:  # reported, never hidden
                 line["interface"] = {"error": repr(exc)}
+            try:
+                line["stability"] = stability_summary(stream)
+            except Exception as exc:  # reported, never hidden
+                line["stability"] = {"error": repr(exc)}
         if not args.no_warm_start and world == 1 and NX == 4096:
             try:
                 line["warm_start"] = warm_start_ab(stream)
@@ -647,6 +651,18 @@ def interface_summary(stream):
     return {"seconds": time.perf_counter() - t0,
             "rows": [{"a": r.a, "T_over_Tc": r.t_over_tc, "width": r.width, "max_u": r.max_u,
                       "density_ratio": r.density_ratio, "stable": r.stable} for r in rows]}
+
+
+def stability_summary(stream):
+    """Sec. IV C / Fig. 4 as batched multi-section on the 600 x 250 splash: for each
+    viscosity ratio the bracket of the lowest liquid viscosity that stays finite and
+    positive to t* = 3."""
+    from paper_1211_6932_gb300 import stability as st
+    t0 = time.perf_counter()
+    br = st.lowest_stable_viscosity(stream=stream)
+    return {"seconds": time.perf_counter() - t0, "t_star": 3.0,
+            "brackets": [{"ratio": b.ratio, "unstable_nu_l": b.unstable, "stable_nu_l": b.stable}
+                         for b in br]}
 
 
 def warm_start_ab(stream):
