@@ -531,6 +531,10 @@ def run_gpu(args):
                 line["stability"] = stability_summary(stream)
             except Exception as exc:  # reported, never hidden
                 line["stability"] = {"error": repr(exc)}
+            try:
+                line["calibration"] = calibration_summary(stream)
+            except Exception as exc:  # reported, never hidden
+                line["calibration"] = {"error": repr(exc)}
         if not args.no_warm_start and world == 1 and NX == 4096:
             try:
                 line["warm_start"] = warm_start_ab(stream)
@@ -663,6 +667,25 @@ def stability_summary(stream):
     return {"seconds": time.perf_counter() - t0, "t_star": 3.0,
             "brackets": [{"ratio": b.ratio, "unstable_nu_l": b.unstable, "stable_nu_l": b.stable}
                          for b in br]}
+
+
+def calibration_summary(stream):
+    """sigma of the improved forcing that makes a flat lattice film's vapour density the
+    Maxwell value, for a = 0.25, 0.5, 1 at T/Tc 0.6 and 0.8 (batched films), next to the
+    continuum calibration through Eq. 21."""
+    from paper_1211_6932_gb300 import calibration as cb
+    t0 = time.perf_counter()
+    res = cb.sigma_lattice([(a, tr) for a in (0.25, 0.5, 1.0) for tr in (0.6, 0.8)],
+                           stream=stream)
+    rows = []
+    for c in res:
+        try:
+            s21 = cb.sigma_eq21(c.a, c.t_over_tc)
+        except Exception:
+            s21 = None
+        rows.append({"a": c.a, "T_over_Tc": c.t_over_tc, "sigma_lattice": c.sigma,
+                     "bracket": [c.lo, c.hi], "sigma_eq21": s21})
+    return {"seconds": time.perf_counter() - t0, "rows": rows}
 
 
 def warm_start_ab(stream):

@@ -172,6 +172,19 @@ int lbm_sync(lbm_handle* h);
  */
 int lbm_selftest_timeout(lbm_handle* h, long long polls);
 
+/*
+ * Discrete pressure tensor of Eq. 18 at every node of the current state (a diagnostic):
+ *   P = rho c_s^2 I + (G/2) psi(x) sum_q w(|e_q|^2) psi(x + e_q) e_q e_q,
+ * w = 1/3 on the axes and 1/12 on the diagonals (Eq. 7), psi of Eq. 24, rho as in
+ * lbm_moments; psi beyond a wall is that of the adjacent fluid row.  With include_sigma
+ * != 0 the improved forcing's extra stress is added: by Eq. 26 it is the isotropic
+ * 2 G^2 sigma |grad psi|^2, evaluated with the force stencil's gradient,
+ * G grad psi = -F/psi (Eq. 7), i.e. 2 sigma |F/psi|^2.  Outputs: host (ny, nx) doubles
+ * pxx, pyy, pxy.  Evaluated in double precision.  Synchronous.
+ */
+int lbm_pressure_tensor(lbm_handle* h, double* pxx, double* pyy, double* pxy,
+                        int include_sigma);
+
 /* Density and velocity of Eq. 6 (rho v = sum e f + F/2) into host (ny, nx) doubles;
  * any pointer may be NULL.  Synchronous. */
 int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy);
@@ -248,6 +261,24 @@ void* lbm_stream(const lbm_handle* h);
  * a parameter is not positive.
  */
 int lbm_maxwell(lbm_eos eos, double* rho_l, double* rho_v);
+
+/*
+ * The coexistence densities the model selects for a flat interface: the mechanical-
+ * stability condition of Eq. 21 with psi of Eq. 24 and eps = -16 G sigma (Eq. 29 with
+ * alpha = 0, beta = 3), solved like lbm_maxwell (host only, no GPU).  LBM_EINVAL if T is
+ * not below T_c, G >= 0, sigma < 0 or no root is bracketed.
+ */
+int lbm_mechanical_stability(lbm_eos eos, double G, double sigma, double* rho_l,
+                             double* rho_v);
+
+/*
+ * The sigma for which Eq. 21 gives the Maxwell vapour density of eos (Eq. 22): the
+ * calibration of the improved forcing against thermodynamics (Sec. IV A-B): a scan of
+ * sigma = 0.01, 0.02, .. 0.5 for the first sign change between two values at which Eq. 21
+ * has a solution, then bisection.  Host only.  LBM_EINVAL if there is none (Eq. 21 has
+ * no positive-pressure solution for small sigma at low reduced temperatures).
+ */
+int lbm_sigma_consistent(lbm_eos eos, double G, double* sigma);
 
 /* ---------------------------------------------------------------------------------- */
 /* Batches: many independent lattices (uneven sizes, own EOS and rates) advanced by one

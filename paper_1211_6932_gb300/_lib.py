@@ -73,6 +73,7 @@ SIGNATURES = {
     "lbm_step": (c_int, [c_void_p, c_int]),
     "lbm_sync": (c_int, [c_void_p]),
     "lbm_selftest_timeout": (c_int, [c_void_p, c_longlong]),
+    "lbm_pressure_tensor": (c_int, [c_void_p, dptr, dptr, dptr, c_int]),
     "lbm_moments": (c_int, [c_void_p, dptr, dptr, dptr]),
     "lbm_moments_device": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_diagnostics": (c_int, [c_void_p, ctypes.POINTER(lbm_diag)]),
@@ -88,6 +89,8 @@ SIGNATURES = {
     "lbm_autotune": (c_int, [c_void_p, c_int, ctypes.c_char_p, ctypes.POINTER(c_int),
                              ctypes.POINTER(c_int), ctypes.POINTER(c_int), dptr]),
     "lbm_maxwell": (c_int, [lbm_eos, dptr, dptr]),
+    "lbm_mechanical_stability": (c_int, [lbm_eos, c_double, c_double, dptr, dptr]),
+    "lbm_sigma_consistent": (c_int, [lbm_eos, c_double, dptr]),
     "lbm_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(lbm_instance),
                                  c_int, c_void_p, c_int, c_int, c_int, c_int]),
     "lbm_batch_destroy": (None, [c_void_p]),

@@ -1070,6 +1070,38 @@ int lbm_diagnostics(lbm_handle* h, lbm_diag* out) {
   return diagnostics(&h->b, out);
 }
 
+int lbm_pressure_tensor(lbm_handle* h, double* pxx, double* pyy, double* pxy,
+                        int include_sigma) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  Batch* b = &h->b;
+  if (!pxx || !pyy || !pxy) return set_err(b->err, LBM_EINVAL, "outputs must not be NULL");
+  int rc = ensure_fields(b);
+  if (!rc) rc = moments_device(b, 0, b->fields[0], nullptr, nullptr, false);
+  if (rc) return rc;
+  const InstParams& P = b->inst[0];
+  const size_t N = (size_t)P.nx * P.ny;
+  // sigma back from the per-instance constant 12 sigma s_e (s_e > 0 is checked at create)
+  const double sigma = include_sigma ? P.sig12_e / (12.0 * P.s[1]) : 0.0;
+  double* d = nullptr;
+  rc = dev_alloc(b, (void**)&d, 3 * N * sizeof(double));
+  if (rc) return rc;
+  cudaError_t e =
+      b->fp64 ? lbm::launch_pressure<double>((const double*)b->fields[0] + P.dense_off, P, sigma,
+                                             d, d + N, d + 2 * N, b->stream)
+              : lbm::launch_pressure<float>((const float*)b->fields[0] + P.dense_off, P, sigma, d,
+                                            d + N, d + 2 * N, b->stream);
+  double* outs[3] = {pxx, pyy, pxy};
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+    e = cudaMemcpyAsync(outs[k], d + k * N, N * sizeof(double), cudaMemcpyDeviceToHost,
+                        b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  cudaFree(d);
+  if (e != cudaSuccess)
+    return set_err(b->err, LBM_ECUDA, "pressure tensor failed: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
 int lbm_selftest_timeout(lbm_handle* h, long long polls) {
   DeviceGuard g_(h ? &h->b : nullptr);
   if (!h) return LBM_EINVAL;

@@ -42,6 +42,12 @@ template <typename S>
 cudaError_t launch_phase_sums(const S* rho, long long n, double vmax, double lmin, double* part,
                               cudaStream_t st);
 
+// Discrete pressure tensor of Eq. 18 from a dense density array of one instance (plus the
+// improved forcing's isotropic 2 sigma |F/psi|^2 when sigma != 0): three (ny, nx) doubles.
+template <typename S>
+cudaError_t launch_pressure(const S* rho, const InstParams& P, double sigma, double* pxx,
+                            double* pyy, double* pxy, cudaStream_t st);
+
 // One-block kernel whose bounded mbarrier wait runs out after `polls` polls and sets
 // STATUS_TIMEOUT in *status (lbm_selftest_timeout).
 cudaError_t launch_wait_selftest(int* status, long long polls, cudaStream_t st);

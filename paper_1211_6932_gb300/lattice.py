@@ -71,6 +71,25 @@ def maxwell(eos: Eos):
     return rl.value, rv.value
 
 
+def mechanical_stability(eos: Eos, sigma, G=-1.0):
+    """Flat-interface coexistence densities of Eq. 21 (library host solver)."""
+    rl, rv = ctypes.c_double(), ctypes.c_double()
+    rc = C.lib().lbm_mechanical_stability(eos.c(), float(G), float(sigma), ctypes.byref(rl),
+                                          ctypes.byref(rv))
+    if rc != 0:
+        raise LbmError(rc, "no solution of the mechanical-stability condition")
+    return rl.value, rv.value
+
+
+def sigma_consistent(eos: Eos, G=-1.0):
+    """The sigma that makes Eq. 21 give the Maxwell vapour density (library host solver)."""
+    s = ctypes.c_double()
+    rc = C.lib().lbm_sigma_consistent(eos.c(), float(G), ctypes.byref(s))
+    if rc != 0:
+        raise LbmError(rc, "no consistent sigma bracketed")
+    return s.value
+
+
 def _diag_dict(d):
     return {"mass": d.mass, "mom_x": d.mom_x, "mom_y": d.mom_y, "max_u": d.max_u,
             "dinf": d.dinf, "step": d.step, "nonfinite": d.nonfinite}
@@ -173,6 +192,13 @@ class Lattice:
 
     def sync(self):
         self._check(self._L.lbm_sync(self._h))
+
+    def pressure_tensor(self, include_sigma=False):
+        """(pxx, pyy, pxy) of Eq. 18 as (ny, nx) arrays (lbm_pressure_tensor)."""
+        out = [np.empty(self.shape) for _ in range(3)]
+        self._check(self._L.lbm_pressure_tensor(self._h, *[_d(a) for a in out],
+                                                1 if include_sigma else 0))
+        return tuple(out)
 
     def selftest_timeout(self, polls=1000):
         """Run the bounded-wait failure check (lbm_selftest_timeout); raises LbmError with
