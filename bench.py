@@ -548,6 +548,10 @@ def run_gpu(args):
                 line["calibration"] = calibration_summary(stream)
             except Exception as exc:  # reported, never hidden
                 line["calibration"] = {"error": repr(exc)}
+            try:
+                line["dynamics"] = dynamics_summary(stream)
+            except Exception as exc:  # reported, never hidden
+                line["dynamics"] = {"error": repr(exc)}
         if not args.no_warm_start and world == 1 and NX == 4096:
             try:
                 line["warm_start"] = warm_start_ab(stream)
@@ -699,6 +703,21 @@ def calibration_summary(stream):
         rows.append({"a": c.a, "T_over_Tc": c.t_over_tc, "sigma_lattice": c.sigma,
                      "bracket": [c.lo, c.hi], "sigma_eq21": s21})
     return {"seconds": time.perf_counter() - t0, "rows": rows}
+
+
+def dynamics_summary(stream):
+    """The paper's dynamic checks: Laplace law, the Sec. IV A oscillation against Eq. 32,
+    the splash spread coefficient at Re 200 and 1000."""
+    from paper_1211_6932_gb300 import dynamics as dy
+    t0 = time.perf_counter()
+    lf = dy.laplace_law(stream=stream)
+    osc = dy.ellipse_period(stream=stream)
+    c200 = dy.splash_spread(re=200.0, stream=stream).c
+    c1000 = dy.splash_spread(re=1000.0, stream=stream).c
+    return {"seconds": time.perf_counter() - t0,
+            "laplace": {"gamma": lf.gamma, "intercept": lf.intercept, "r2": lf.r2},
+            "oscillation": {"period": osc.period, "lamb": osc.lamb, "printed": 2600},
+            "splash_C": {"re200": c200, "re1000": c1000, "printed": 1.3}}
 
 
 def warm_start_ab(stream):

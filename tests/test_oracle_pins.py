@@ -485,3 +485,45 @@ def test_laplace_law():
     fit = np.polyval([slope, icpt], inv_r)
     r2 = 1 - np.sum((dp - fit) ** 2) / np.sum((dp - np.mean(dp)) ** 2)
     assert slope > 0 and r2 > 0.98 and abs(icpt) < 0.35 * min(dp)
+
+
+def test_conserved_moment_rates_have_no_effect():
+    """s_rho, s_j relax conserved moments (m - m_eq = 0 for rho and j): any values give
+    bitwise the same run."""
+    nx, ny = 14, 11
+    rho, ux, uy = smooth_field(nx, ny, 9, base=0.2, amp=0.08)
+    f0 = oracle.equilibrium(rho, ux, uy)
+    outs = []
+    for s0, s3 in ((1.0, 1.0), (0.7, 1.3), (1.9, 0.4)):
+        s = list(oracle.rates_for(0.8))
+        s[0], s[3], s[5] = s0, s3, s3
+        p = oracle.Params(nx=nx, ny=ny, a=A, b=B, R=R, T=0.7 * tc(A), sigma=0.114, s=tuple(s))
+        outs.append(oracle.run(p, f0, 6))
+    # M^-1 applied to the same post-collision moments: equal to rounding of the back
+    # transformation (the relaxed conserved moments equal their equilibria exactly)
+    assert np.max(np.abs(outs[1] - outs[0])) < 1e-15 and np.max(np.abs(outs[2] - outs[0])) < 1e-15
+
+
+def test_centred_droplet_stays_mirror_symmetric():
+    """A droplet centred on the domain keeps its x and y mirror symmetry (Sec. IV A's
+    stationary droplet): to 1e-13 after 200 steps."""
+    n = 40
+    rl, rv, _ = thermo.maxwell(A, B, R, 0.7 * tc(A))
+    p = oracle.Params(nx=n, ny=n, a=A, b=B, R=R, T=0.7 * tc(A), sigma=0.114,
+                      s=oracle.rates_for(0.8))
+    f = oracle.run(p, oracle.equilibrium(wl.droplet(n, n, rl, rv, 10.0, 4.0)), 200)
+    r = oracle.fields(p, f)["rho"]
+    assert np.max(np.abs(r - r[:, ::-1])) < 1e-13 and np.max(np.abs(r - r[::-1, :])) < 1e-13
+    assert np.max(np.abs(r - r.T)) < 1e-13
+
+
+def test_x_uniform_film_is_independent_of_nx():
+    """An x-uniform film evolves the same on a 3-wide strip and an 8-wide one."""
+    rl, rv, _ = thermo.maxwell(A, B, R, 0.7 * tc(A))
+    outs = []
+    for nx in (3, 8):
+        p = oracle.Params(nx=nx, ny=40, a=A, b=B, R=R, T=0.7 * tc(A), sigma=0.114,
+                          s=oracle.rates_for(0.8))
+        f = oracle.run(p, oracle.equilibrium(wl.flat_film(nx, 40, rl, rv, 4.0, 20)), 100)
+        outs.append(oracle.fields(p, f)["rho"])
+    assert np.max(np.abs(outs[0][:, 0] - outs[1][:, 5])) < 1e-14
