@@ -106,10 +106,14 @@ int lbm_curved_densities(lbm_eos eos, const lbm_warm_params* p, double kappa, do
                          double* rho_out);
 
 #define LBM_WARM_CURVATURE 1 /* flag: phase densities of lbm_curved_densities */
+#define LBM_WARM_BALANCED 2  /* flag: start from u0 = -F / (2 rho) (F of Eq. 7 for the
+                                field) instead of rest, so that the force-corrected velocity
+                                of Eq. 6 is zero at t = 0 */
 
 /*
- * Initialise the lattice with droplets (u = 0, populations at equilibrium, as
- * lbm_init_fields): at every node the largest over droplets of
+ * Initialise the lattice with droplets (populations at the equilibrium of Eq. 3 at
+ * u = 0, or at u0 with LBM_WARM_BALANCED, as lbm_init_fields): at every node the largest
+ * over droplets of
  *   (rho_in + rho_out)/2 - (rho_in - rho_out)/2 tanh(2 (r - R - shift) / width),
  * r the periodic distance to the droplet centre, R its radius; rho_out where no droplet
  * is within 8 widths.  (rho_in, rho_out) = (p->rho_l, p->rho_v), or with

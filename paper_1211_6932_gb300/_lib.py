@@ -56,6 +56,7 @@ class lbm_droplet(ctypes.Structure):
 
 
 LBM_WARM_CURVATURE = 1
+LBM_WARM_BALANCED = 2
 fptr = ctypes.POINTER(ctypes.c_float)
 LBM_MLP_NPARAMS = 4805
 

@@ -1120,7 +1120,8 @@ int lbm_init_droplets(lbm_handle* h, const lbm_droplet* drops, int n, const lbm_
   Batch* b = &h->b;
   if (!drops || !p) return set_err(b->err, LBM_EINVAL, "drops and params must not be NULL");
   if (n < 1 || n > 65536) return set_err(b->err, LBM_EINVAL, "droplet count %d not in [1, 65536]", n);
-  if (flags & ~LBM_WARM_CURVATURE) return set_err(b->err, LBM_EINVAL, "unknown flags %d", flags);
+  if (flags & ~(LBM_WARM_CURVATURE | LBM_WARM_BALANCED))
+    return set_err(b->err, LBM_EINVAL, "unknown flags %d", flags);
   if (!(p->width > 0.0) || !std::isfinite(p->width) || !(p->rho_v > 0.0) ||
       !(p->rho_l > p->rho_v) || !std::isfinite(p->rho_l) || !std::isfinite(p->shift))
     return set_err(b->err, LBM_EINVAL, "warm-start parameters out of range");
@@ -1142,20 +1143,25 @@ int lbm_init_droplets(lbm_handle* h, const lbm_droplet* drops, int n, const lbm_
   for (int k = 0; k < n; ++k)
     recs[k] = make_double4(drops[k].cx, drops[k].cy, drops[k].radius + p->shift, rin);
   const size_t N = (size_t)P.nx * P.ny;
+  const bool balanced = (flags & LBM_WARM_BALANCED) != 0;
   double* d_rho = nullptr;
   double4* d_drops = nullptr;
-  int rc = dev_alloc(b, (void**)&d_rho, N * sizeof(double));
+  int rc = dev_alloc(b, (void**)&d_rho, (balanced ? 3 : 1) * N * sizeof(double));
   if (!rc) rc = dev_alloc(b, (void**)&d_drops, n * sizeof(double4));
   if (!rc) {
     cudaError_t e = cudaMemcpyAsync(d_drops, recs.data(), n * sizeof(double4),
                                     cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
       e = lbm::launch_fill_droplets(d_rho, P.nx, P.ny, d_drops, n, rout, p->width, b->stream);
+    if (e == cudaSuccess && balanced)
+      e = lbm::launch_balanced_velocity(d_rho, P, d_rho + N, d_rho + 2 * N, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess)
       rc = set_err(b->err, LBM_ECUDA, "droplet fill failed: %s", cudaGetErrorString(e));
   }
-  if (!rc) rc = init_instance(b, 0, d_rho, nullptr, nullptr, true);
+  if (!rc)
+    rc = init_instance(b, 0, d_rho, balanced ? d_rho + N : nullptr,
+                       balanced ? d_rho + 2 * N : nullptr, true);
   if (d_rho) cudaFree(d_rho);
   if (d_drops) cudaFree(d_drops);
   return rc;

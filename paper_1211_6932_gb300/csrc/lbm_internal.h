@@ -34,6 +34,10 @@ cudaError_t launch_diag_finalize(const double* part_sum, const float* part_max,
 cudaError_t launch_fill_droplets(double* rho, int nx, int ny, const double4* drops, int n,
                                  double rho_v, double width, cudaStream_t st);
 
+// u0 = -F / (2 rho) (Eq. 7 force of the density field) for a force-balanced start.
+cudaError_t launch_balanced_velocity(const double* rho, const InstParams& P, double* ux,
+                                     double* uy, cudaStream_t st);
+
 // Phase sums of a dense density array (n values of type S): per block, the sum and count
 // of values below vmax and above lmin, written to part[4 * block]; returns the number of
 // blocks used (at most kPhaseBlocks).

@@ -44,6 +44,37 @@ __global__ void __launch_bounds__(kFillThreads) fill_droplets_kernel(
   if (live) rho[node] = best;
 }
 
+// u0 = -F / (2 rho) with F of Eq. 7 from psi of Eq. 24 of the density field: the initial
+// velocity for which the force-corrected velocity of Eq. 6, (sum e f + F/2) / rho, is zero
+// when f is the equilibrium at (rho, u0).  psi beyond a wall is that of the adjacent row.
+__global__ void __launch_bounds__(256) balanced_velocity_kernel(
+    const double* __restrict__ rho, InstParams P, double* __restrict__ ux,
+    double* __restrict__ uy) {
+  const int nx = P.nx, ny = P.ny;
+  const long long N = (long long)nx * ny;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx), y = (int)(i / nx);
+    auto psi_at = [&](int xx, int yy) {
+      xx = wrapi(xx, nx);
+      yy = P.walls ? (yy < 0 ? 0 : (yy >= ny ? ny - 1 : yy)) : wrapi(yy, ny);
+      return psi_eval_f64(rho[(long long)yy * nx + xx], P.b4, P.RT, P.a, P.two_over_G);
+    };
+    double gx = 0.0, gy = 0.0;
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+      const double w = (q <= 4) ? (1.0 / 3.0) : (1.0 / 12.0);
+      const double wp = w * psi_at(x + ex_of(q), y + ey_of(q));
+      gx += wp * ex_of(q);
+      gy += wp * ey_of(q);
+    }
+    const double f = -P.G * psi_at(x, y);  // F = -G psi(x) sum w psi(x + e) e
+    const double r = rho[i];
+    ux[i] = -0.5 * f * gx / r;
+    uy[i] = -0.5 * f * gy / r;
+  }
+}
+
 template <typename S>
 __global__ void __launch_bounds__(256) phase_sums_kernel(const S* __restrict__ rho, long long n,
                                                          double vmax, double lmin,
@@ -84,6 +115,15 @@ cudaError_t launch_fill_droplets(double* rho, int nx, int ny, const double4* dro
   const long long blocks = (N + kFillThreads - 1) / kFillThreads;
   fill_droplets_kernel<<<(unsigned)blocks, kFillThreads, 0, st>>>(rho, nx, ny, drops, n, rho_v,
                                                                   width);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_balanced_velocity(const double* rho, const InstParams& P, double* ux,
+                                    double* uy, cudaStream_t st) {
+  const long long N = (long long)P.nx * P.ny;
+  long long g = (N + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  balanced_velocity_kernel<<<(int)(g < 1 ? 1 : g), 256, 0, st>>>(rho, P, ux, uy);
   return cudaGetLastError();
 }
 

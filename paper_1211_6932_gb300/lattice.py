@@ -233,15 +233,18 @@ class Lattice:
         ptr = out_dev.data_ptr() if hasattr(out_dev, "data_ptr") else int(out_dev)
         self._check(self._L.lbm_diagnostics_noalloc(self._h, ctypes.c_void_p(ptr)))
 
-    def init_droplets(self, drops, params, curvature=False):
+    def init_droplets(self, drops, params, curvature=False, balanced=False):
         """Droplet field from (n, 3) rows (cx, cy, radius) and a warm.WarmParams
-        (lbm_init_droplets; curvature=True applies LBM_WARM_CURVATURE)."""
+        (lbm_init_droplets; curvature / balanced set LBM_WARM_CURVATURE /
+        LBM_WARM_BALANCED)."""
         d = np.ascontiguousarray(drops, dtype=np.float64)
         if d.ndim != 2 or d.shape[1] != 3:
             raise ValueError("drops must be an (n, 3) array of (cx, cy, radius)")
         arr = (C.lbm_droplet * len(d))(*[C.lbm_droplet(*row) for row in d])
+        flags = (C.LBM_WARM_CURVATURE if curvature else 0) | (C.LBM_WARM_BALANCED if balanced
+                                                              else 0)
         self._check(self._L.lbm_init_droplets(self._h, arr, len(d), ctypes.byref(params.c()),
-                                              C.LBM_WARM_CURVATURE if curvature else 0))
+                                              flags))
 
     def phase_stats(self, rho_vap_max, rho_liq_min):
         """(mean vapour density, vapour nodes, mean liquid density, liquid nodes)."""

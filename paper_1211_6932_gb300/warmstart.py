@@ -10,7 +10,10 @@
 2. ``Surrogate``: the network of lbm_mlp.h trained on those rows by full-batch Adam on
    the GPU; its prediction decoded (lbm_warm_decode) gives the warm-start parameters.
 3. ``relax``: a droplet field initialised on the device (lbm_init_droplets), stepped,
-   with the phase-averaged densities (lbm_phase_stats) recorded at every check.
+   with the phase-averaged densities (lbm_phase_stats) recorded at every check.  The
+   warm start uses the network's parameters with the vapour curvature law
+   (LBM_WARM_CURVATURE) and a force-balanced start (LBM_WARM_BALANCED, u0 = -F/(2 rho)),
+   which removes the start-up impulse that otherwise rings through the liquid.
 4. ``settling_step``: the first check after which the phase densities stay within a
    tolerance of reference values.
 
@@ -143,10 +146,11 @@ class Relaxation:
     thresholds: tuple  # (rho_vap_max, rho_liq_min)
 
 
-def relax(lat: Lattice, drops, params: WarmParams, curvature, thresholds, check_every, horizon):
+def relax(lat: Lattice, drops, params: WarmParams, curvature, thresholds, check_every, horizon,
+          balanced=False):
     """Initialise lat with the droplets, then step to `horizon`, recording the phase
     densities every check_every steps (including step 0)."""
-    lat.init_droplets(drops, params, curvature=curvature)
+    lat.init_droplets(drops, params, curvature=curvature, balanced=balanced)
     steps, vap, liq = [0], [], []
     v, _, l_, _ = lat.phase_stats(*thresholds)
     vap.append(v)

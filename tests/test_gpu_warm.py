@@ -86,3 +86,23 @@ def test_phase_stats_matches_density_field(precision):
     assert v == pytest.approx(rho[rho < vmax].mean(), rel=1e-12)
     assert l_ == pytest.approx(rho[rho > lmin].mean(), rel=1e-12)
     assert nv > 0 and nl > 0
+
+
+def test_balanced_start_has_zero_force_corrected_velocity():
+    """LBM_WARM_BALANCED: populations at the equilibrium of u0 = -F/(2 rho), so the
+    velocity of Eq. 6 is zero everywhere at t = 0; the populations equal the oracle's
+    equilibrium at the oracle's u0."""
+    from paper_1211_6932_gb300.warm import WarmParams
+    ctx, rl, rv = lattice(180, 150, "fp64")
+    p = WarmParams(rl, rv, 4.5, 0.3, 0.0)
+    ref_rho = ow.droplet_field(180, 150, DROPS, [rl] * len(DROPS), rv, 4.5, 0.3)
+    with ctx as L:
+        L.init_droplets(DROPS, p, balanced=True)
+        m = L.moments()
+        got = L.get_populations()
+    assert np.max(np.abs(m["ux"])) < 1e-15 and np.max(np.abs(m["uy"])) < 1e-15
+    c = dict(nx=180, ny=150, a=A, T=T, sigma=0.114, s=(1.0, 1.1, 1.1, 1.0, 1.1, 1.0, 1.1, 1.0, 1.0),
+             visc="linear", nu_l=0.05, nu_v=0.5, walls=False, G=-1.0)
+    fl = oracle.fields(pairs.oracle_params(c), oracle.equilibrium(ref_rho))
+    u0x, u0y = -0.5 * fl["Fx"] / ref_rho, -0.5 * fl["Fy"] / ref_rho
+    assert np.max(np.abs(got - oracle.equilibrium(ref_rho, u0x, u0y))) <= 1e-14

@@ -1,11 +1,11 @@
 """What the trained network gains: the 4096^2 field of 64 droplets (radii 40..200) at
-a = 0.25, T = 0.6 T_c, sigma = 0.114, viscosity ratio 10, started from the network's
-warm-start parameters settles its phase densities in fewer steps than from Eq. 31 with
-the Maxwell densities, and settles to the same values.
+a = 0.25, T = 0.6 T_c, sigma = 0.114, viscosity ratio 10, started from the warm start
+(the network's parameters with the vapour curvature law and a force-balanced start)
+settles its phase densities in fewer steps than from Eq. 31 with the Maxwell densities
+at rest, and settles to the same values.
 
-The training set here is a reduced one (48 draws in a box around the field's parameters,
-grids 64..160) so that the test runs in well under a minute; the benchmark uses the full
-256-draw set."""
+The training set is the benchmark's: 256 draws over the whole parameter box of the
+batched workload, one film and two droplets each (about 20 s on the GPU)."""
 import numpy as np
 import pytest
 
@@ -19,12 +19,10 @@ A, TR, SIGMA, RATIO = 0.25, 0.6, 0.114, 10.0
 @pytest.fixture(scope="module")
 def surrogate():
     from paper_1211_6932_gb300 import warmstart as ws
-    draws = wl.warm_draws(48, seed=2, lo=64, hi=160, a=(0.2, 0.32), tr=(0.55, 0.65),
-                          sig=(0.9, 1.1), ratio=(5.0, 15.0))
-    ds = ws.equilibria(draws, max_steps=40000, avg_samples=10, avg_stride=200)
-    assert len(ds.x) >= 44, ds.dropped
+    ds = ws.equilibria(wl.warm_draws(256, seed=6), max_steps=60000)
+    assert len(ds.x) >= 240, ds.dropped
     sur = ws.Surrogate(seed=0)
-    losses = sur.fit(ds, steps=3000, lr=3e-3)
+    losses = sur.fit(ds, steps=4000, lr=3e-3)
     assert losses[-1] < 1e-2 * losses[0]
     yield sur
     sur.close()
@@ -47,12 +45,13 @@ def test_warm_start_settles_sooner_to_the_same_state(surrogate):
     with Lattice(4096, 4096, eos, sigma=SIGMA, s=ws.RATES, nu_l=0.05, nu_v=0.05 * RATIO,
                  precision="fp32", visc_mode="linear") as L:
         rp = ws.relax(L, drops, plain, False, thr, 100, 30000)
-        rw = ws.relax(L, drops, warm, True, thr, 100, 30000)
+        rw = ws.relax(L, drops, warm, True, thr, 100, 30000, balanced=True)
     ref_v, ref_l = ws.tail_mean(rp.vap), ws.tail_mean(rp.liq)
-    sp = ws.settling_step(rp, ref_v, ref_l, 0.01, 0.002)
-    sw = ws.settling_step(rw, ref_v, ref_l, 0.01, 0.002)
-    assert sp is not None and sw is not None
-    assert sw < 0.7 * sp, (sw, sp)
+    for tv, tl in ((0.01, 0.002), (0.005, 0.001)):
+        sp = ws.settling_step(rp, ref_v, ref_l, tv, tl)
+        sw = ws.settling_step(rw, ref_v, ref_l, tv, tl)
+        assert sp is not None and sw is not None
+        assert sw < 0.5 * sp, (tv, tl, sw, sp)
     # the starting vapour is much closer to where the field settles
     assert abs(rw.vap[0] / ref_v - 1) < 0.5 * abs(rp.vap[0] / ref_v - 1)
     # same final state
