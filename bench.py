@@ -633,6 +633,14 @@ def other_workloads(stream):
         L.init_fields(rho, ux, uy)
         timed("c3_splash_2048x512_walls_fp32", L, 2000, 2048 * 512, "f32", 72,
               "75 MB of state: L2-resident")
+    # c5 field, FP32 storage with psi of Eq. 24 evaluated in FP64 (the psi_fp64 option)
+    e = Eos(a=A, T=eos_T(), b=B, R=R)
+    rl, rv = maxwell(e)
+    with Lattice(NX, NY, e, sigma=SIGMA, s=RATES, nu_l=NU_L, nu_v=NU_V, visc_mode="linear",
+                 precision="fp32", psi_fp64=True, stream=stream) as L:
+        L.init_fields(field(rl, rv))
+        timed("c5_droplets64_%dx%d_fp32_psi_fp64" % (NX, NY), L, 500, NX * NY, "f32", 72,
+              "FP32 storage and arithmetic, psi in FP64")
     # c5 field in the FP64 parity mode
     e = Eos(a=A, T=eos_T(), b=B, R=R)
     rl, rv = maxwell(e)
