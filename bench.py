@@ -225,8 +225,9 @@ def max_over_ranks(v, world):
     return float(t.item())
 
 
-def cpu_baseline(steps=None, budget_s=15.0):
-    """The FP64 oracle on a 1024 x 1024 window of the workload, on the host cores."""
+def cpu_baseline(steps=None, budget_s=12.0):
+    """The FP64 oracle on a 1024 x 1024 window of the workload, on the host cores: as many
+    steps as fill about budget_s seconds (10 to 2000)."""
     import numpy as np
 
     import oracle
@@ -243,7 +244,7 @@ def cpu_baseline(steps=None, budget_s=15.0):
         t0 = time.perf_counter()
         f = oracle.run(p, f, 1)
         one = time.perf_counter() - t0
-        steps = max(1, min(200, int(budget_s / max(one, 1e-6))))
+        steps = max(10, min(2000, int(budget_s / max(one, 1e-6))))
     t0 = time.perf_counter()
     f = oracle.run(p, f, steps)
     dt = time.perf_counter() - t0
