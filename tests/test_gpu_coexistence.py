@@ -2,7 +2,6 @@
 films, run as one batch (Sec. IV A, Fig. 1: a = 0.5, sigma = 0.11, tau_nu = 0.6 and 0.8),
 against the Maxwell rule (Eq. 22) and the mechanical-stability condition (Eq. 21), and the
 batch's FP64 film against the oracle."""
-import numpy as np
 import pytest
 
 import oracle

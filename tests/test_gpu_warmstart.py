@@ -6,7 +6,6 @@ at rest, and settles to the same values.
 
 The training set is the benchmark's: 256 draws over the whole parameter box of the
 batched workload, one film and two droplets each (about 20 s on the GPU)."""
-import numpy as np
 import pytest
 
 from paper_1211_6932_gb300 import workloads as wl

@@ -1,6 +1,5 @@
 """Pins of the discrete pressure tensor oracle (Eq. 18) against closed forms."""
 import numpy as np
-import pytest
 
 import oracle
 from oracle import pressure as op
