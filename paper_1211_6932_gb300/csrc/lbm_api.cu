@@ -1139,17 +1139,17 @@ int lbm_init_droplets(lbm_handle* h, const lbm_droplet* drops, int n, const lbm_
   if ((flags & LBM_WARM_CURVATURE) && lbm_curved_densities(eos, p, kappa, &rin, &rout) != LBM_OK)
     return set_err(b->err, LBM_EINVAL, "no curved-interface densities for these parameters");
   if (!(rin > rout)) return set_err(b->err, LBM_EINVAL, "liquid density not above the vapour's");
-  std::vector<double4> recs(n);
+  std::vector<lbm::DropRec> recs(n);
   for (int k = 0; k < n; ++k)
-    recs[k] = make_double4(drops[k].cx, drops[k].cy, drops[k].radius + p->shift, rin);
+    recs[k] = lbm::DropRec{drops[k].cx, drops[k].cy, drops[k].radius + p->shift, rin};
   const size_t N = (size_t)P.nx * P.ny;
   const bool balanced = (flags & LBM_WARM_BALANCED) != 0;
   double* d_rho = nullptr;
-  double4* d_drops = nullptr;
+  lbm::DropRec* d_drops = nullptr;
   int rc = dev_alloc(b, (void**)&d_rho, (balanced ? 3 : 1) * N * sizeof(double));
-  if (!rc) rc = dev_alloc(b, (void**)&d_drops, n * sizeof(double4));
+  if (!rc) rc = dev_alloc(b, (void**)&d_drops, n * sizeof(lbm::DropRec));
   if (!rc) {
-    cudaError_t e = cudaMemcpyAsync(d_drops, recs.data(), n * sizeof(double4),
+    cudaError_t e = cudaMemcpyAsync(d_drops, recs.data(), n * sizeof(lbm::DropRec),
                                     cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess)
       e = lbm::launch_fill_droplets(d_rho, P.nx, P.ny, d_drops, n, rout, p->width, b->stream);

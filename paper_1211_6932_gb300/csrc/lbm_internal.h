@@ -29,9 +29,15 @@ cudaError_t launch_diag_finalize(const double* part_sum, const float* part_max,
                                  const int* part_bad, const int* item_begin, int n_inst,
                                  double* out, cudaStream_t st);
 
+// One droplet of lbm_init_droplets: centre, radius of the half-density circle, liquid
+// density.
+struct DropRec {
+  double cx, cy, r_half, rho_in;
+};
+
 // Droplet fill of lbm_init_droplets: rho (ny, nx) doubles on the device; drops holds n
-// records (cx, cy, r_half, rho_in) with r_half the radius of the half-density circle.
-cudaError_t launch_fill_droplets(double* rho, int nx, int ny, const double4* drops, int n,
+// records.
+cudaError_t launch_fill_droplets(double* rho, int nx, int ny, const DropRec* drops, int n,
                                  double rho_v, double width, cudaStream_t st);
 
 // u0 = -F / (2 rho) (Eq. 7 force of the density field) for a force-balanced start.

@@ -14,9 +14,9 @@ constexpr int kDropTile = 256;  // droplets staged in shared memory per pass
 // One thread per node: the largest tanh profile over the droplets within reach (8
 // widths beyond the half-density circle), else rho_v.
 __global__ void __launch_bounds__(kFillThreads) fill_droplets_kernel(
-    double* __restrict__ rho, int nx, int ny, const double4* __restrict__ drops, int n,
+    double* __restrict__ rho, int nx, int ny, const DropRec* __restrict__ drops, int n,
     double rho_v, double width) {
-  __shared__ double4 sd[kDropTile];
+  __shared__ DropRec sd[kDropTile];
   const long long N = (long long)nx * ny;
   const long long node = (long long)blockIdx.x * kFillThreads + threadIdx.x;
   const bool live = node < N;
@@ -30,14 +30,14 @@ __global__ void __launch_bounds__(kFillThreads) fill_droplets_kernel(
     __syncthreads();
     if (!live) continue;
     for (int k = 0; k < m; ++k) {
-      const double4 d = sd[k];
-      double dx = fabs((double)x - d.x);
+      const DropRec d = sd[k];
+      double dx = fabs((double)x - d.cx);
       dx = fmin(dx, (double)nx - dx);
-      double dy = fabs((double)y - d.y);
+      double dy = fabs((double)y - d.cy);
       dy = fmin(dy, (double)ny - dy);
-      const double s = sqrt(dx * dx + dy * dy) - d.z;
+      const double s = sqrt(dx * dx + dy * dy) - d.r_half;
       if (s > reach) continue;
-      const double v = 0.5 * (d.w + rho_v) - 0.5 * (d.w - rho_v) * tanh(2.0 * s / width);
+      const double v = 0.5 * (d.rho_in + rho_v) - 0.5 * (d.rho_in - rho_v) * tanh(2.0 * s / width);
       best = fmax(best, v);
     }
   }
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(256) phase_sums_kernel(const S* __restrict__ r
 
 }  // namespace
 
-cudaError_t launch_fill_droplets(double* rho, int nx, int ny, const double4* drops, int n,
+cudaError_t launch_fill_droplets(double* rho, int nx, int ny, const DropRec* drops, int n,
                                  double rho_v, double width, cudaStream_t st) {
   const long long N = (long long)nx * ny;
   const long long blocks = (N + kFillThreads - 1) / kFillThreads;
