@@ -53,6 +53,9 @@ struct Batch {
   size_t dense_elems = 0;
   void* rho_prev = nullptr;
   void* fields[3] = {nullptr, nullptr, nullptr};
+  double* staging = nullptr;  // 3 x (largest instance) doubles: host uploads and downloads
+  size_t staging_elems = 0;
+  int* d_flag = nullptr;      // one int for the initialisation's validity check
   double* d_part_sum = nullptr;
   float* d_part_max = nullptr;
   int* d_part_bad = nullptr;
@@ -177,6 +180,8 @@ void destroy_batch(Batch* b) {
   free_dev(b->d_part_bad);
   free_dev(b->d_diag);
   free_dev(b->d_status);
+  free_dev(b->staging);
+  free_dev(b->d_flag);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   b->stream = nullptr;
@@ -468,6 +473,22 @@ int dev_alloc(Batch* b, void** p, size_t bytes) {
   return LBM_OK;
 }
 
+// Device doubles for 3 fields of the largest instance, kept for the handle's lifetime
+// (host transfers go through it without per-call allocation).
+int ensure_staging(Batch* b) {
+  if (b->staging) return LBM_OK;
+  size_t m = 1;
+  for (const auto& P : b->inst) m = std::max(m, (size_t)P.nx * P.ny);
+  CK(b, cudaMalloc(&b->staging, 3 * m * sizeof(double)));
+  b->staging_elems = m;
+  return LBM_OK;
+}
+
+int ensure_flag(Batch* b) {
+  if (!b->d_flag) CK(b, cudaMalloc(&b->d_flag, sizeof(int)));
+  return LBM_OK;
+}
+
 int init_instance(Batch* b, int i, const double* rho, const double* ux, const double* uy,
                   bool device_ptrs) {
   if (i < 0 || i >= b->n_inst) return set_err(b->err, LBM_EINVAL, "instance %d out of range", i);
@@ -475,14 +496,13 @@ int init_instance(Batch* b, int i, const double* rho, const double* ux, const do
   const InstParams& P = b->inst[i];
   const size_t N = (size_t)P.nx * P.ny;
   const double *dr = rho, *du = ux, *dv = uy;
-  void* tmp = nullptr;
-  int* dbad = nullptr;
-  int rc = LBM_OK;
+  int rc = ensure_flag(b);
+  if (rc) return rc;
+  int* dbad = b->d_flag;
   if (!device_ptrs) {
-    const int nf = 1 + (ux ? 1 : 0) + (uy ? 1 : 0);
-    rc = dev_alloc(b, &tmp, nf * N * sizeof(double));
+    rc = ensure_staging(b);
     if (rc) return rc;
-    double* t = (double*)tmp;
+    double* t = b->staging;
     cudaMemcpyAsync(t, rho, N * sizeof(double), cudaMemcpyHostToDevice, b->stream);
     dr = t;
     t += N;
@@ -496,11 +516,6 @@ int init_instance(Batch* b, int i, const double* rho, const double* ux, const do
       dv = t;
     }
   }
-  rc = dev_alloc(b, (void**)&dbad, sizeof(int));
-  if (rc) {
-    cudaFree(tmp);
-    return rc;
-  }
   cudaMemsetAsync(dbad, 0, sizeof(int), b->stream);
   cudaError_t e;
   if (b->fp64)
@@ -513,8 +528,6 @@ int init_instance(Batch* b, int i, const double* rho, const double* ux, const do
   int bad = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-  cudaFree(tmp);
-  cudaFree(dbad);
   if (e != cudaSuccess)
     return set_err(b->err, LBM_ECUDA, "initialisation failed: %s", cudaGetErrorString(e));
   // The other slab mirrors the state so frozen and active instances agree.
@@ -635,17 +648,20 @@ int moments_host(Batch* b, int i, double* rho, double* ux, double* uy) {
   const InstParams& P = b->inst[i];
   const size_t N = (size_t)P.nx * P.ny;
   double* outs[3] = {rho, ux, uy};
-  std::vector<float> tmp;
+  if (!b->fp64) {
+    rc = ensure_staging(b);
+    if (rc) return rc;
+  }
   for (int k = 0; k < 3; ++k) {
     if (!outs[k]) continue;
     const char* src = (const char*)b->fields[k] + P.dense_off * b->esz;
     if (b->fp64) {
       CK(b, cudaMemcpyAsync(outs[k], src, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
     } else {
-      tmp.resize(N);
-      CK(b, cudaMemcpyAsync(tmp.data(), src, N * sizeof(float), cudaMemcpyDeviceToHost, b->stream));
-      CK(b, cudaStreamSynchronize(b->stream));
-      for (size_t n = 0; n < N; ++n) outs[k][n] = tmp[n];
+      // widen on the device, then one transfer of doubles into the caller's buffer
+      double* w = b->staging + k * b->staging_elems;
+      CK(b, lbm::launch_widen((const float*)src, w, (long long)N, b->stream));
+      CK(b, cudaMemcpyAsync(outs[k], w, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
     }
   }
   CK(b, cudaStreamSynchronize(b->stream));

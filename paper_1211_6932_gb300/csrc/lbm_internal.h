@@ -58,6 +58,9 @@ template <typename S>
 cudaError_t launch_pressure(const S* rho, const InstParams& P, double sigma, double* pxx,
                             double* pyy, double* pxy, cudaStream_t st);
 
+// dst[i] = (double)src[i] for n values.
+cudaError_t launch_widen(const float* src, double* dst, long long n, cudaStream_t st);
+
 // One-block kernel whose bounded mbarrier wait runs out after `polls` polls and sets
 // STATUS_TIMEOUT in *status (lbm_selftest_timeout).
 cudaError_t launch_wait_selftest(int* status, long long polls, cudaStream_t st);

@@ -83,6 +83,21 @@ __global__ void wait_selftest_kernel(int* __restrict__ status, long long polls) 
   if (threadIdx.x == 0 && !mbar_wait_polls(&bar, 0u, polls)) atomicOr(status, STATUS_TIMEOUT);
 }
 
+// float -> double copy on the device (host reads of FP32 fields land as doubles).
+__global__ void __launch_bounds__(256) widen_kernel(const float* __restrict__ src,
+                                                    double* __restrict__ dst, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i];
+}
+
+cudaError_t launch_widen(const float* src, double* dst, long long n, cudaStream_t st) {
+  long long g = (n + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  widen_kernel<<<(int)(g < 1 ? 1 : g), 256, 0, st>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_wait_selftest(int* status, long long polls, cudaStream_t st) {
   wait_selftest_kernel<<<1, 32, 0, st>>>(status, polls);
   return cudaGetLastError();
