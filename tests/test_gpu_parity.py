@@ -61,7 +61,8 @@ def test_fp64_viscosity_modes_and_sigma(visc, sigma):
         assert pairs.rel_err(L.get_populations(), oracle.run(p, f, 60)) <= 60e-12
 
 
-@pytest.mark.parametrize("nt,vec", [(64, 1), (128, 1), (256, 1), (64, 2), (128, 2)])
+@pytest.mark.parametrize("nt,vec", [(64, 1), (128, 1), (256, 1), (32, 2), (64, 2), (96, 2),
+                                    (128, 2)])
 @pytest.mark.parametrize("walls", [False, True])
 def test_fp32_per_step_parity(nt, vec, walls):
     c = pairs.case(131, 70, tr=0.6, sigma=0.114, walls=walls, visc="linear", nu_l=0.05,
@@ -91,6 +92,21 @@ def test_fp32_psi_fp64_option_matches():
         ok, err = fp32_close(L.get_populations(), oracle.run(p, f_in, 1),
                              oracle.fields(p, f_in)["rho"])
         assert ok, err
+
+
+def test_fp64_config1_full_run():
+    """Config 1 in full: the 128^2 droplet (a = 0.25, T = 0.7 T_c, sigma = 0.114, r0 = 30,
+    W = 4, tau = 1) for 5000 steps in FP64 against the oracle: the per-step bound of
+    1e-12 leaves the whole run within 1e-10 relative (measured far below)."""
+    c = pairs.case(128, 128, a=0.25, tr=0.7, sigma=0.114, s=pairs.RATES_C1)
+    p = pairs.oracle_params(c)
+    f = pairs.droplet_state(c, r0=30, W=4.0)
+    ref = oracle.run(p, f, 5000)
+    with pairs.gpu_lattice(c, "fp64") as L:
+        L.set_populations(f)
+        L.step(5000)
+        got = L.get_populations()
+    assert pairs.rel_err(got, ref) <= 1e-10
 
 
 def test_fp32_droplet_run_density_and_coexistence():
@@ -176,8 +192,8 @@ def test_tiling_and_graph_do_not_change_results():
     c = pairs.case(203, 77, tr=0.65, sigma=0.114, visc="step", nu_l=0.04, nu_v=0.3)
     f = pairs.droplet_state(c, vel=0.01)
     outs = {}
-    cfgs = ((64, 2, 0), (64, 2, 5), (64, 2, 77), (64, 2, 1), (128, 2, 9), (128, 1, 0),
-            (64, 1, 33), (256, 1, 7))
+    cfgs = ((64, 2, 0), (64, 2, 5), (64, 2, 77), (64, 2, 1), (128, 2, 9), (128, 2, 16),
+            (32, 2, 11), (96, 2, 24), (96, 2, 3), (128, 1, 0), (64, 1, 33), (256, 1, 7))
     for nt, vec, rows in cfgs:
         with pairs.gpu_lattice(c, "fp32", tile_threads=nt, tile_vec=vec, tile_rows=rows) as L:
             L.set_populations(f)
