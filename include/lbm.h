@@ -76,16 +76,21 @@ typedef struct {
   void* stream;   /* cudaStream_t to queue work on; NULL: a stream the handle owns */
   int device;     /* CUDA device ordinal; -1 (default): the library's current device.
                      Every call on the handle makes this device current first. */
-  int tile_threads; /* threads per CTA of the step kernel; 0 (default): 64 for FP32_DEV,
-                       128 for FP64 */
+  int tile_threads; /* threads per CTA of the step kernel; 0 (default): 128.
+                       LBM_TILE_PER_INSTANCE (FP32_DEV with tile_vec 2 only): each
+                       instance gets the pair-kernel width (32, 64, 96 or 128 threads)
+                       that wastes least of its columns; one launch per width per step */
   int tile_vec;     /* adjacent columns per thread: 1, or 2 (FP32 only: packed float2
                        arithmetic); available (threads, vec) pairs: FP32 (64|128|256, 1),
-                       (64|128, 2); FP64 (64|128, 1).  0 (default): 2 for FP32_DEV, 1 for
-                       FP64.  A CTA owns threads*vec - 4 columns. */
+                       (32|64|96|128, 2); FP64 (64|128, 1).  0 (default): 2 for FP32_DEV,
+                       1 for FP64.  A CTA owns threads*vec - 4 columns. */
   int tile_rows;  /* rows per CTA sweep; 0 (default): sized to fill the GPU */
 } lbm_options;
 
 typedef struct lbm_handle lbm_handle;
+
+/* tile_threads value: a pair-kernel width per instance (see lbm_options.tile_threads). */
+#define LBM_TILE_PER_INSTANCE (-1)
 
 /* Diagnostics of the current state (Eq. 6 fields), accumulated in double precision. */
 typedef struct {
@@ -239,9 +244,10 @@ int lbm_get_tiling(const lbm_handle* h, int* threads, int* vec, int* rows);
 int lbm_set_tiling(lbm_handle* h, int threads, int vec, int rows);
 
 /*
- * Pick the step kernel's tiling by measurement: every available (threads, vec) pair with
- * chunk heights of 8, 16, 32 and 64 rows is timed over `steps` steps (CUDA events on the
- * handle's stream) on a saved copy of the state, which is restored afterwards (state and
+ * Pick the step kernel's tiling by measurement: every available (threads, vec) pair, and
+ * for FP32_DEV LBM_TILE_PER_INSTANCE, with chunk heights of 8, 16, 32 and 64 rows is
+ * timed over `steps` steps, rounded up to even, stepped as lbm_step steps them (graph
+ * replays for each 64; CUDA events on the handle's stream) on a saved copy of the state, which is restored afterwards (state and
  * step count are unchanged).  The fastest is kept.  cache_path (may be NULL) names a text
  * file of earlier choices keyed by precision, lattice sizes and GPU; a hit skips the
  * timing, a miss appends the new choice.  The chosen values are returned through the
@@ -338,8 +344,11 @@ int lbm_batch_active(const lbm_batch* b);
 /* lbm_autotune for a batch (all active instances are stepped together). */
 int lbm_batch_autotune(lbm_batch* b, int steps, const char* cache_path, int* threads,
                        int* vec, int* rows, double* ms_per_step);
-/* Tiling in use by a batch. */
+/* Tiling in use by a batch (threads is LBM_TILE_PER_INSTANCE for per-instance widths). */
 int lbm_batch_get_tiling(const lbm_batch* b, int* threads, int* vec, int* rows);
+/* Step-kernel launches per step of lbm_batch_step (0 when nothing is active; with
+ * LBM_TILE_PER_INSTANCE one per pair-kernel width in use, else 1). */
+int lbm_batch_launches_per_step(const lbm_batch* b);
 
 #ifdef __cplusplus
 }

@@ -16,6 +16,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTA
 LBM_FP64, LBM_FP32_DEV = 0, 1
 LBM_VISC_CONST, LBM_VISC_STEP, LBM_VISC_LINEAR = 0, 1, 2
 LBM_BC_PERIODIC, LBM_BC_WALLS_Y = 0, 1
+LBM_TILE_PER_INSTANCE = -1
 
 
 class lbm_eos(ctypes.Structure):
@@ -107,6 +108,7 @@ SIGNATURES = {
                                    ctypes.POINTER(c_int), ctypes.POINTER(c_int), dptr]),
     "lbm_batch_get_tiling": (c_int, [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                                      ctypes.POINTER(c_int)]),
+    "lbm_batch_launches_per_step": (c_int, [c_void_p]),
     # include/lbm_mlp.h
     "lbm_mlp_create": (c_int, [ctypes.POINTER(c_void_p), fptr, c_int, c_void_p, c_int]),
     "lbm_mlp_destroy": (None, [c_void_p]),

@@ -44,7 +44,7 @@ struct Batch {
   int n_items = 0, cap_items = 0;
   std::vector<WorkItem> all_items;  // every instance, for diagnostics
   WorkItem* d_all_items = nullptr;
-  int n_all = 0;
+  int n_all = 0, cap_all = 0;
   std::vector<int> item_begin;  // per instance, into all_items
   int* d_item_begin = nullptr;
   void* slab[2] = {nullptr, nullptr};
@@ -65,6 +65,16 @@ struct Batch {
   bool own_stream = false;
   cudaStream_t cap_stream = nullptr;
   int nt = 0, vec = 0, rows_req = 0, rows = 0;  // threads and columns/thread per CTA, rows per sweep
+  // Step launches: group g runs items [grp_begin[g], grp_begin[g+1]) with grp_nt[g]
+  // threads.  One group, unless nt == LBM_TILE_PER_INSTANCE: then one per pair-kernel
+  // width, each instance in the group of the width inst_nt[i].
+  static constexpr int kMaxGroups = 4;
+  std::vector<int> inst_nt;
+  int n_groups = 0;
+  int grp_nt[kMaxGroups] = {0, 0, 0, 0};
+  int grp_begin[kMaxGroups + 1] = {0, 0, 0, 0, 0};
+  cudaStream_t grp_stream[kMaxGroups - 1] = {nullptr, nullptr, nullptr};  // graph branches
+  cudaEvent_t grp_fork = nullptr, grp_join[kMaxGroups - 1] = {nullptr, nullptr, nullptr};
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   std::string err;
   int sms = 0;
@@ -183,50 +193,113 @@ void destroy_batch(Batch* b) {
   free_dev(b->staging);
   free_dev(b->d_flag);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  for (auto& st : b->grp_stream)
+    if (st) cudaStreamDestroy(st);
+  for (auto& ev : b->grp_join)
+    if (ev) cudaEventDestroy(ev);
+  if (b->grp_fork) cudaEventDestroy(b->grp_fork);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   b->stream = nullptr;
 }
 
-int sweep_occupancy(const Batch* b) {
-  return b->fp64 ? lbm::sweep_occupancy<double>(b->nt, b->vec)
-                 : lbm::sweep_occupancy<float>(b->nt, b->vec);
+bool per_instance(const Batch* b) { return b->nt == LBM_TILE_PER_INSTANCE; }
+
+// Whether a tiling request is available for a precision.
+bool tiling_ok(bool fp64, int nt, int vec) {
+  if (nt == LBM_TILE_PER_INSTANCE) return !fp64 && vec == 2;
+  return lbm::cfg_supported(fp64, nt, vec);
 }
+
+// Threads per CTA of the moments/diagnostics pass (one uniform tiling over all instances).
+int mom_nt(const Batch* b) { return per_instance(b) ? 128 : b->nt; }
+
+constexpr int kPairThreads[Batch::kMaxGroups] = {32, 64, 96, 128};
+
+// Pair-kernel width for an instance of nx columns: the fewest launched columns, where a
+// strip of 2 nt - 4 owned columns costs its 2 nt computed columns plus a fixed share of
+// about 12 columns per row (the halo columns it loads and the per-row barrier and wait
+// overhead; fitted to single-field step times at 64 and 128 threads, which cost
+// 1.116 (2 nt) + 14 column-equivalents).  Ties go to the wider CTA.
+int pair_threads_for(int nx) {
+  int best = 128;
+  long long best_cost = -1;
+  for (int g = Batch::kMaxGroups - 1; g >= 0; --g) {
+    const int nt = kPairThreads[g];
+    const int W = lbm::strip_width(nt, 2);
+    const long long cost = (long long)((nx + W - 1) / W) * (2 * nt + 12);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = nt;
+    }
+  }
+  return best;
+}
+
+// Step-kernel threads per CTA of instance i under the current tiling.
+int step_nt(const Batch* b, int i) { return per_instance(b) ? b->inst_nt[i] : b->nt; }
 
 // Rows per CTA sweep: about six waves of resident CTAs (measured best on 4096^2: fewer
 // rows cost halo re-reads and row-loop start-up, more rows leave SMs idle in the tail),
-// clamped to [8, 64].
+// clamped to [8, 64].  With per-instance widths each strip row counts as 1 / (resident
+// CTAs of its width) of an SM.
 int default_rows(const Batch* b) {
-  const int W = lbm::strip_width(b->nt, b->vec);
-  long long strip_rows = 0;
+  double sm_rows = 0.0;
   for (int i = 0; i < b->n_inst; ++i)
-    if (b->active[i]) strip_rows += (long long)((b->inst[i].nx + W - 1) / W) * b->inst[i].ny;
-  const long long target = (long long)std::max(b->sms, 1) * sweep_occupancy(b) * 6;
-  long long r = (strip_rows + target - 1) / std::max(target, 1LL);
+    if (b->active[i]) {
+      const int nt = step_nt(b, i);
+      const int W = lbm::strip_width(nt, b->vec);
+      const int occ = b->fp64 ? lbm::sweep_occupancy<double>(nt, b->vec)
+                              : lbm::sweep_occupancy<float>(nt, b->vec);
+      sm_rows += (double)((b->inst[i].nx + W - 1) / W) * b->inst[i].ny / std::max(occ, 1);
+    }
+  const double target = (double)std::max(b->sms, 1) * 6.0;
+  const long long r = (long long)std::ceil(sm_rows / target);
   return (int)std::min<long long>(64, std::max<long long>(8, r));
 }
 
-void make_items(const Batch* b, bool only_active, int rows, std::vector<WorkItem>& out,
-                std::vector<int>* begin) {
-  const int W = lbm::strip_width(b->nt, b->vec);  // owned columns per CTA
-  out.clear();
-  if (begin) begin->assign(1, 0);
-  for (int i = 0; i < b->n_inst; ++i) {
-    if (!only_active || b->active[i]) {
-      const InstParams& P = b->inst[i];
-      const int strips = (P.nx + W - 1) / W;
-      const int chunks = (P.ny + rows - 1) / rows;
-      for (int c = 0; c < chunks; ++c)
-        for (int s = 0; s < strips; ++s) {
-          WorkItem w{};
-          w.inst = i;
-          w.x0 = s * W;
-          w.y0 = c * rows;
-          w.y1 = std::min(P.ny, (c + 1) * rows);
-          w.dir = (c & 1) ? -1 : 1;
-          out.push_back(w);
-        }
+// Work items of instance i: strips of W owned columns by chunks of `rows` rows.
+void append_items(const InstParams& P, int i, int W, int rows, std::vector<WorkItem>& out) {
+  const int strips = (P.nx + W - 1) / W;
+  const int chunks = (P.ny + rows - 1) / rows;
+  for (int c = 0; c < chunks; ++c)
+    for (int s = 0; s < strips; ++s) {
+      WorkItem w{};
+      w.inst = i;
+      w.x0 = s * W;
+      w.y0 = c * rows;
+      w.y1 = std::min(P.ny, (c + 1) * rows);
+      w.dir = (c & 1) ? -1 : 1;
+      out.push_back(w);
     }
-    if (begin) begin->push_back((int)out.size());
+}
+
+// Step items of the active instances, grouped by kernel width (b->items, b->grp_*).
+void make_step_items(Batch* b) {
+  b->items.clear();
+  b->n_groups = 0;
+  b->grp_begin[0] = 0;
+  for (int g = 0; g < Batch::kMaxGroups; ++g) {
+    const int nt = per_instance(b) ? kPairThreads[g] : b->nt;
+    const size_t before = b->items.size();
+    for (int i = 0; i < b->n_inst; ++i)
+      if (b->active[i] && step_nt(b, i) == nt)
+        append_items(b->inst[i], i, lbm::strip_width(nt, b->vec), b->rows, b->items);
+    if (b->items.size() > before) {
+      b->grp_nt[b->n_groups] = nt;
+      b->grp_begin[++b->n_groups] = (int)b->items.size();
+    }
+    if (!per_instance(b)) break;
+  }
+}
+
+// Items of every instance for the moments/diagnostics pass, with per-instance ranges.
+void make_all_items(const Batch* b, std::vector<WorkItem>& out, std::vector<int>& begin) {
+  const int W = lbm::strip_width(mom_nt(b), b->vec);
+  out.clear();
+  begin.assign(1, 0);
+  for (int i = 0; i < b->n_inst; ++i) {
+    append_items(b->inst[i], i, W, b->rows, out);
+    begin.push_back((int)out.size());
   }
 }
 
@@ -234,22 +307,33 @@ void make_items(const Batch* b, bool only_active, int rows, std::vector<WorkItem
 int rebuild_items(Batch* b) {
   drop_graphs(b);
   if (b->stream) CK(b, cudaStreamSynchronize(b->stream));
+  if (per_instance(b)) {
+    b->inst_nt.resize(b->n_inst);
+    for (int i = 0; i < b->n_inst; ++i) b->inst_nt[i] = pair_threads_for(b->inst[i].nx);
+  }
   b->rows = b->rows_req > 0 ? b->rows_req : default_rows(b);
-  make_items(b, true, b->rows, b->items, nullptr);
-  make_items(b, false, b->rows, b->all_items, &b->item_begin);
+  make_step_items(b);
+  make_all_items(b, b->all_items, b->item_begin);
   b->n_items = (int)b->items.size();
   const int n_all = (int)b->all_items.size();
-  if (n_all > b->n_all || !b->d_all_items) {
+  if (n_all > b->cap_all || !b->d_all_items) {
     free_dev(b->d_all_items);
-    free_dev(b->d_items);
     free_dev(b->d_part_sum);
     free_dev(b->d_part_max);
     free_dev(b->d_part_bad);
+    b->cap_all = 0;
     CK(b, cudaMalloc(&b->d_all_items, sizeof(WorkItem) * std::max(n_all, 1)));
-    CK(b, cudaMalloc(&b->d_items, sizeof(WorkItem) * std::max(n_all, 1)));
     CK(b, cudaMalloc(&b->d_part_sum, sizeof(double) * 3 * std::max(n_all, 1)));
     CK(b, cudaMalloc(&b->d_part_max, sizeof(float) * 2 * std::max(n_all, 1)));
     CK(b, cudaMalloc(&b->d_part_bad, sizeof(int) * std::max(n_all, 1)));
+    b->cap_all = n_all;
+  }
+  // Step items can outnumber the moments items (narrower strips under per-instance widths).
+  if (b->n_items > b->cap_items || !b->d_items) {
+    free_dev(b->d_items);
+    b->cap_items = 0;
+    CK(b, cudaMalloc(&b->d_items, sizeof(WorkItem) * std::max(b->n_items, 1)));
+    b->cap_items = b->n_items;
   }
   b->n_all = n_all;
   CK(b, cudaMemcpy(b->d_all_items, b->all_items.data(), sizeof(WorkItem) * n_all,
@@ -327,7 +411,7 @@ int create_batch(Batch* b, int n, const lbm_instance* in, bool fp64, int psi_fp6
                  void* stream, int device, int nt, int vec, int rows) {
   if (n < 1 || !in) return set_err(b->err, LBM_EINVAL, "need at least one instance");
   const int nt_ = nt ? nt : default_threads(fp64), vec_ = vec ? vec : default_vec(fp64);
-  if (!lbm::cfg_supported(fp64, nt_, vec_))
+  if (!tiling_ok(fp64, nt_, vec_))
     return set_err(b->err, LBM_EINVAL,
                    "tile_threads %d with tile_vec %d is not available for this precision", nt_,
                    vec_);
@@ -386,34 +470,93 @@ int create_batch(Batch* b, int n, const lbm_instance* in, bool fp64, int psi_fp6
   return rebuild_items(b);
 }
 
-int launch_step(Batch* b, cudaStream_t st) {
-  const int c = b->cur;
+// One step of the instances of launch group g, from slab c into slab c ^ 1.
+int launch_group(Batch* b, int g, int c, cudaStream_t st) {
+  const WorkItem* items = b->d_items + b->grp_begin[g];
+  const int n = b->grp_begin[g + 1] - b->grp_begin[g];
   cudaError_t e;
   if (b->fp64) {
     MomArgs<double> mo{};
-    e = lbm::launch_sweep<double>(b->nt, b->vec, lbm::MODE_STEP, (const double*)b->slab[c],
-                                  (double*)b->slab[c ^ 1], b->d_inst, b->d_items, b->n_items,
-                                  mo, b->d_status, st);
+    e = lbm::launch_sweep<double>(b->grp_nt[g], b->vec, lbm::MODE_STEP,
+                                  (const double*)b->slab[c], (double*)b->slab[c ^ 1], b->d_inst,
+                                  items, n, mo, b->d_status, st);
   } else {
     MomArgs<float> mo{};
-    e = lbm::launch_sweep<float>(b->nt, b->vec, lbm::MODE_STEP, (const float*)b->slab[c],
-                                 (float*)b->slab[c ^ 1], b->d_inst, b->d_items, b->n_items,
-                                 mo, b->d_status, st);
+    e = lbm::launch_sweep<float>(b->grp_nt[g], b->vec, lbm::MODE_STEP,
+                                 (const float*)b->slab[c], (float*)b->slab[c ^ 1], b->d_inst,
+                                 items, n, mo, b->d_status, st);
   }
   if (e != cudaSuccess)
     return set_err(b->err, LBM_ECUDA, "step kernel launch failed: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+// One step of every active instance: the launch groups one after another on st.
+int launch_step(Batch* b, cudaStream_t st) {
+  for (int g = 0; g < b->n_groups; ++g) {
+    int rc = launch_group(b, g, b->cur, st);
+    if (rc) return rc;
+  }
   b->cur ^= 1;
   return LBM_OK;
 }
 
-// Capture kGraphSteps consecutive steps that start from slab `start`.
+// Streams and events that fork the launch groups into parallel graph branches.
+int ensure_branches(Batch* b) {
+  for (int g = 0; g + 1 < b->n_groups; ++g) {
+    if (!b->grp_stream[g])
+      CK(b, cudaStreamCreateWithFlags(&b->grp_stream[g], cudaStreamNonBlocking));
+    if (!b->grp_join[g])
+      CK(b, cudaEventCreateWithFlags(&b->grp_join[g], cudaEventDisableTiming));
+  }
+  if (!b->grp_fork) CK(b, cudaEventCreateWithFlags(&b->grp_fork, cudaEventDisableTiming));
+  return LBM_OK;
+}
+
+// n steps queued on st.  With several launch groups (which touch disjoint instances) each
+// group runs its chain of n launches on its own stream, forked from st and joined back,
+// so the groups overlap on the GPU and fill each other's tails.  b->cur is unchanged.
+int queue_steps(Batch* b, int n, cudaStream_t st) {
+  const int start = b->cur;
+  if (b->n_groups <= 1) {
+    int rc = LBM_OK;
+    for (int k = 0; k < n && rc == LBM_OK; ++k) rc = launch_step(b, st);
+    b->cur = start;
+    return rc;
+  }
+  int rc = ensure_branches(b);
+  if (rc) return rc;
+  cudaError_t e = cudaEventRecord(b->grp_fork, st);
+  for (int k = 0; k + 1 < b->n_groups && e == cudaSuccess; ++k)
+    e = cudaStreamWaitEvent(b->grp_stream[k], b->grp_fork, 0);
+  if (e != cudaSuccess)
+    return set_err(b->err, LBM_ECUDA, "stream fork failed: %s", cudaGetErrorString(e));
+  for (int gi = 0; gi < b->n_groups && rc == LBM_OK; ++gi) {
+    cudaStream_t sg = gi == 0 ? st : b->grp_stream[gi - 1];
+    for (int k = 0; k < n && rc == LBM_OK; ++k) rc = launch_group(b, gi, start ^ (k & 1), sg);
+  }
+  // Join every branch that was forked, even after a failed launch.
+  for (int k = 0; k + 1 < b->n_groups; ++k) {
+    e = cudaEventRecord(b->grp_join[k], b->grp_stream[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->grp_join[k], 0);
+    if (e != cudaSuccess && rc == LBM_OK)
+      rc = set_err(b->err, LBM_ECUDA, "stream join failed: %s", cudaGetErrorString(e));
+  }
+  return rc;
+}
+
+// Capture kGraphSteps consecutive steps that start from slab `start` (one branch per
+// launch group).
 int capture_graph(Batch* b, int start) {
   const int saved = b->cur;
+  if (b->n_groups > 1) {
+    int rc = ensure_branches(b);  // created outside the capture
+    if (rc) return rc;
+  }
   b->cur = start;
   cudaGraph_t g = nullptr;
   CK(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-  int rc = LBM_OK;
-  for (int k = 0; k < kGraphSteps && rc == LBM_OK; ++k) rc = launch_step(b, b->cap_stream);
+  int rc = queue_steps(b, kGraphSteps, b->cap_stream);
   cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
   b->cur = saved;
   if (rc) {
@@ -444,9 +587,10 @@ int do_steps(Batch* b, long long n) {
       CK(b, cudaGraphLaunch(b->graph[b->cur], b->stream));
       n -= kGraphSteps;
     } else {
-      int rc = launch_step(b, b->stream);
+      int rc = queue_steps(b, (int)n, b->stream);
       if (rc) return rc;
-      --n;
+      b->cur ^= (int)(n & 1);
+      n = 0;
     }
   }
   for (int i = 0; i < b->n_inst; ++i)
@@ -604,7 +748,7 @@ int moments_pass(Batch* b, const WorkItem* d_items, int n, MomArgs<S> mo) {
   mo.part_sum = b->d_part_sum;
   mo.part_max = b->d_part_max;
   mo.part_bad = b->d_part_bad;
-  cudaError_t e = lbm::launch_sweep<S>(b->nt, b->vec, lbm::MODE_MOMENTS, (const S*)b->slab[b->cur],
+  cudaError_t e = lbm::launch_sweep<S>(mom_nt(b), b->vec, lbm::MODE_MOMENTS, (const S*)b->slab[b->cur],
                                        nullptr, b->d_inst, d_items, n, mo, b->d_status,
                                        b->stream);
   if (e != cudaSuccess)
@@ -812,7 +956,7 @@ void cache_store(const char* path, const std::string& key, const TileChoice& c) 
 }
 
 int apply_tiling(Batch* b, int nt, int vec, int rows) {
-  if (!lbm::cfg_supported(b->fp64, nt, vec))
+  if (!tiling_ok(b->fp64, nt, vec))
     return set_err(b->err, LBM_EINVAL, "tiling %d threads x %d columns not available", nt, vec);
   b->nt = nt;
   b->vec = vec;
@@ -833,7 +977,7 @@ int autotune(Batch* b, int steps, const char* cache_path, TileChoice& best) {
   }
   const std::string key = tune_key(b);
   TileChoice hit;
-  if (cache_lookup(cache_path, key, hit) && lbm::cfg_supported(b->fp64, hit.nt, hit.vec)) {
+  if (cache_lookup(cache_path, key, hit) && tiling_ok(b->fp64, hit.nt, hit.vec)) {
     best = hit;
     return apply_tiling(b, hit.nt, hit.vec, hit.rows);
   }
@@ -848,27 +992,31 @@ int autotune(Batch* b, int steps, const char* cache_path, TileChoice& best) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CK(b, cudaEventCreate(&e0));
   CK(b, cudaEventCreate(&e1));
-  const int nts[] = {32, 64, 96, 128, 256};
+  const int nts[] = {32, 64, 96, 128, 256, LBM_TILE_PER_INSTANCE};
   const int vecs[] = {1, 2};
   const int rows_c[] = {8, 16, 32, 64};
   best = TileChoice();
   int rc = LBM_OK;
   for (int vec : vecs)
     for (int nt : nts) {
-      if (!lbm::cfg_supported(b->fp64, nt, vec)) continue;
+      if (!tiling_ok(b->fp64, nt, vec)) continue;
       for (int rows : rows_c) {
         rc = apply_tiling(b, nt, vec, rows);
         if (rc) break;
-        for (int k = 0; k < 2 && rc == LBM_OK; ++k) rc = launch_step(b, b->stream);  // warm
+        // Timed as stepping runs (graph replays for each kGraphSteps); an even count
+        // returns to the same slab, so the warm-up run captures the graph the timed run
+        // replays.
+        const int n_t = steps + (steps & 1);
+        rc = do_steps(b, n_t);  // warm-up
         if (rc) break;
         CK(b, cudaEventRecord(e0, b->stream));
-        for (int k = 0; k < steps && rc == LBM_OK; ++k) rc = launch_step(b, b->stream);
+        rc = do_steps(b, n_t);
         if (rc) break;
         CK(b, cudaEventRecord(e1, b->stream));
         CK(b, cudaEventSynchronize(e1));
         float ms = 0.f;
         CK(b, cudaEventElapsedTime(&ms, e0, e1));
-        const double per = ms / steps;
+        const double per = ms / n_t;
         if (best.ms < 0 || per < best.ms) {
           best.nt = nt;
           best.vec = vec;
@@ -935,7 +1083,7 @@ int noalloc_diag_pass(Batch* b, double* part_sum, float* part_max, int* part_bad
   mo.part_max = part_max;
   mo.part_bad = part_bad;
   mo.flags = lbm::MOM_DIAG;  // no fields, no reference density
-  cudaError_t e = lbm::launch_sweep<S>(b->nt, b->vec, lbm::MODE_MOMENTS,
+  cudaError_t e = lbm::launch_sweep<S>(mom_nt(b), b->vec, lbm::MODE_MOMENTS,
                                        (const S*)b->slab[b->cur], nullptr, b->d_inst,
                                        b->d_all_items, b->n_all, mo, b->d_status, b->stream);
   if (e != cudaSuccess)
@@ -1280,7 +1428,7 @@ int lbm_set_tiling(lbm_handle* h, int threads, int vec, int rows) {
   Batch* b = &h->b;
   const int nt_ = threads ? threads : default_threads(b->fp64);
   const int vec_ = vec ? vec : default_vec(b->fp64);
-  if (!lbm::cfg_supported(b->fp64, nt_, vec_))
+  if (!tiling_ok(b->fp64, nt_, vec_))
     return set_err(b->err, LBM_EINVAL,
                    "tile_threads %d with tile_vec %d is not available for this precision", nt_,
                    vec_);
@@ -1473,6 +1621,11 @@ int lbm_batch_get_tiling(const lbm_batch* b, int* threads, int* vec, int* rows) 
   if (vec) *vec = b->b.vec;
   if (rows) *rows = b->b.rows;
   return LBM_OK;
+}
+
+int lbm_batch_launches_per_step(const lbm_batch* b) {
+  if (!b) return LBM_EINVAL;
+  return b->b.n_items > 0 ? b->b.n_groups : 0;
 }
 
 int lbm_batch_run_to_equilibrium(lbm_batch* bb, double tol, int check_every,

@@ -801,6 +801,13 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
   const int xend = min(x0 + WO, nx);
   const bool owner = tid >= 1 && tid <= NT - 2 && xa < xend;
   const int n_bulk = ((xend - x0) / 4) * 4;  // columns written by the bulk store
+  // Ghost columns (periodic copies at -2, -1, nx, nx+1).  For even nx >= 4 the owners of
+  // the pairs (0, 1) and (nx-2, nx-1) mirror them as pairs to (nx, nx+1) and (-2, -1);
+  // every other case (odd nx, nx < 4) takes the general per-column path.
+  const bool ghost_pairs = (nx & 1) == 0 && nx >= 4;
+  constexpr int NO_GHOST = -(1 << 30);
+  const int gpair = !ghost_pairs ? NO_GHOST : xa == 0 ? nx : xa == nx - 2 ? -2 : NO_GHOST;
+  const bool ghost_slow = !ghost_pairs && (xa < 2 || xa + 1 >= nx - 2);
   const int dir = it.dir < 0 ? -1 : 1;
   const int y0 = it.y0, y1 = it.y1;
   const int nload = y1 - y0 + 4;
@@ -964,9 +971,16 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
 #pragma unroll
           for (int q = 0; q < Q; ++q)
             *reinterpret_cast<float2*>(dst + (long long)q * plane + xa) = h[q];
+          if (gpair != NO_GHOST) {
+            // the mirrored pair starts at an even column too (nx even)
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+              *reinterpret_cast<float2*>(dst + (long long)q * plane + gpair) = h[q];
+          }
         }
         const bool tail = ST ? c0 + 2 > n_bulk : xa + 1 >= xend;
-        if (tail || xa < 2 || xa + 1 >= nx - 2) {
+        const bool ghost_here = ST ? (xa < 2 || xa + 1 >= nx - 2) : ghost_slow;
+        if (tail || ghost_here) {
           // Columns not covered above (past the last full group of four when staged, the
           // odd last column otherwise), and the ghost copies -2, -1, nx, nx+1 of the
           // columns they mirror, are written directly.
@@ -981,7 +995,7 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
 #pragma unroll
               for (int q = 0; q < Q; ++q) dst[(long long)q * plane + x] = v[q];
             }
-            if (x < 2 || x >= nx - 2) {
+            if ((ST || !ghost_pairs) && (x < 2 || x >= nx - 2)) {
               auto put = [&](int g) {
                 if (wrapi(g, nx) == x) {
 #pragma unroll

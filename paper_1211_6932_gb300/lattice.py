@@ -10,6 +10,7 @@ from . import _lib as C
 _PREC = {"fp64": C.LBM_FP64, "fp32": C.LBM_FP32_DEV, "fp32_dev": C.LBM_FP32_DEV}
 _VISC = {None: -1, "const": C.LBM_VISC_CONST, "step": C.LBM_VISC_STEP,
          "linear": C.LBM_VISC_LINEAR}
+TILE_PER_INSTANCE = C.LBM_TILE_PER_INSTANCE  # tile_threads: a kernel width per instance
 _BC = {"periodic": C.LBM_BC_PERIODIC, "walls": C.LBM_BC_WALLS_Y, "walls_y": C.LBM_BC_WALLS_Y}
 
 
@@ -420,7 +421,13 @@ class Batch:
 
     @property
     def tiling(self):
+        """(threads per CTA or TILE_PER_INSTANCE, columns per thread, rows per sweep)."""
         t, v, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         self._check(self._L.lbm_batch_get_tiling(self._h, ctypes.byref(t), ctypes.byref(v),
                                                  ctypes.byref(r)))
         return t.value, v.value, r.value
+
+    @property
+    def launches_per_step(self):
+        """Step-kernel launches per step (one per pair-kernel width in use)."""
+        return self._check(self._L.lbm_batch_launches_per_step(self._h))

@@ -70,14 +70,47 @@ def test_fp32_batch_equals_single_lattices_bitwise():
     b.close()
 
 
-def test_run_to_equilibrium_freezes_converged_instances():
+def test_per_instance_widths_equal_uniform_tiling_bitwise():
+    """Per-instance kernel widths (one launch per width, graph branches per width) give
+    the populations and diagnostics of the uniform tiling bit for bit, through graph
+    replays (64 steps) and single launches."""
+    from paper_1211_6932_gb300 import Batch
+    from paper_1211_6932_gb300.lattice import TILE_PER_INSTANCE
+    cs = CASES + [pairs.case(400, 40, a=0.25, tr=0.75, sigma=0.114),
+                  pairs.case(220, 36, a=0.5, tr=0.8, sigma=0.11, walls=True)]
+    fields = [start_fields(c, 30 + i) for i, c in enumerate(cs)]
+    out = []
+    for threads in (0, TILE_PER_INSTANCE):
+        b = Batch([instance(c) for c in cs], precision="fp32", tile_threads=threads)
+        for i, fl in enumerate(fields):
+            b.init_fields(i, *fl)
+        b.step(70)
+        # widths 32 (nx 5, 400), 64 (70, 64), 96 (130, 257) and 128 (220)
+        assert b.launches_per_step == (1 if threads == 0 else 4)
+        pops = [b.get_populations(i) for i in range(len(cs))]
+        diags = b.diagnostics()
+        b.step(3)
+        out.append((pops, diags, [b.get_populations(i) for i in range(len(cs))]))
+        assert b.tiling[0] == (threads or 128)
+        b.close()
+    (p0, d0, q0), (p1, d1, q1) = out
+    for i in range(len(cs)):
+        assert np.array_equal(p0[i], p1[i]), i
+        assert np.array_equal(q0[i], q1[i]), i
+        for k in ("mass", "mom_x", "mom_y", "max_u", "nonfinite"):
+            assert d0[i][k] == d1[i][k], (i, k)
+
+
+@pytest.mark.parametrize("threads", [0, -1])
+def test_run_to_equilibrium_freezes_converged_instances(threads):
     """Flat films converge; a converged instance is no longer stepped (its state and step
-    count stay fixed) while the others continue."""
+    count stay fixed) while the others continue (uniform and per-instance widths: the
+    launch groups are rebuilt at each retirement)."""
     from paper_1211_6932_gb300 import Batch
     cs = [pairs.case(3, 64, a=0.5, tr=0.85, sigma=0.11),
           pairs.case(4, 96, a=0.25, tr=0.8, sigma=0.114),
           pairs.case(130, 67, a=0.5, tr=0.8, sigma=0.11)]
-    b = Batch([instance(c) for c in cs], precision="fp32")
+    b = Batch([instance(c) for c in cs], precision="fp32", tile_threads=threads)
     for i, c in enumerate(cs):
         rl, rv = pairs.maxwell(c)
         if c["nx"] <= 4:
@@ -90,6 +123,7 @@ def test_run_to_equilibrium_freezes_converged_instances():
     assert (steps > 0).all() and (steps % 100 == 0).all()
     frozen = [b.get_populations(i) for i in range(3)]
     b.step(50)  # nothing is active any more
+    assert b.launches_per_step == 0
     for i in range(3):
         assert np.array_equal(b.get_populations(i), frozen[i])
     d = b.diagnostics()
@@ -148,7 +182,8 @@ def test_autotune_keeps_state_and_uses_cache(tmp_path):
         L.step(3)
         before = L.get_populations()
         t, v, r, ms = L.autotune(steps=6, cache=cache)
-        assert (t, v) in ((64, 1), (128, 1), (256, 1), (32, 2), (64, 2), (96, 2), (128, 2))
+        assert (t, v) in ((64, 1), (128, 1), (256, 1), (32, 2), (64, 2), (96, 2), (128, 2),
+                          (-1, 2))
         assert r in (8, 16, 32, 64)
         assert ms > 0 and L.tiling == (t, v, r)
         assert L.step_count == 3
