@@ -994,7 +994,9 @@ int autotune(Batch* b, int steps, const char* cache_path, TileChoice& best) {
   CK(b, cudaEventCreate(&e1));
   const int nts[] = {32, 64, 96, 128, 256, LBM_TILE_PER_INSTANCE};
   const int vecs[] = {1, 2};
-  const int rows_c[] = {8, 16, 32, 64};
+  // Chunk heights: the best one depends on how the CTA count falls into waves of resident
+  // CTAs, which moves the step time by several per cent between neighbouring heights.
+  const int rows_c[] = {8, 12, 16, 20, 24, 28, 32, 40, 48, 64};
   best = TileChoice();
   int rc = LBM_OK;
   for (int vec : vecs)
@@ -1009,14 +1011,18 @@ int autotune(Batch* b, int steps, const char* cache_path, TileChoice& best) {
         const int n_t = steps + (steps & 1);
         rc = do_steps(b, n_t);  // warm-up
         if (rc) break;
-        CK(b, cudaEventRecord(e0, b->stream));
-        rc = do_steps(b, n_t);
+        double per = -1.0;  // the better of two timed runs
+        for (int rep = 0; rep < 2 && rc == LBM_OK; ++rep) {
+          CK(b, cudaEventRecord(e0, b->stream));
+          rc = do_steps(b, n_t);
+          if (rc) break;
+          CK(b, cudaEventRecord(e1, b->stream));
+          CK(b, cudaEventSynchronize(e1));
+          float ms = 0.f;
+          CK(b, cudaEventElapsedTime(&ms, e0, e1));
+          if (per < 0 || ms / n_t < per) per = ms / n_t;
+        }
         if (rc) break;
-        CK(b, cudaEventRecord(e1, b->stream));
-        CK(b, cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CK(b, cudaEventElapsedTime(&ms, e0, e1));
-        const double per = ms / n_t;
         if (best.ms < 0 || per < best.ms) {
           best.nt = nt;
           best.vec = vec;
