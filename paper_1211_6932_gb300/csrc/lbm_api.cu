@@ -215,18 +215,19 @@ int mom_nt(const Batch* b) { return per_instance(b) ? 128 : b->nt; }
 
 constexpr int kPairThreads[Batch::kMaxGroups] = {32, 64, 96, 128};
 
-// Pair-kernel width for an instance of nx columns: the fewest launched columns, where a
-// strip of 2 nt - 4 owned columns costs its 2 nt computed columns plus a fixed share of
-// about 12 columns per row (the halo columns it loads and the per-row barrier and wait
-// overhead; fitted to single-field step times at 64 and 128 threads, which cost
-// 1.116 (2 nt) + 14 column-equivalents).  Ties go to the wider CTA.
+// Pair-kernel width for an instance of nx columns: the least strip time, where a strip row
+// of 2 nt - 4 owned columns costs its 2 nt computed columns plus a fixed 57
+// column-equivalents (the per-row work that does not scale with width: copy issue,
+// barrier, halo columns, the instance's ghost columns; fitted to batches of equal
+// instances that fill their strips exactly, 60, 124 and 252 columns wide, at 45.9, 64.1
+// and 74.4 GLUPS).  Ties go to the wider CTA.
 int pair_threads_for(int nx) {
   int best = 128;
   long long best_cost = -1;
   for (int g = Batch::kMaxGroups - 1; g >= 0; --g) {
     const int nt = kPairThreads[g];
     const int W = lbm::strip_width(nt, 2);
-    const long long cost = (long long)((nx + W - 1) / W) * (2 * nt + 12);
+    const long long cost = (long long)((nx + W - 1) / W) * (2 * nt + 57);
     if (best_cost < 0 || cost < best_cost) {
       best_cost = cost;
       best = nt;
@@ -983,27 +984,37 @@ int autotune(Batch* b, int steps, const char* cache_path, TileChoice& best) {
   }
   if (b->n_items == 0) return set_err(b->err, LBM_ESTATE, "no active instance to tune on");
   // Save the state (both slabs agree for frozen instances; the current one for the rest).
+  // Errors below are recorded in rc and the loop left, so the copy and the events are
+  // always released and the state always restored.
   void* backup = nullptr;
   const size_t bytes = b->slab_elems * b->esz;
   CK(b, cudaMalloc(&backup, bytes));
-  CK(b, cudaMemcpyAsync(backup, b->slab[b->cur], bytes, cudaMemcpyDeviceToDevice, b->stream));
+  int rc = LBM_OK;
+  auto cu = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && rc == LBM_OK)
+      rc = set_err(b->err, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA,
+                   "%s failed: %s", what, cudaGetErrorString(e));
+    return rc == LBM_OK;
+  };
   const int saved_cur = b->cur;
   const std::vector<long long> saved_steps = b->steps;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  CK(b, cudaEventCreate(&e0));
-  CK(b, cudaEventCreate(&e1));
+  const bool saved =
+      cu(cudaMemcpyAsync(backup, b->slab[b->cur], bytes, cudaMemcpyDeviceToDevice, b->stream),
+         "state backup");  // nothing is stepped unless the copy was queued
+  cu(cudaEventCreate(&e0), "cudaEventCreate");
+  cu(cudaEventCreate(&e1), "cudaEventCreate");
   const int nts[] = {32, 64, 96, 128, 256, LBM_TILE_PER_INSTANCE};
   const int vecs[] = {1, 2};
   // Chunk heights: the best one depends on how the CTA count falls into waves of resident
   // CTAs, which moves the step time by several per cent between neighbouring heights.
   const int rows_c[] = {8, 12, 16, 20, 24, 28, 32, 40, 48, 64};
   best = TileChoice();
-  int rc = LBM_OK;
-  for (int vec : vecs)
+  for (int vec : vecs) {
     for (int nt : nts) {
       if (!tiling_ok(b->fp64, nt, vec)) continue;
       for (int rows : rows_c) {
-        rc = apply_tiling(b, nt, vec, rows);
+        if (rc == LBM_OK) rc = apply_tiling(b, nt, vec, rows);
         if (rc) break;
         // Timed as stepping runs (graph replays for each kGraphSteps); an even count
         // returns to the same slab, so the warm-up run captures the graph the timed run
@@ -1012,14 +1023,14 @@ int autotune(Batch* b, int steps, const char* cache_path, TileChoice& best) {
         rc = do_steps(b, n_t);  // warm-up
         if (rc) break;
         double per = -1.0;  // the better of two timed runs
-        for (int rep = 0; rep < 2 && rc == LBM_OK; ++rep) {
-          CK(b, cudaEventRecord(e0, b->stream));
+        for (int rep = 0; rep < 2; ++rep) {
+          if (!cu(cudaEventRecord(e0, b->stream), "cudaEventRecord")) break;
           rc = do_steps(b, n_t);
           if (rc) break;
-          CK(b, cudaEventRecord(e1, b->stream));
-          CK(b, cudaEventSynchronize(e1));
+          if (!cu(cudaEventRecord(e1, b->stream), "cudaEventRecord")) break;
+          if (!cu(cudaEventSynchronize(e1), "cudaEventSynchronize")) break;
           float ms = 0.f;
-          CK(b, cudaEventElapsedTime(&ms, e0, e1));
+          if (!cu(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime")) break;
           if (per < 0 || ms / n_t < per) per = ms / n_t;
         }
         if (rc) break;
@@ -1032,12 +1043,16 @@ int autotune(Batch* b, int steps, const char* cache_path, TileChoice& best) {
       }
       if (rc) break;
     }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+    if (rc) break;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
   // Restore the state into both slabs and the bookkeeping.
-  cudaMemcpyAsync(b->slab[0], backup, bytes, cudaMemcpyDeviceToDevice, b->stream);
-  cudaMemcpyAsync(b->slab[1], backup, bytes, cudaMemcpyDeviceToDevice, b->stream);
-  cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream);
+  if (saved) {
+    cudaMemcpyAsync(b->slab[0], backup, bytes, cudaMemcpyDeviceToDevice, b->stream);
+    cudaMemcpyAsync(b->slab[1], backup, bytes, cudaMemcpyDeviceToDevice, b->stream);
+    cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream);
+  }
   cudaStreamSynchronize(b->stream);
   cudaFree(backup);
   b->cur = saved_cur;

@@ -85,7 +85,7 @@ def test_per_instance_widths_equal_uniform_tiling_bitwise():
         for i, fl in enumerate(fields):
             b.init_fields(i, *fl)
         b.step(70)
-        # widths 32 (nx 5, 400), 64 (70, 64), 96 (130, 257) and 128 (220)
+        # widths 32 (nx 5), 64 (70, 64), 96 (130, 257) and 128 (220, 400)
         assert b.launches_per_step == (1 if threads == 0 else 4)
         pops = [b.get_populations(i) for i in range(len(cs))]
         diags = b.diagnostics()
