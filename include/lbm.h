@@ -40,6 +40,7 @@ extern "C" {
                               returned; the state was not advanced correctly) */
 #define LBM_ESTATE (-6)    /* call not valid in the handle's current state */
 #define LBM_EIO (-7)       /* file could not be read/written, or failed its checksum */
+#define LBM_ECORRUPT (-8)  /* a guard band around a device buffer was overwritten */
 
 /* Floating-point format of the stored populations. */
 #define LBM_FP64 0     /* double populations and double arithmetic */
@@ -350,6 +351,40 @@ int lbm_batch_get_tiling(const lbm_batch* b, int* threads, int* vec, int* rows);
 /* Step-kernel launches per step of lbm_batch_step (0 when nothing is active; with
  * LBM_TILE_PER_INSTANCE one per pair-kernel width in use, else 1). */
 int lbm_batch_launches_per_step(const lbm_batch* b);
+
+/*
+ * Integrity checks and fault injection (for tests of the library and of its callers).
+ *
+ * The population slabs, the moment fields, the previous-density array and the host
+ * staging buffer of a handle are allocated with 4096-byte guard bands of a fixed byte
+ * pattern on each side.  lbm_check_guards (lbm_batch_check_guards) synchronises the
+ * handle's stream and reads them back: LBM_OK while every guard byte is intact,
+ * LBM_ECORRUPT (the message names the buffer and the offset) if any kernel or copy wrote
+ * outside its buffer.
+ */
+int lbm_check_guards(lbm_handle* h);
+int lbm_batch_check_guards(lbm_batch* b);
+
+/*
+ * lbm_debug_fail_alloc(n), n >= 0: the next n device allocations made by lattice and
+ * batch handles (process-wide) succeed and the one after fails, as an out-of-memory
+ * would (the call that made it returns LBM_ENOMEM and releases what it had allocated);
+ * the hook then disarms itself.  n < 0 disarms it.  Returns the previous setting.
+ */
+int lbm_debug_fail_alloc(int n);
+
+/* Device allocations made by lattice and batch handles and not yet released
+ * (process-wide): returns to its earlier value once every handle created since is
+ * destroyed, whether or not its calls failed. */
+long long lbm_debug_live_allocs(void);
+
+/*
+ * Overwrite one byte of the guard band just after guarded buffer `which` of the handle
+ * (0 and 1: the population slabs, 2: the previous density), so that lbm_check_guards
+ * must report it.  A host-side copy into memory the handle owns: no kernel runs and
+ * nothing outside the allocation is touched.  LBM_EINVAL for an unknown buffer.
+ */
+int lbm_debug_corrupt_guard(lbm_handle* h, int which);
 
 #ifdef __cplusplus
 }

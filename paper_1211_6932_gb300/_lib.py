@@ -11,8 +11,8 @@ c_int, c_double, c_void_p, c_size_t, c_longlong = (ctypes.c_int, ctypes.c_double
 dptr = ctypes.POINTER(ctypes.c_double)
 llptr = ctypes.POINTER(ctypes.c_longlong)
 
-LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE, LBM_EIO = (
-    0, -1, -2, -3, -4, -5, -6, -7)
+(LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE, LBM_EIO,
+ LBM_ECORRUPT) = (0, -1, -2, -3, -4, -5, -6, -7, -8)
 LBM_FP64, LBM_FP32_DEV = 0, 1
 LBM_VISC_CONST, LBM_VISC_STEP, LBM_VISC_LINEAR = 0, 1, 2
 LBM_BC_PERIODIC, LBM_BC_WALLS_Y = 0, 1
@@ -109,6 +109,11 @@ SIGNATURES = {
     "lbm_batch_get_tiling": (c_int, [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                                      ctypes.POINTER(c_int)]),
     "lbm_batch_launches_per_step": (c_int, [c_void_p]),
+    "lbm_check_guards": (c_int, [c_void_p]),
+    "lbm_batch_check_guards": (c_int, [c_void_p]),
+    "lbm_debug_fail_alloc": (c_int, [c_int]),
+    "lbm_debug_live_allocs": (ctypes.c_longlong, []),
+    "lbm_debug_corrupt_guard": (c_int, [c_void_p, c_int]),
     # include/lbm_mlp.h
     "lbm_mlp_create": (c_int, [ctypes.POINTER(c_void_p), fptr, c_int, c_void_p, c_int]),
     "lbm_mlp_destroy": (None, [c_void_p]),

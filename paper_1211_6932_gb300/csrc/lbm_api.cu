@@ -6,7 +6,10 @@
 // steps are replayed from a captured CUDA graph.
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdint>
@@ -76,6 +79,13 @@ struct Batch {
   cudaStream_t grp_stream[kMaxGroups - 1] = {nullptr, nullptr, nullptr};  // graph branches
   cudaEvent_t grp_fork = nullptr, grp_join[kMaxGroups - 1] = {nullptr, nullptr, nullptr};
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  // Buffers allocated with guard bands (lbm_check_guards): base pointer, user bytes, name.
+  struct Guarded {
+    char* base;
+    size_t bytes;
+    const char* name;
+  };
+  std::vector<Guarded> guarded;
   std::string err;
   int sms = 0;
   int device = -1;
@@ -107,6 +117,45 @@ int set_err(std::string& dst, int code, const char* fmt, ...) {
   } while (0)
 
 size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
+
+// Fault injection (lbm_debug_fail_alloc): while >= 0, the number of device allocations
+// that still succeed before one fails.
+std::atomic<int> g_fail_after{-1};
+std::atomic<long long> g_live_allocs{0};  // device allocations not yet released
+
+// Every device allocation of the lattice and batch handles goes through here.
+cudaError_t dev_malloc_raw(void** p, size_t bytes) {
+  int n = g_fail_after.load();
+  while (n >= 0 && !g_fail_after.compare_exchange_weak(n, n - 1)) {
+  }
+  if (n == 0) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) g_live_allocs.fetch_add(1);
+  return e;
+}
+template <typename T>
+cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc_raw(reinterpret_cast<void**>(p), bytes);
+}
+// ... and every release.
+void dev_free(void* p) {
+  if (!p) return;
+  cudaFree(p);
+  g_live_allocs.fetch_sub(1);
+}
+
+// Guard bands: this many bytes of kCanary before and after each guarded buffer.
+constexpr size_t kGuard = 4096;
+constexpr unsigned char kCanary = 0xA5;
+
+// NVTX range over a public call (shown by Nsight Systems / Compute when attached).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 // Default kernel configuration per precision (threads per CTA, columns per thread).
 int default_threads(bool) { return 128; }  // best measured for both precisions
@@ -160,8 +209,42 @@ void fill_mirror(lbm::PhysParams<R>& m, const InstParams& P) {
 
 template <typename T>
 void free_dev(T*& p) {
-  if (p) cudaFree((void*)p);
+  dev_free((void*)p);
   p = nullptr;
+}
+
+// Device buffer of `bytes` with kGuard bytes of kCanary on each side; *p is the user part.
+int guarded_alloc(Batch* b, void** p, size_t bytes, const char* name) {
+  char* base = nullptr;
+  CK(b, dev_malloc(&base, bytes + 2 * kGuard));
+  b->guarded.push_back({base, bytes, name});  // freed by destroy_batch from here on
+  CK(b, cudaMemsetAsync(base, kCanary, kGuard, b->stream));
+  CK(b, cudaMemsetAsync(base + kGuard + bytes, kCanary, kGuard, b->stream));
+  *p = base + kGuard;
+  return LBM_OK;
+}
+
+void free_guarded(Batch* b) {
+  for (auto& g : b->guarded) dev_free(g.base);
+  b->guarded.clear();
+}
+
+// LBM_ECORRUPT if a byte of any guard band changed (a write outside its buffer).
+int check_guards(Batch* b) {
+  CK(b, cudaStreamSynchronize(b->stream));
+  std::vector<unsigned char> h(2 * kGuard);
+  for (const auto& g : b->guarded) {
+    CK(b, cudaMemcpy(h.data(), g.base, kGuard, cudaMemcpyDeviceToHost));
+    CK(b, cudaMemcpy(h.data() + kGuard, g.base + kGuard + g.bytes, kGuard,
+                     cudaMemcpyDeviceToHost));
+    for (size_t k = 0; k < 2 * kGuard; ++k)
+      if (h[k] != kCanary)
+        return set_err(b->err, LBM_ECORRUPT, "%s: guard byte %s the buffer overwritten (%s %zu)",
+                       g.name, k < kGuard ? "before" : "after",
+                       k < kGuard ? "offset -" : "offset +",
+                       k < kGuard ? kGuard - k : k - kGuard);
+  }
+  return LBM_OK;
 }
 
 void drop_graphs(Batch* b) {
@@ -181,16 +264,16 @@ void destroy_batch(Batch* b) {
   free_dev(b->d_items);
   free_dev(b->d_all_items);
   free_dev(b->d_item_begin);
-  free_dev(b->slab[0]);
-  free_dev(b->slab[1]);
-  free_dev(b->rho_prev);
-  for (auto& f : b->fields) free_dev(f);
+  b->slab[0] = b->slab[1] = nullptr;  // guarded buffers
+  b->rho_prev = nullptr;
+  for (auto& f : b->fields) f = nullptr;
+  b->staging = nullptr;
+  free_guarded(b);
   free_dev(b->d_part_sum);
   free_dev(b->d_part_max);
   free_dev(b->d_part_bad);
   free_dev(b->d_diag);
   free_dev(b->d_status);
-  free_dev(b->staging);
   free_dev(b->d_flag);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   for (auto& st : b->grp_stream)
@@ -323,17 +406,17 @@ int rebuild_items(Batch* b) {
     free_dev(b->d_part_max);
     free_dev(b->d_part_bad);
     b->cap_all = 0;
-    CK(b, cudaMalloc(&b->d_all_items, sizeof(WorkItem) * std::max(n_all, 1)));
-    CK(b, cudaMalloc(&b->d_part_sum, sizeof(double) * 3 * std::max(n_all, 1)));
-    CK(b, cudaMalloc(&b->d_part_max, sizeof(float) * 2 * std::max(n_all, 1)));
-    CK(b, cudaMalloc(&b->d_part_bad, sizeof(int) * std::max(n_all, 1)));
+    CK(b, dev_malloc(&b->d_all_items, sizeof(WorkItem) * std::max(n_all, 1)));
+    CK(b, dev_malloc(&b->d_part_sum, sizeof(double) * 3 * std::max(n_all, 1)));
+    CK(b, dev_malloc(&b->d_part_max, sizeof(float) * 2 * std::max(n_all, 1)));
+    CK(b, dev_malloc(&b->d_part_bad, sizeof(int) * std::max(n_all, 1)));
     b->cap_all = n_all;
   }
   // Step items can outnumber the moments items (narrower strips under per-instance widths).
   if (b->n_items > b->cap_items || !b->d_items) {
     free_dev(b->d_items);
     b->cap_items = 0;
-    CK(b, cudaMalloc(&b->d_items, sizeof(WorkItem) * std::max(b->n_items, 1)));
+    CK(b, dev_malloc(&b->d_items, sizeof(WorkItem) * std::max(b->n_items, 1)));
     b->cap_items = b->n_items;
   }
   b->n_all = n_all;
@@ -342,7 +425,7 @@ int rebuild_items(Batch* b) {
   if (b->n_items)
     CK(b, cudaMemcpy(b->d_items, b->items.data(), sizeof(WorkItem) * b->n_items,
                      cudaMemcpyHostToDevice));
-  if (!b->d_item_begin) CK(b, cudaMalloc(&b->d_item_begin, sizeof(int) * (b->n_inst + 1)));
+  if (!b->d_item_begin) CK(b, dev_malloc(&b->d_item_begin, sizeof(int) * (b->n_inst + 1)));
   CK(b, cudaMemcpy(b->d_item_begin, b->item_begin.data(), sizeof(int) * (b->n_inst + 1),
                    cudaMemcpyHostToDevice));
   return LBM_OK;
@@ -458,15 +541,21 @@ int create_batch(Batch* b, int n, const lbm_instance* in, bool fp64, int psi_fp6
   }
   CK(b, cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
   for (int k = 0; k < 2; ++k) {
-    CK(b, cudaMalloc(&b->slab[k], b->slab_elems * b->esz));
+    int rc = guarded_alloc(b, &b->slab[k], b->slab_elems * b->esz,
+                           k == 0 ? "population slab 0" : "population slab 1");
+    if (rc) return rc;
     CK(b, cudaMemsetAsync(b->slab[k], 0, b->slab_elems * b->esz, b->stream));
   }
-  CK(b, cudaMalloc(&b->rho_prev, b->dense_elems * b->esz));
-  CK(b, cudaMalloc(&b->d_inst, sizeof(InstParams) * n));
+  {
+    int rc = guarded_alloc(b, &b->rho_prev, std::max<size_t>(b->dense_elems, 1) * b->esz,
+                           "previous density");
+    if (rc) return rc;
+  }
+  CK(b, dev_malloc(&b->d_inst, sizeof(InstParams) * n));
   CK(b, cudaMemcpyAsync(b->d_inst, b->inst.data(), sizeof(InstParams) * n,
                         cudaMemcpyHostToDevice, b->stream));
-  CK(b, cudaMalloc(&b->d_diag, sizeof(double) * 6 * n));
-  CK(b, cudaMalloc(&b->d_status, sizeof(int)));
+  CK(b, dev_malloc(&b->d_diag, sizeof(double) * 6 * n));
+  CK(b, dev_malloc(&b->d_status, sizeof(int)));
   CK(b, cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream));
   return rebuild_items(b);
 }
@@ -614,7 +703,7 @@ int sync_status(Batch* b) {
 
 // Device scratch of `bytes`, freed by the caller.
 int dev_alloc(Batch* b, void** p, size_t bytes) {
-  CK(b, cudaMalloc(p, std::max<size_t>(bytes, 16)));
+  CK(b, dev_malloc(p, std::max<size_t>(bytes, 16)));
   return LBM_OK;
 }
 
@@ -624,13 +713,14 @@ int ensure_staging(Batch* b) {
   if (b->staging) return LBM_OK;
   size_t m = 1;
   for (const auto& P : b->inst) m = std::max(m, (size_t)P.nx * P.ny);
-  CK(b, cudaMalloc(&b->staging, 3 * m * sizeof(double)));
+  int rc = guarded_alloc(b, (void**)&b->staging, 3 * m * sizeof(double), "staging");
+  if (rc) return rc;
   b->staging_elems = m;
   return LBM_OK;
 }
 
 int ensure_flag(Batch* b) {
-  if (!b->d_flag) CK(b, cudaMalloc(&b->d_flag, sizeof(int)));
+  if (!b->d_flag) CK(b, dev_malloc(&b->d_flag, sizeof(int)));
   return LBM_OK;
 }
 
@@ -716,7 +806,7 @@ int set_pops(Batch* b, int i, const double* f) {
                         cudaMemcpyDeviceToDevice, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-  cudaFree(tmp);
+  dev_free(tmp);
   if (e != cudaSuccess)
     return set_err(b->err, LBM_ECUDA, "set populations failed: %s", cudaGetErrorString(e));
   b->steps[i] = 0;
@@ -737,7 +827,7 @@ int get_pops(Batch* b, int i, double* f) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(f, tmp, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-  cudaFree(tmp);
+  dev_free(tmp);
   if (e != cudaSuccess)
     return set_err(b->err, LBM_ECUDA, "get populations failed: %s", cudaGetErrorString(e));
   return LBM_OK;
@@ -759,7 +849,11 @@ int moments_pass(Batch* b, const WorkItem* d_items, int n, MomArgs<S> mo) {
 
 int ensure_fields(Batch* b) {
   for (auto& f : b->fields)
-    if (!f) CK(b, cudaMalloc(&f, std::max<size_t>(b->dense_elems, 1) * b->esz));
+    if (!f) {
+      int rc = guarded_alloc(b, &f, std::max<size_t>(b->dense_elems, 1) * b->esz,
+                             "moment field");
+      if (rc) return rc;
+    }
   return LBM_OK;
 }
 
@@ -874,7 +968,7 @@ int eval_psi(Batch* b, const double* rho, double* psi, size_t n) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(psi, dp, n * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-  cudaFree(tmp);
+  dev_free(tmp);
   if (e != cudaSuccess) return set_err(b->err, LBM_ECUDA, "psi evaluation failed: %s", cudaGetErrorString(e));
   return LBM_OK;
 }
@@ -988,7 +1082,7 @@ int autotune(Batch* b, int steps, const char* cache_path, TileChoice& best) {
   // always released and the state always restored.
   void* backup = nullptr;
   const size_t bytes = b->slab_elems * b->esz;
-  CK(b, cudaMalloc(&backup, bytes));
+  CK(b, dev_malloc(&backup, bytes));
   int rc = LBM_OK;
   auto cu = [&](cudaError_t e, const char* what) {
     if (e != cudaSuccess && rc == LBM_OK)
@@ -1054,7 +1148,7 @@ int autotune(Batch* b, int steps, const char* cache_path, TileChoice& best) {
     cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream);
   }
   cudaStreamSynchronize(b->stream);
-  cudaFree(backup);
+  dev_free(backup);
   b->cur = saved_cur;
   b->steps = saved_steps;
   if (rc) return rc;
@@ -1147,6 +1241,7 @@ void lbm_options_default(lbm_options* o) {
 
 int lbm_create(lbm_handle** out, int nx, int ny, lbm_eos eos, double G, double sigma,
                const double s[9], double nu_l, double nu_v, const lbm_options* opt) {
+  Range r_("lbm_create");
   if (!out || !s) return set_err(g_thread_err, LBM_EINVAL, "out and s must not be NULL");
   *out = nullptr;
   lbm_options o;
@@ -1197,6 +1292,7 @@ const char* lbm_last_error(const lbm_handle* h) {
 }
 
 int lbm_init_fields(lbm_handle* h, const double* rho, const double* ux, const double* uy) {
+  Range r_("lbm_init_fields");
   DeviceGuard g_(h ? &h->b : nullptr);
   if (!h) return LBM_EINVAL;
   return init_instance(&h->b, 0, rho, ux, uy, false);
@@ -1224,6 +1320,7 @@ int lbm_get_populations(lbm_handle* h, double* f) {
 }
 
 int lbm_step(lbm_handle* h, int n) {
+  Range r_("lbm_step");
   DeviceGuard g_(h ? &h->b : nullptr);
   if (!h) return LBM_EINVAL;
   return do_steps(&h->b, n);
@@ -1236,6 +1333,7 @@ int lbm_sync(lbm_handle* h) {
 }
 
 int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy) {
+  Range r_("lbm_moments");
   DeviceGuard g_(h ? &h->b : nullptr);
   if (!h) return LBM_EINVAL;
   int rc = moments_host(&h->b, 0, rho, ux, uy);
@@ -1250,6 +1348,7 @@ int lbm_moments_device(lbm_handle* h, void* rho, void* ux, void* uy) {
 }
 
 int lbm_diagnostics(lbm_handle* h, lbm_diag* out) {
+  Range r_("lbm_diagnostics");
   DeviceGuard g_(h ? &h->b : nullptr);
   if (!h || !out) return h ? set_err(h->b.err, LBM_EINVAL, "out must not be NULL") : LBM_EINVAL;
   return diagnostics(&h->b, out);
@@ -1257,6 +1356,7 @@ int lbm_diagnostics(lbm_handle* h, lbm_diag* out) {
 
 int lbm_pressure_tensor(lbm_handle* h, double* pxx, double* pyy, double* pxy,
                         int include_sigma) {
+  Range r_("lbm_pressure_tensor");
   DeviceGuard g_(h ? &h->b : nullptr);
   if (!h) return LBM_EINVAL;
   Batch* b = &h->b;
@@ -1281,7 +1381,7 @@ int lbm_pressure_tensor(lbm_handle* h, double* pxx, double* pyy, double* pxy,
     e = cudaMemcpyAsync(outs[k], d + k * N, N * sizeof(double), cudaMemcpyDeviceToHost,
                         b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-  cudaFree(d);
+  dev_free(d);
   if (e != cudaSuccess)
     return set_err(b->err, LBM_ECUDA, "pressure tensor failed: %s", cudaGetErrorString(e));
   return LBM_OK;
@@ -1300,6 +1400,7 @@ int lbm_selftest_timeout(lbm_handle* h, long long polls) {
 
 int lbm_init_droplets(lbm_handle* h, const lbm_droplet* drops, int n, const lbm_warm_params* p,
                       int flags) {
+  Range r_("lbm_init_droplets");
   DeviceGuard g_(h ? &h->b : nullptr);
   if (!h) return LBM_EINVAL;
   Batch* b = &h->b;
@@ -1347,12 +1448,13 @@ int lbm_init_droplets(lbm_handle* h, const lbm_droplet* drops, int n, const lbm_
   if (!rc)
     rc = init_instance(b, 0, d_rho, balanced ? d_rho + N : nullptr,
                        balanced ? d_rho + 2 * N : nullptr, true);
-  if (d_rho) cudaFree(d_rho);
-  if (d_drops) cudaFree(d_drops);
+  dev_free(d_rho);
+  dev_free(d_drops);
   return rc;
 }
 
 int lbm_phase_stats(lbm_handle* h, double rho_vap_max, double rho_liq_min, double out[4]) {
+  Range r_("lbm_phase_stats");
   DeviceGuard g_(h ? &h->b : nullptr);
   if (!h) return LBM_EINVAL;
   Batch* b = &h->b;
@@ -1375,7 +1477,7 @@ int lbm_phase_stats(lbm_handle* h, double rho_vap_max, double rho_liq_min, doubl
     e = cudaMemcpyAsync(part.data(), d_part, part.size() * sizeof(double),
                         cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-  cudaFree(d_part);
+  dev_free(d_part);
   if (e != cudaSuccess)
     return set_err(b->err, LBM_ECUDA, "phase sums failed: %s", cudaGetErrorString(e));
   double sv = 0.0, cv = 0.0, sl = 0.0, cl = 0.0;
@@ -1393,6 +1495,7 @@ int lbm_phase_stats(lbm_handle* h, double rho_vap_max, double rho_liq_min, doubl
 }
 
 int lbm_diagnostics_noalloc(lbm_handle* h, double* out_dev) {
+  Range r_("lbm_diagnostics_noalloc");
   DeviceGuard g_(h ? &h->b : nullptr);
   if (!h) return LBM_EINVAL;
   Batch* b = &h->b;
@@ -1464,6 +1567,7 @@ void* lbm_stream(const lbm_handle* h) { return h ? (void*)h->b.stream : nullptr;
 
 int lbm_autotune(lbm_handle* h, int steps, const char* cache_path, int* threads, int* vec,
                  int* rows, double* ms_per_step) {
+  Range r_("lbm_autotune");
   DeviceGuard g_(h ? &h->b : nullptr);
   if (!h) return LBM_EINVAL;
   TileChoice c;
@@ -1477,6 +1581,7 @@ int lbm_autotune(lbm_handle* h, int steps, const char* cache_path, int* threads,
 }
 
 int lbm_save(lbm_handle* h, const char* path) {
+  Range r_("lbm_save");
   DeviceGuard g_(h ? &h->b : nullptr);
   if (!h || !path) return LBM_EINVAL;
   Batch* b = &h->b;
@@ -1510,6 +1615,7 @@ int lbm_save(lbm_handle* h, const char* path) {
 }
 
 int lbm_load(lbm_handle* h, const char* path) {
+  Range r_("lbm_load");
   DeviceGuard g_(h ? &h->b : nullptr);
   if (!h || !path) return LBM_EINVAL;
   Batch* b = &h->b;
@@ -1552,6 +1658,7 @@ int lbm_load(lbm_handle* h, const char* path) {
 int lbm_batch_create(lbm_batch** out, int n, const lbm_instance* inst, int precision,
                      void* stream, int device, int tile_threads, int tile_vec,
                      int tile_rows) {
+  Range r_("lbm_batch_create");
   if (!out) return set_err(g_thread_err, LBM_EINVAL, "out must not be NULL");
   *out = nullptr;
   if (precision != LBM_FP64 && precision != LBM_FP32_DEV)
@@ -1583,18 +1690,21 @@ const char* lbm_batch_last_error(const lbm_batch* b) {
 
 int lbm_batch_init_fields(lbm_batch* b, int i, const double* rho, const double* ux,
                           const double* uy) {
+  Range r_("lbm_batch_init_fields");
   DeviceGuard g_(b ? &b->b : nullptr);
   if (!b) return LBM_EINVAL;
   return init_instance(&b->b, i, rho, ux, uy, false);
 }
 
 int lbm_batch_step(lbm_batch* b, int n) {
+  Range r_("lbm_batch_step");
   DeviceGuard g_(b ? &b->b : nullptr);
   if (!b) return LBM_EINVAL;
   return do_steps(&b->b, n);
 }
 
 int lbm_batch_moments(lbm_batch* b, int i, double* rho, double* ux, double* uy) {
+  Range r_("lbm_batch_moments");
   DeviceGuard g_(b ? &b->b : nullptr);
   if (!b) return LBM_EINVAL;
   if (i < 0 || i >= b->b.n_inst) return set_err(b->b.err, LBM_EINVAL, "instance out of range");
@@ -1609,6 +1719,7 @@ int lbm_batch_get_populations(lbm_batch* b, int i, double* f) {
 }
 
 int lbm_batch_diagnostics(lbm_batch* b, lbm_diag* out) {
+  Range r_("lbm_batch_diagnostics");
   DeviceGuard g_(b ? &b->b : nullptr);
   if (!b || !out) return LBM_EINVAL;
   return diagnostics(&b->b, out);
@@ -1624,6 +1735,7 @@ int lbm_batch_active(const lbm_batch* b) {
 
 int lbm_batch_autotune(lbm_batch* b, int steps, const char* cache_path, int* threads,
                        int* vec, int* rows, double* ms_per_step) {
+  Range r_("lbm_batch_autotune");
   DeviceGuard g_(b ? &b->b : nullptr);
   if (!b) return LBM_EINVAL;
   TileChoice c;
@@ -1644,6 +1756,39 @@ int lbm_batch_get_tiling(const lbm_batch* b, int* threads, int* vec, int* rows) 
   return LBM_OK;
 }
 
+int lbm_check_guards(lbm_handle* h) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  return check_guards(&h->b);
+}
+
+int lbm_batch_check_guards(lbm_batch* b) {
+  DeviceGuard g_(b ? &b->b : nullptr);
+  if (!b) return LBM_EINVAL;
+  return check_guards(&b->b);
+}
+
+int lbm_debug_fail_alloc(int n) { return g_fail_after.exchange(n < 0 ? -1 : n); }
+
+long long lbm_debug_live_allocs(void) { return g_live_allocs.load(); }
+
+int lbm_debug_corrupt_guard(lbm_handle* h, int which) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  Batch* b = &h->b;
+  const void* user = which == 0 ? b->slab[0] : which == 1 ? b->slab[1]
+                   : which == 2 ? b->rho_prev : nullptr;
+  for (const auto& g : b->guarded)
+    if (user && g.base + kGuard == user) {
+      const unsigned char bad = (unsigned char)~kCanary;
+      CK(b, cudaMemcpyAsync(g.base + kGuard + g.bytes, &bad, 1, cudaMemcpyHostToDevice,
+                            b->stream));
+      CK(b, cudaStreamSynchronize(b->stream));
+      return LBM_OK;
+    }
+  return set_err(b->err, LBM_EINVAL, "no guarded buffer %d", which);
+}
+
 int lbm_batch_launches_per_step(const lbm_batch* b) {
   if (!b) return LBM_EINVAL;
   return b->b.n_items > 0 ? b->b.n_groups : 0;
@@ -1651,6 +1796,7 @@ int lbm_batch_launches_per_step(const lbm_batch* b) {
 
 int lbm_batch_run_to_equilibrium(lbm_batch* bb, double tol, int check_every,
                                  long long max_steps, long long* steps_out) {
+  Range r_("lbm_batch_run_to_equilibrium");
   DeviceGuard g_(bb ? &bb->b : nullptr);
   if (!bb) return LBM_EINVAL;
   Batch* b = &bb->b;

@@ -11,6 +11,19 @@ _PREC = {"fp64": C.LBM_FP64, "fp32": C.LBM_FP32_DEV, "fp32_dev": C.LBM_FP32_DEV}
 _VISC = {None: -1, "const": C.LBM_VISC_CONST, "step": C.LBM_VISC_STEP,
          "linear": C.LBM_VISC_LINEAR}
 TILE_PER_INSTANCE = C.LBM_TILE_PER_INSTANCE  # tile_threads: a kernel width per instance
+
+
+def debug_fail_alloc(n):
+    """lbm_debug_fail_alloc: the next n device allocations of lattice and batch handles
+    succeed and the one after fails with LBM_ENOMEM (n < 0 disarms); returns the previous
+    setting."""
+    return C.lib().lbm_debug_fail_alloc(int(n))
+
+
+def debug_live_allocs():
+    """lbm_debug_live_allocs: device allocations of lattice and batch handles not yet
+    released (process-wide)."""
+    return int(C.lib().lbm_debug_live_allocs())
 _BC = {"periodic": C.LBM_BC_PERIODIC, "walls": C.LBM_BC_WALLS_Y, "walls_y": C.LBM_BC_WALLS_Y}
 
 
@@ -200,6 +213,45 @@ class Lattice:
         self._check(self._L.lbm_pressure_tensor(self._h, *[_d(a) for a in out],
                                                 1 if include_sigma else 0))
         return tuple(out)
+
+    def check_guards(self):
+        """lbm_check_guards: raises LbmError (LBM_ECORRUPT) if a guard band around one of
+        the handle's device buffers was overwritten."""
+        self._check(self._L.lbm_check_guards(self._h))
+
+    def debug_corrupt_guard(self, which=0):
+        """lbm_debug_corrupt_guard: overwrite one guard byte of buffer `which` (tests)."""
+        self._check(self._L.lbm_debug_corrupt_guard(self._h, int(which)))
+
+    def run(self, steps, log_every=100, log=None):
+        """Advance `steps` steps; every `log_every` steps (and at the end) append one JSON
+        line to `log` (a writable text file, or None to skip writing) with the step count,
+        the diagnostics of Eq. 6 fields (mass, momentum, max |v|, |d rho|_inf over the
+        interval) and the MLUPS of the interval (wall clock, stream synchronised).
+        Returns the list of records."""
+        import json
+        import time
+        recs = []
+        done = 0
+        self.diagnostics()  # reference density for the first |d rho|_inf
+        while done < steps:
+            n = min(int(log_every), steps - done)
+            self.sync()
+            t0 = time.perf_counter()
+            self.step(n)
+            self.sync()
+            dt = time.perf_counter() - t0
+            done += n
+            d = self.diagnostics()
+            rec = {"step": d["step"], "mass": d["mass"], "mom_x": d["mom_x"],
+                   "mom_y": d["mom_y"], "max_u": d["max_u"], "dinf": d["dinf"],
+                   "nonfinite": d["nonfinite"],
+                   "mlups": self.shape[0] * self.shape[1] * n / dt / 1e6}
+            recs.append(rec)
+            if log is not None:
+                log.write(json.dumps(rec) + "\n")
+                log.flush()
+        return recs
 
     def selftest_timeout(self, polls=1000):
         """Run the bounded-wait failure check (lbm_selftest_timeout); raises LbmError with
@@ -426,6 +478,10 @@ class Batch:
         self._check(self._L.lbm_batch_get_tiling(self._h, ctypes.byref(t), ctypes.byref(v),
                                                  ctypes.byref(r)))
         return t.value, v.value, r.value
+
+    def check_guards(self):
+        """lbm_batch_check_guards (see Lattice.check_guards)."""
+        self._check(self._L.lbm_batch_check_guards(self._h))
 
     @property
     def launches_per_step(self):
