@@ -473,10 +473,13 @@ def run_gpu(args):
     value = world * n_nodes * K / (total_ms_max * 1e-3) / 1e6
 
     # End to end through the C ABI with host buffers: upload the initial fields from
-    # pinned memory, 100 steps, read the density back.
+    # pinned memory, 100 steps, read the density back.  Host buffers are in the storage
+    # precision (float32 for FP32: lbm_init_fields_f32 / lbm_moments_f32).
     e2e_steps = max(1, min(5, K // DIAG_EVERY))
-    rho_h = torch.from_numpy(rho).pin_memory()
-    out_h = torch.empty((NY, NX), dtype=torch.float64).pin_memory()
+    hdt = np.float32 if PREC == "fp32" else np.float64
+    rho_h = torch.from_numpy(rho.astype(hdt)).pin_memory()
+    out_h = torch.empty((NY, NX), dtype=torch.float32 if PREC == "fp32"
+                        else torch.float64).pin_memory()
     rho_np, out_np = rho_h.numpy(), out_h.numpy()
     L.init_fields(rho_np)
     L.step(DIAG_EVERY)
@@ -513,7 +516,8 @@ def run_gpu(args):
                          "algorithmic_bytes_per_launch": bytes_lu * n_nodes,
                          "avg_launch_ms": avg_launch_ms},
             "e2e": {"value": e2e_value, "unit": "MLUPS",
-                    "h2d_bytes_per_step": n_nodes * 8, "d2h_bytes_per_step": n_nodes * 8,
+                    "h2d_bytes_per_step": n_nodes * rho_h.element_size(),
+                    "d2h_bytes_per_step": n_nodes * out_h.element_size(),
                     "lbm_steps_per_step": DIAG_EVERY},
             "clocks": clocks,
             "diagnostics": diag_last,

@@ -142,6 +142,10 @@ const char* lbm_last_error(const lbm_handle* h);
  */
 int lbm_init_fields(lbm_handle* h, const double* rho, const double* ux, const double* uy);
 
+/* Same as lbm_init_fields from host (ny, nx) floats: half the bytes on the host link;
+ * the fields are widened to double on the device before the same initialisation. */
+int lbm_init_fields_f32(lbm_handle* h, const float* rho, const float* ux, const float* uy);
+
 /* Same as lbm_init_fields with device pointers (double, (ny, nx), caller-owned). */
 int lbm_init_fields_device(lbm_handle* h, const double* rho, const double* ux,
                            const double* uy);
@@ -194,6 +198,10 @@ int lbm_pressure_tensor(lbm_handle* h, double* pxx, double* pyy, double* pxy,
 /* Density and velocity of Eq. 6 (rho v = sum e f + F/2) into host (ny, nx) doubles;
  * any pointer may be NULL.  Synchronous. */
 int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy);
+
+/* Same into host (ny, nx) floats: FP32_DEV fields as computed, FP64 fields rounded to
+ * the nearest float on the device; half the bytes on the host link.  Synchronous. */
+int lbm_moments_f32(lbm_handle* h, float* rho, float* ux, float* uy);
 
 /* Same into caller-owned device arrays of (ny, nx) elements of the storage type
  * (double for LBM_FP64, float for LBM_FP32_DEV); any pointer may be NULL.  Queued on the
@@ -322,8 +330,12 @@ int lbm_batch_init_fields(lbm_batch* b, int i, const double* rho, const double* 
                           const double* uy);
 /* Advance every active instance n steps (one launch per step, CUDA-graph replay). */
 int lbm_batch_step(lbm_batch* b, int n);
-/* Host moments of instance i, as lbm_moments. */
+/* Float host variant of lbm_batch_init_fields, as lbm_init_fields_f32. */
+int lbm_batch_init_fields_f32(lbm_batch* b, int i, const float* rho, const float* ux,
+                              const float* uy);
+/* Host moments of instance i, as lbm_moments (lbm_batch_moments_f32: as lbm_moments_f32). */
 int lbm_batch_moments(lbm_batch* b, int i, double* rho, double* ux, double* uy);
+int lbm_batch_moments_f32(lbm_batch* b, int i, float* rho, float* ux, float* uy);
 /* Host populations of instance i, as lbm_get_populations. */
 int lbm_batch_get_populations(lbm_batch* b, int i, double* f);
 /* Per-instance diagnostics (out has n entries), as lbm_diagnostics. */

@@ -109,6 +109,10 @@ SIGNATURES = {
     "lbm_batch_get_tiling": (c_int, [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                                      ctypes.POINTER(c_int)]),
     "lbm_batch_launches_per_step": (c_int, [c_void_p]),
+    "lbm_init_fields_f32": (c_int, [c_void_p, fptr, fptr, fptr]),
+    "lbm_moments_f32": (c_int, [c_void_p, fptr, fptr, fptr]),
+    "lbm_batch_init_fields_f32": (c_int, [c_void_p, c_int, fptr, fptr, fptr]),
+    "lbm_batch_moments_f32": (c_int, [c_void_p, c_int, fptr, fptr, fptr]),
     "lbm_check_guards": (c_int, [c_void_p]),
     "lbm_batch_check_guards": (c_int, [c_void_p]),
     "lbm_debug_fail_alloc": (c_int, [c_int]),

@@ -58,6 +58,7 @@ struct Batch {
   void* fields[3] = {nullptr, nullptr, nullptr};
   double* staging = nullptr;  // 3 x (largest instance) doubles: host uploads and downloads
   size_t staging_elems = 0;
+  float* staging32 = nullptr;  // 3 x (largest instance) floats: float host transfers
   int* d_flag = nullptr;      // one int for the initialisation's validity check
   double* d_part_sum = nullptr;
   float* d_part_max = nullptr;
@@ -268,6 +269,7 @@ void destroy_batch(Batch* b) {
   b->rho_prev = nullptr;
   for (auto& f : b->fields) f = nullptr;
   b->staging = nullptr;
+  b->staging32 = nullptr;
   free_guarded(b);
   free_dev(b->d_part_sum);
   free_dev(b->d_part_max);
@@ -719,6 +721,15 @@ int ensure_staging(Batch* b) {
   return LBM_OK;
 }
 
+// Device floats for 3 fields of the largest instance (float host transfers).
+int ensure_staging32(Batch* b) {
+  if (b->staging32) return LBM_OK;
+  int rc = ensure_staging(b);  // sets staging_elems
+  if (rc) return rc;
+  return guarded_alloc(b, (void**)&b->staging32, 3 * b->staging_elems * sizeof(float),
+                       "float staging");
+}
+
 int ensure_flag(Batch* b) {
   if (!b->d_flag) CK(b, dev_malloc(&b->d_flag, sizeof(int)));
   return LBM_OK;
@@ -783,6 +794,27 @@ int init_instance(Batch* b, int i, const double* rho, const double* ux, const do
                    "%d nodes have a density outside (0, 4/b), a negative psi^2 (Eq. 24) or "
                    "a non-finite velocity", bad);
   return LBM_OK;
+}
+
+// init_instance from host floats: one transfer of floats per field, widened to double on
+// the device, then the double path.
+int init_instance_f32(Batch* b, int i, const float* rho, const float* ux, const float* uy) {
+  if (i < 0 || i >= b->n_inst) return set_err(b->err, LBM_EINVAL, "instance %d out of range", i);
+  if (!rho) return set_err(b->err, LBM_EINVAL, "rho must not be NULL");
+  int rc = ensure_staging32(b);
+  if (rc) return rc;
+  const size_t N = (size_t)b->inst[i].nx * b->inst[i].ny;
+  const float* in[3] = {rho, ux, uy};
+  const double* dev[3] = {nullptr, nullptr, nullptr};
+  for (int k = 0; k < 3; ++k) {
+    if (!in[k]) continue;
+    float* f = b->staging32 + k * b->staging_elems;
+    double* d = b->staging + k * b->staging_elems;
+    CK(b, cudaMemcpyAsync(f, in[k], N * sizeof(float), cudaMemcpyHostToDevice, b->stream));
+    CK(b, lbm::launch_widen(f, d, (long long)N, b->stream));
+    dev[k] = d;
+  }
+  return init_instance(b, i, dev[0], dev[1], dev[2], true);
 }
 
 int set_pops(Batch* b, int i, const double* f) {
@@ -902,6 +934,36 @@ int moments_host(Batch* b, int i, double* rho, double* ux, double* uy) {
       CK(b, lbm::launch_widen((const float*)src, w, (long long)N, b->stream));
       CK(b, cudaMemcpyAsync(outs[k], w, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
     }
+  }
+  CK(b, cudaStreamSynchronize(b->stream));
+  return LBM_OK;
+}
+
+// moments_host into host floats: FP32 fields are transferred as stored, FP64 fields are
+// rounded to float on the device first.
+int moments_host_f32(Batch* b, int i, float* rho, float* ux, float* uy) {
+  int rc = ensure_fields(b);
+  if (rc) return rc;
+  rc = moments_device(b, i, rho ? b->fields[0] : nullptr, ux ? b->fields[1] : nullptr,
+                      uy ? b->fields[2] : nullptr, false);
+  if (rc) return rc;
+  if (b->fp64) {
+    rc = ensure_staging32(b);
+    if (rc) return rc;
+  }
+  const InstParams& P = b->inst[i];
+  const size_t N = (size_t)P.nx * P.ny;
+  float* outs[3] = {rho, ux, uy};
+  for (int k = 0; k < 3; ++k) {
+    if (!outs[k]) continue;
+    const char* src = (const char*)b->fields[k] + P.dense_off * b->esz;
+    const float* f = (const float*)src;
+    if (b->fp64) {
+      float* w = b->staging32 + k * b->staging_elems;
+      CK(b, lbm::launch_narrow((const double*)src, w, (long long)N, b->stream));
+      f = w;
+    }
+    CK(b, cudaMemcpyAsync(outs[k], f, N * sizeof(float), cudaMemcpyDeviceToHost, b->stream));
   }
   CK(b, cudaStreamSynchronize(b->stream));
   return LBM_OK;
@@ -1347,6 +1409,20 @@ int lbm_moments_device(lbm_handle* h, void* rho, void* ux, void* uy) {
   return moments_device(&h->b, 0, rho, ux, uy, true);
 }
 
+int lbm_init_fields_f32(lbm_handle* h, const float* rho, const float* ux, const float* uy) {
+  Range r_("lbm_init_fields_f32");
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  return init_instance_f32(&h->b, 0, rho, ux, uy);
+}
+
+int lbm_moments_f32(lbm_handle* h, float* rho, float* ux, float* uy) {
+  Range r_("lbm_moments_f32");
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  return moments_host_f32(&h->b, 0, rho, ux, uy);
+}
+
 int lbm_diagnostics(lbm_handle* h, lbm_diag* out) {
   Range r_("lbm_diagnostics");
   DeviceGuard g_(h ? &h->b : nullptr);
@@ -1709,6 +1785,22 @@ int lbm_batch_moments(lbm_batch* b, int i, double* rho, double* ux, double* uy) 
   if (!b) return LBM_EINVAL;
   if (i < 0 || i >= b->b.n_inst) return set_err(b->b.err, LBM_EINVAL, "instance out of range");
   return moments_host(&b->b, i, rho, ux, uy);
+}
+
+int lbm_batch_init_fields_f32(lbm_batch* b, int i, const float* rho, const float* ux,
+                              const float* uy) {
+  Range r_("lbm_batch_init_fields_f32");
+  DeviceGuard g_(b ? &b->b : nullptr);
+  if (!b) return LBM_EINVAL;
+  return init_instance_f32(&b->b, i, rho, ux, uy);
+}
+
+int lbm_batch_moments_f32(lbm_batch* b, int i, float* rho, float* ux, float* uy) {
+  Range r_("lbm_batch_moments_f32");
+  DeviceGuard g_(b ? &b->b : nullptr);
+  if (!b) return LBM_EINVAL;
+  if (i < 0 || i >= b->b.n_inst) return set_err(b->b.err, LBM_EINVAL, "instance out of range");
+  return moments_host_f32(&b->b, i, rho, ux, uy);
 }
 
 int lbm_batch_get_populations(lbm_batch* b, int i, double* f) {

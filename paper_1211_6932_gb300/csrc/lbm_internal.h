@@ -60,6 +60,8 @@ cudaError_t launch_pressure(const S* rho, const InstParams& P, double sigma, dou
 
 // dst[i] = (double)src[i] for n values.
 cudaError_t launch_widen(const float* src, double* dst, long long n, cudaStream_t st);
+// dst[i] = src[i] rounded to the nearest float, for n values.
+cudaError_t launch_narrow(const double* src, float* dst, long long n, cudaStream_t st);
 
 // One-block kernel whose bounded mbarrier wait runs out after `polls` polls and sets
 // STATUS_TIMEOUT in *status (lbm_selftest_timeout).

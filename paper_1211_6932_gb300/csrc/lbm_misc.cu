@@ -1,5 +1,6 @@
 // Small device kernels outside the step: the per-instance diagnostics totals, the
-// float-to-double widening of host reads, and the bounded-wait self-test.
+// float-to-double widening and double-to-float narrowing of host transfers, and the
+// bounded-wait self-test.
 #include "lbm_kernels_impl.cuh"
 
 namespace lbm {
@@ -82,6 +83,21 @@ cudaError_t launch_widen(const float* src, double* dst, long long n, cudaStream_
   long long g = (n + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
   widen_kernel<<<(int)(g < 1 ? 1 : g), 256, 0, st>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
+// double -> float (round to nearest) on the device, for float host reads of FP64 fields.
+__global__ void __launch_bounds__(256) narrow_kernel(const double* __restrict__ src,
+                                                     float* __restrict__ dst, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = __double2float_rn(src[i]);
+}
+
+cudaError_t launch_narrow(const double* src, float* dst, long long n, cudaStream_t st) {
+  long long g = (n + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  narrow_kernel<<<(int)(g < 1 ? 1 : g), 256, 0, st>>>(src, dst, n);
   return cudaGetLastError();
 }
 

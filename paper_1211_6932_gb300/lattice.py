@@ -49,6 +49,19 @@ def _d(a):
     return a.ctypes.data_as(C.dptr) if a is not None else None
 
 
+def _f(a):
+    return a.ctypes.data_as(C.fptr) if a is not None else None
+
+
+def _f32(a, shape):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.shape != shape:
+        raise ValueError("expected shape %s, got %s" % (shape, a.shape))
+    return a
+
+
 def _f64(a, shape):
     if a is None:
         return None
@@ -182,6 +195,12 @@ class Lattice:
 
     # -- state ---------------------------------------------------------------------------
     def init_fields(self, rho, ux=None, uy=None):
+        """Equilibrium start from host (ny, nx) fields; float32 arrays take the float
+        transfer (lbm_init_fields_f32), anything else is sent as float64."""
+        if getattr(rho, "dtype", None) == np.float32:
+            r, u, v = _f32(rho, self.shape), _f32(ux, self.shape), _f32(uy, self.shape)
+            self._check(self._L.lbm_init_fields_f32(self._h, _f(r), _f(u), _f(v)))
+            return
         r = _f64(rho, self.shape)
         u = _f64(ux, self.shape)
         v = _f64(uy, self.shape)
@@ -258,16 +277,27 @@ class Lattice:
         code LBM_ETIMEOUT when the timeout is detected and reported."""
         self._check(self._L.lbm_selftest_timeout(self._h, int(polls)))
 
-    def moments(self, out=None):
-        """rho, ux, uy of Eq. 6 as host arrays.  With out= (a float64 (ny, nx) array, e.g.
-        a pinned buffer) only the density is copied, into out."""
+    def moments(self, out=None, dtype=np.float64):
+        """rho, ux, uy of Eq. 6 as host arrays of dtype (float64, or float32 for the float
+        transfer, lbm_moments_f32).  With out= (a C-contiguous float64 or float32 (ny, nx)
+        array, e.g. a pinned buffer) only the density is copied, into out."""
         if out is not None:
-            if out.dtype != np.float64 or out.shape != self.shape or not out.flags.c_contiguous:
-                raise ValueError("out must be a C-contiguous float64 array of shape %s" % (self.shape,))
-            self._check(self._L.lbm_moments(self._h, _d(out), None, None))
+            if (out.dtype not in (np.float64, np.float32) or out.shape != self.shape
+                    or not out.flags.c_contiguous):
+                raise ValueError("out must be a C-contiguous float64 or float32 array of "
+                                 "shape %s" % (self.shape,))
+            if out.dtype == np.float32:
+                self._check(self._L.lbm_moments_f32(self._h, _f(out), None, None))
+            else:
+                self._check(self._L.lbm_moments(self._h, _d(out), None, None))
             return out
-        res = {k: np.empty(self.shape) for k in ("rho", "ux", "uy")}
-        self._check(self._L.lbm_moments(self._h, _d(res["rho"]), _d(res["ux"]), _d(res["uy"])))
+        res = {k: np.empty(self.shape, dtype=dtype) for k in ("rho", "ux", "uy")}
+        if np.dtype(dtype) == np.float32:
+            self._check(self._L.lbm_moments_f32(self._h, _f(res["rho"]), _f(res["ux"]),
+                                                _f(res["uy"])))
+        else:
+            self._check(self._L.lbm_moments(self._h, _d(res["rho"]), _d(res["ux"]),
+                                            _d(res["uy"])))
         return res
 
     def moments_device(self, rho=None, ux=None, uy=None):
@@ -419,19 +449,30 @@ class Batch:
         return len(self.instances)
 
     def init_fields(self, i, rho, ux=None, uy=None):
+        """As Lattice.init_fields for instance i (float32 arrays: the float transfer)."""
         inst = self.instances[i]
         shp = (inst.ny, inst.nx)
+        if getattr(rho, "dtype", None) == np.float32:
+            r, u, v = _f32(rho, shp), _f32(ux, shp), _f32(uy, shp)
+            self._check(self._L.lbm_batch_init_fields_f32(self._h, int(i), _f(r), _f(u),
+                                                          _f(v)))
+            return
         r, u, v = _f64(rho, shp), _f64(ux, shp), _f64(uy, shp)
         self._check(self._L.lbm_batch_init_fields(self._h, int(i), _d(r), _d(u), _d(v)))
 
     def step(self, n=1):
         self._check(self._L.lbm_batch_step(self._h, int(n)))
 
-    def moments(self, i):
+    def moments(self, i, dtype=np.float64):
+        """rho, ux, uy of instance i as host arrays of dtype (float64 or float32)."""
         inst = self.instances[i]
-        out = {k: np.empty((inst.ny, inst.nx)) for k in ("rho", "ux", "uy")}
-        self._check(self._L.lbm_batch_moments(self._h, int(i), _d(out["rho"]), _d(out["ux"]),
-                                              _d(out["uy"])))
+        out = {k: np.empty((inst.ny, inst.nx), dtype=dtype) for k in ("rho", "ux", "uy")}
+        if np.dtype(dtype) == np.float32:
+            self._check(self._L.lbm_batch_moments_f32(self._h, int(i), _f(out["rho"]),
+                                                      _f(out["ux"]), _f(out["uy"])))
+        else:
+            self._check(self._L.lbm_batch_moments(self._h, int(i), _d(out["rho"]),
+                                                  _d(out["ux"]), _d(out["uy"])))
         return out
 
     def density(self, i):
