@@ -581,8 +581,9 @@ def run_gpu(args):
 
 def other_workloads(stream):
     """MLUPS of the other configurations, reported beside the headline (not roofline
-    evidence: c1 is latency-bound, c2 and c3 fit in L2), and of the FP64 parity mode on the
-    4096^2 field (144 B per lattice update).  Each: 3 warm-up steps and a 64-step graph
+    evidence: c1 is latency-bound, c2 and c3 fit in L2), of the FP64 parity mode on the
+    4096^2 field (144 B per lattice update) and of the 256-instance batch (c4, autotuned,
+    640 graph-replayed steps).  Each: 3 warm-up steps and a 64-step graph
     capture, then `steps` steps timed with CUDA events on the lattice's stream."""
     import torch
 
@@ -657,6 +658,33 @@ def other_workloads(stream):
         L.init_fields(field(rl, rv))
         timed("c5_droplets64_%dx%d_fp64" % (NX, NY), L, 200, NX * NY, "f64", 144,
               "FP64 populations and arithmetic (the 1e-12 parity mode)")
+    # c4: the 256-instance batch (autotuned tiling), one GPU
+    from paper_1211_6932_gb300 import Batch
+    insts, fields, n_total = batch256_instances()
+    b = Batch(insts, precision="fp32", stream=stream)
+    try:
+        for i, rho in enumerate(fields):
+            b.init_fields(i, rho)
+        nt, vec, rows, _ = b.autotune(steps=64)
+        b.step(3)
+        b.step(64)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(640)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / 640
+        bad = sum(d["nonfinite"] for d in b.diagnostics())
+        peak, kind = load_peak()
+        out.append({"workload": "c4_batch256_64to512_fp32", "nodes": n_total, "dtype": "f32",
+                    "steps": 640, "ms_per_step": ms, "mlups": n_total / (ms * 1e-3) / 1e6,
+                    "hbm_frac": 72 * n_total / (ms * 1e-3) / 1e9 / peak, "peak_source": kind,
+                    "note": "256 ragged instances, %.2f GB of state" % (72 * n_total / 1e9),
+                    "tiling": ["per_instance" if nt < 0 else nt, vec, rows],
+                    "launches_per_step": b.launches_per_step, "nonfinite_nodes": bad})
+    finally:
+        b.close()
     return out
 
 
