@@ -138,3 +138,33 @@ def test_splash_2048x512_walls_column_parity():
     cols = sorted({0, 1, 2047, 2046, 1024} | {k * strip + d for k in range(1, 6) for d in (-1, 0)}
                   | {int(v) for v in rng.integers(0, 2048, 10)})
     assert column_check(p, f0, f1, cols) <= 2e-6
+
+
+def test_slab_beyond_2_31_elements():
+    """Maximum-size indexing: a batch whose population slab holds more than 2^31 elements
+    (a 17000^2 instance, 2.6e9 elements per slab, 21 GB for both), followed by a small
+    droplet that therefore starts beyond element 2^31.  The small instance matches the
+    oracle step for step; the large uniform vapour stays at rest, finite, with its mass
+    conserved; no write leaves its buffer."""
+    from paper_1211_6932_gb300 import Batch, Eos, Instance
+    big = pairs.case(17000, 17000, tr=0.7, sigma=0.114)
+    small = pairs.case(64, 48, tr=0.7, sigma=0.114)
+    rl, rv = pairs.maxwell(small)
+    insts = [Instance(nx=c["nx"], ny=c["ny"], eos=Eos(a=c["a"], T=c["T"]), G=c["G"],
+                      sigma=c["sigma"], s=c["s"], rho_l=rl, rho_v=rv) for c in (big, small)]
+    b = Batch(insts, precision="fp32")
+    try:
+        b.init_fields(0, np.full((17000, 17000), rv, dtype=np.float32))
+        b.init_fields(1, wl.droplet(64, 48, rl, rv, 12.0, 4.0))
+        f0 = b.get_populations(1)
+        m0 = b.diagnostics()[0]["mass"]
+        b.step(3)
+        d = b.diagnostics()
+        got = b.get_populations(1)
+        b.check_guards()
+    finally:
+        b.close()
+    ref = oracle.run(pairs.oracle_params(small), f0, 3)
+    assert close32(got, ref, tol=6e-6) <= 6e-6
+    assert d[0]["nonfinite"] == 0 and d[0]["max_u"] < 1e-7
+    assert abs(d[0]["mass"] / m0 - 1) < 1e-6
