@@ -624,7 +624,7 @@ def other_workloads(stream):
     with Lattice(128, 128, e, sigma=0.114, s=tau8, precision="fp64", stream=stream) as L:
         L.init_fields(wl.droplet(128, 128, rl, rv, 30.0, 4.0))
         timed("c1_droplet_128x128_fp64", L, 5000, 128 * 128, "f64", 144,
-              "1.2 MB of state: latency-bound")
+              "1.2 MB of state: latency-bound; autotuned tiling", tune=True)
     # c2: 1024^2 oscillating ellipse, linear viscosity
     e = Eos(a=0.25, T=0.6 * wl.t_crit(0.25))
     rl, rv = maxwell(e)

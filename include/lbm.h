@@ -254,8 +254,8 @@ int lbm_set_tiling(lbm_handle* h, int threads, int vec, int rows);
 
 /*
  * Pick the step kernel's tiling by measurement: every available (threads, vec) pair, and
- * for FP32_DEV LBM_TILE_PER_INSTANCE, with chunk heights of 8, 12, 16, 20, 24, 28, 32,
- * 40, 48 and 64 rows is timed twice (the better time counts) over `steps` steps, rounded
+ * for FP32_DEV LBM_TILE_PER_INSTANCE, with chunk heights of 1, 2, 4, 8, 12, 16, 20, 24,
+ * 28, 32, 40, 48 and 64 rows is timed twice (the better time counts) over `steps` steps, rounded
  * up to even, stepped as lbm_step steps them (graph replays for each 64; CUDA events on
  * the handle's stream) on a saved copy of the state, which is restored afterwards (state and
  * step count are unchanged).  The fastest is kept.  cache_path (may be NULL) names a text

@@ -326,8 +326,10 @@ int step_nt(const Batch* b, int i) { return per_instance(b) ? b->inst_nt[i] : b-
 
 // Rows per CTA sweep: about six waves of resident CTAs (measured best on 4096^2: fewer
 // rows cost halo re-reads and row-loop start-up, more rows leave SMs idle in the tail),
-// clamped to [8, 64].  With per-instance widths each strip row counts as 1 / (resident
-// CTAs of its width) of an SM.
+// clamped to [8, 64] for FP32 and [1, 64] for FP64, whose rows are FP64-pipe bound: on a
+// 128^2 FP64 lattice one-row chunks spread the work over 4x more SMs (1.0 against 0.27
+// GLUPS), while FP32 lattices of 1M nodes lose 20-40 % below 8 rows.  With per-instance
+// widths each strip row counts as 1 / (resident CTAs of its width) of an SM.
 int default_rows(const Batch* b) {
   double sm_rows = 0.0;
   for (int i = 0; i < b->n_inst; ++i)
@@ -340,7 +342,7 @@ int default_rows(const Batch* b) {
     }
   const double target = (double)std::max(b->sms, 1) * 6.0;
   const long long r = (long long)std::ceil(sm_rows / target);
-  return (int)std::min<long long>(64, std::max<long long>(8, r));
+  return (int)std::min<long long>(64, std::max<long long>(b->fp64 ? 1 : 8, r));
 }
 
 // Work items of instance i: strips of W owned columns by chunks of `rows` rows.
@@ -1164,7 +1166,8 @@ int autotune(Batch* b, int steps, const char* cache_path, TileChoice& best) {
   const int vecs[] = {1, 2};
   // Chunk heights: the best one depends on how the CTA count falls into waves of resident
   // CTAs, which moves the step time by several per cent between neighbouring heights.
-  const int rows_c[] = {8, 12, 16, 20, 24, 28, 32, 40, 48, 64};
+  // Heights below 8 are for small grids, where more (shorter) chunks fill more SMs.
+  const int rows_c[] = {1, 2, 4, 8, 12, 16, 20, 24, 28, 32, 40, 48, 64};
   best = TileChoice();
   for (int vec : vecs) {
     for (int nt : nts) {
