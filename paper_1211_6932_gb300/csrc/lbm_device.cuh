@@ -748,7 +748,9 @@ __global__ void __launch_bounds__(NT, MinBlocks<S, NT>::value) sweep_kernel(
 // and does their arithmetic with packed float2 instructions.  Threads 1 .. NT-2 own the
 // WO = 2 NT - 4 columns of the strip; threads 0 and NT-1 evaluate psi of the halo
 // columns -1 and WO (their other column is unused); thread 0 issues the bulk copies.
-template <int NT, int NS_ = 4, int ST = 0>
+// Owners write their post-collision pair straight from registers (one 8-byte store per
+// population).
+template <int NT, int NS_ = 4>
 struct Sweep2Cfg {
   static constexpr int WO = 2 * NT - 4;      // owned columns per CTA (a multiple of 4)
   static constexpr int SEG = WO + 8;         // ring row: columns x0-4 .. x0+WO+3
@@ -757,8 +759,7 @@ struct Sweep2Cfg {
   static constexpr size_t BARS = 128;
   static constexpr size_t POP = (size_t)NSLOT * Q * SEG * sizeof(float);
   static constexpr size_t PSI = (size_t)PSI_ROWS * PSW * sizeof(float);
-  static constexpr size_t OUT = ST ? (size_t)2 * Q * PSW * sizeof(float) : 0;  // staged rows
-  static constexpr size_t BYTES = BARS + POP + PSI + OUT;
+  static constexpr size_t BYTES = BARS + POP + PSI;
 };
 
 // Resident CTAs per SM the pair kernel is compiled for (the register cap follows): with
@@ -768,19 +769,18 @@ constexpr int sweep2_min_blocks(int nt) {
   return nt == 64 ? 10 : nt == 96 ? 6 : nt == 128 ? 5 : 65536 / (nt * 128);
 }
 
-template <int NT, int MODE, int NS_ = 4, int ST = 0>
+template <int NT, int MODE, int NS_ = 4>
 __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
     const float* __restrict__ fin, float* __restrict__ fout, const InstParams* __restrict__ insts,
     const WorkItem* __restrict__ items, int n_items, MomArgs<float> mo,
     int* __restrict__ status) {
-  typedef Sweep2Cfg<NT, NS_, ST> C;
+  typedef Sweep2Cfg<NT, NS_> C;
   typedef Num<float2> N;
   constexpr int WO = C::WO, SEG = C::SEG, NS = C::NSLOT, PSW = C::PSW;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
   float* ring = reinterpret_cast<float*>(smem_raw + C::BARS);
   float* psis = reinterpret_cast<float*>(smem_raw + C::BARS + C::POP);
-  float* outs = reinterpret_cast<float*>(smem_raw + C::BARS + C::POP + C::PSI);
   __shared__ int s_abort;
   __shared__ double red_d[NT / 32][3];
   __shared__ float red_f[NT / 32][2];
@@ -800,7 +800,6 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
   const int xa = x0 + c0;                 // its global column (xa, xa + 1)
   const int xend = min(x0 + WO, nx);
   const bool owner = tid >= 1 && tid <= NT - 2 && xa < xend;
-  const int n_bulk = ((xend - x0) / 4) * 4;  // columns written by the bulk store
   // Ghost columns (periodic copies at -2, -1, nx, nx+1).  For even nx >= 4 the owners of
   // the pairs (0, 1) and (nx-2, nx-1) mirror them as pairs to (nx, nx+1) and (-2, -1);
   // every other case (odd nx, nx < 4) takes the general per-column path.
@@ -827,15 +826,6 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
     for (int q = 0; q < Q; ++q)
       bulk_g2s(ring + ((size_t)slot * Q + q) * SEG, src + (long long)q * plane, plane_bytes,
                &bars[slot]);
-  };
-  auto store_row = [&](int k, int yc) {
-    if (n_bulk <= 0) return;
-    float* dst = fout + P.off + (long long)yc * pitch + GHOST + x0;
-#pragma unroll
-    for (int q = 0; q < Q; ++q)
-      bulk_s2g(dst + (long long)q * plane, outs + ((size_t)k * Q + q) * PSW,
-               (uint32_t)(n_bulk * sizeof(float)));
-    bulk_commit();
   };
 
   int issued = 0, islot = 0;  // rows issued and the slot of the next one (issuer only)
@@ -866,14 +856,11 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
   const int last = nload - 2;
   int s = 1;
   for (; s <= last; ++s) {
-    if (issuer) {
-      if (s >= 2 && issued < nload) {
-        fence_proxy_async_smem();
-        issue_row(issued, islot);
-        ++issued;
-        islot = islot + 1 == NS ? 0 : islot + 1;
-      }
-      if (MODE == MODE_STEP && ST) bulk_wait_read_all();
+    if (issuer && s >= 2 && issued < nload) {
+      fence_proxy_async_smem();  // our reads of the freed slot precede the new copy
+      issue_row(issued, islot);
+      ++issued;
+      islot = islot + 1 == NS ? 0 : islot + 1;
     }
     while (waited <= s + 1) {
       if (!mbar_wait_bounded(&bars[wslot], wphase)) s_abort = 1;
@@ -933,7 +920,6 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
     }
     __syncthreads();
     if (s_abort) break;
-    if (MODE == MODE_STEP && ST && issuer && s >= 4) store_row((s - 1) & 1, rstart + (s - 2) * dir);
 
     if (s >= 3 && owner) {
       const int yc = rstart + (s - 1) * dir;
@@ -961,12 +947,7 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
         const bool ok1 = cur_rho.y > 0.f && cur_rho.y < INFINITY;
         flag_bad |= !ok0 || (xa + 1 < xend && !ok1);
         float* dst = fout + P.off + (long long)yc * pitch + GHOST;
-        if (ST) {
-          float* ost = outs + (size_t)(s & 1) * Q * PSW + c0;
-#pragma unroll
-          for (int q = 0; q < Q; ++q) *reinterpret_cast<float2*>(ost + q * PSW) = h[q];
-          fence_proxy_async_smem();
-        } else if (xa + 1 < xend) {
+        if (xa + 1 < xend) {
           // both columns from registers: xa is even, so the pair is 8-byte aligned
 #pragma unroll
           for (int q = 0; q < Q; ++q)
@@ -978,12 +959,11 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
               *reinterpret_cast<float2*>(dst + (long long)q * plane + gpair) = h[q];
           }
         }
-        const bool tail = ST ? c0 + 2 > n_bulk : xa + 1 >= xend;
-        const bool ghost_here = ST ? (xa < 2 || xa + 1 >= nx - 2) : ghost_slow;
-        if (tail || ghost_here) {
-          // Columns not covered above (past the last full group of four when staged, the
-          // odd last column otherwise), and the ghost copies -2, -1, nx, nx+1 of the
-          // columns they mirror, are written directly.
+        const bool tail = xa + 1 >= xend;
+        if (tail || ghost_slow) {
+          // The odd last column (not covered above), and the ghost copies -2, -1, nx,
+          // nx+1 of the columns they mirror when they are not written as pairs, column by
+          // column.
 #pragma unroll
           for (int k = 0; k < 2; ++k) {
             const int x = xa + k;
@@ -991,11 +971,11 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
             float v[Q];
 #pragma unroll
             for (int q = 0; q < Q; ++q) v[q] = k == 0 ? h[q].x : h[q].y;
-            if (ST ? c0 + k >= n_bulk : tail) {
+            if (tail) {
 #pragma unroll
               for (int q = 0; q < Q; ++q) dst[(long long)q * plane + x] = v[q];
             }
-            if ((ST || !ghost_pairs) && (x < 2 || x >= nx - 2)) {
+            if (!ghost_pairs && (x < 2 || x >= nx - 2)) {
               auto put = [&](int g) {
                 if (wrapi(g, nx) == x) {
 #pragma unroll
@@ -1057,19 +1037,11 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
         const int j = issued - 1 - ((issued - 1 - k) % NS);
         mbar_wait_bounded(&bars[k], (uint32_t)((j / NS) & 1));
       }
-      if (MODE == MODE_STEP && ST) bulk_wait_all();
       atomicOr(status, STATUS_TIMEOUT);
     }
     return;
   }
   if (MODE == MODE_STEP) {
-    if (ST) {
-      __syncthreads();
-      if (issuer) {
-        if (last >= 3) store_row(last & 1, rstart + (last - 1) * dir);
-        bulk_wait_all();
-      }
-    }
     if (flag_bad) atomicOr(status, STATUS_NONFINITE);
   } else if (mo.flags & MOM_DIAG) {
     double sm = acc_m.value(), sx = acc_x.value(), sy = acc_y.value();
