@@ -328,7 +328,8 @@ const char* lbm_batch_last_error(const lbm_batch* b);
 /* Equilibrium initialisation of instance i from host fields, as lbm_init_fields. */
 int lbm_batch_init_fields(lbm_batch* b, int i, const double* rho, const double* ux,
                           const double* uy);
-/* Advance every active instance n steps (one launch per step, CUDA-graph replay). */
+/* Advance every active instance n steps (one launch per step and kernel width, CUDA-graph
+ * replay; see lbm_batch_launches_per_step). */
 int lbm_batch_step(lbm_batch* b, int n);
 /* Float host variant of lbm_batch_init_fields, as lbm_init_fields_f32. */
 int lbm_batch_init_fields_f32(lbm_batch* b, int i, const float* rho, const float* ux,

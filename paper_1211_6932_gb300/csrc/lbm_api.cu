@@ -2,8 +2,9 @@
 //
 // Every lattice, single or batched, is an instance of one Batch: the populations of all
 // instances live in two slabs (ping-pong), each instance with its own padded planes; one
-// launch of the fused sweep kernel advances every active instance by one step, and runs of
-// steps are replayed from a captured CUDA graph.
+// launch of the fused sweep kernel advances every active instance by one step (one launch
+// per kernel width under per-instance tiling, the widths as parallel graph branches), and
+// runs of steps are replayed from a captured CUDA graph.
 #include <cuda_runtime.h>
 
 #include <nvtx3/nvToolsExt.h>

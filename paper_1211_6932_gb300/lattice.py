@@ -412,7 +412,8 @@ class Instance:
 
 
 class Batch:
-    """Many independent lattices advanced by one launch per step (lbm_batch_*)."""
+    """Many independent lattices advanced together, one launch per step and kernel width
+    (lbm_batch_*)."""
 
     def __init__(self, instances, precision="fp32", stream=None, tile_threads=0, tile_rows=0,
                  device=None, tile_vec=0):
