@@ -81,6 +81,33 @@ def test_fp32_per_step_parity(nt, vec, walls):
             f = ref
 
 
+@pytest.mark.parametrize("nx,ny", [(1, 7), (5, 3), (3, 40), (4, 9), (254, 5), (253, 33)])
+@pytest.mark.parametrize("walls", [False, True])
+def test_fp32_pair_kernel_degenerate_and_ragged_widths(nx, ny, walls):
+    """The default FP32 pair kernel on widths where the ghost copies overlap the owned
+    columns (nx < 4), odd widths (column-by-column ghosts and tails), even widths one
+    strip wide (paired ghosts) and a width one column past a 252-column strip."""
+    if walls and ny < 5:
+        pytest.skip("wall runs need a few fluid rows")
+    c = pairs.case(nx, ny, tr=0.7, sigma=0.114, walls=walls)
+    p = pairs.oracle_params(c)
+    rl, rv = pairs.maxwell(c)
+    rng = np.random.default_rng(nx * 100 + ny)
+    rho = rv + (rl - rv) * rng.uniform(0.0, 1.0, (ny, nx))
+    f = oracle.equilibrium(rho, 0.01 * rng.uniform(-1, 1, rho.shape),
+                           0.01 * rng.uniform(-1, 1, rho.shape))
+    with pairs.gpu_lattice(c, "fp32") as L:
+        L.set_populations(f)
+        for k in range(2):
+            f_in = L.get_populations()
+            L.step(1)
+            got = L.get_populations()
+            ref = oracle.run(p, f_in, 1)
+            ok, err = fp32_close(got, ref, oracle.fields(p, f_in)["rho"])
+            assert ok, (k, err)
+        L.check_guards()
+
+
 def test_fp32_psi_fp64_option_matches():
     c = pairs.case(64, 64, tr=0.6, sigma=0.114)
     p = pairs.oracle_params(c)
