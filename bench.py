@@ -581,8 +581,9 @@ def run_gpu(args):
 
 def other_workloads(stream):
     """MLUPS of the other configurations, reported beside the headline (not roofline
-    evidence: c1 is latency-bound, c2 and c3 fit in L2), of the FP64 parity mode on the
-    4096^2 field (144 B per lattice update) and of the 256-instance batch (c4, autotuned,
+    evidence: the 128^2 droplet is latency-bound, the ellipse and the splash fit in L2), of
+    the FP64 parity mode on the 4096^2 field (144 B per lattice update) and of the
+    256-instance batch (autotuned,
     640 graph-replayed steps).  Each: 3 warm-up steps and a 64-step graph
     capture, then `steps` steps timed with CUDA events on the lattice's stream."""
     import torch
@@ -618,22 +619,22 @@ def other_workloads(stream):
         out.append(rec)
 
     tau8 = (1.0, 1.1, 1.1, 1.0, 1.1, 1.0, 1.1, 1.25, 1.25)  # Sec. IV A, tau_nu = 0.8
-    # c1: 128^2 droplet, FP64
+    # 128^2 stationary droplet, FP64
     e = Eos(a=0.25, T=0.7 * wl.t_crit(0.25))
     rl, rv = maxwell(e)
     with Lattice(128, 128, e, sigma=0.114, s=tau8, precision="fp64", stream=stream) as L:
         L.init_fields(wl.droplet(128, 128, rl, rv, 30.0, 4.0))
-        timed("c1_droplet_128x128_fp64", L, 5000, 128 * 128, "f64", 144,
+        timed("droplet_128x128_fp64", L, 5000, 128 * 128, "f64", 144,
               "1.2 MB of state: latency-bound; autotuned tiling", tune=True)
-    # c2: 1024^2 oscillating ellipse, linear viscosity
+    # 1024^2 oscillating ellipse, linear viscosity
     e = Eos(a=0.25, T=0.6 * wl.t_crit(0.25))
     rl, rv = maxwell(e)
     with Lattice(1024, 1024, e, sigma=0.114, s=RATES, nu_l=0.05, nu_v=0.5,
                  visc_mode="linear", precision="fp32", stream=stream) as L:
         L.init_fields(wl.ellipse(1024, 1024, rl, rv, 240, 160, 4.0, noise=1e-4, seed=2))
-        timed("c2_ellipse_1024x1024_fp32", L, 2000, 1024 * 1024, "f32", 72,
+        timed("ellipse_1024x1024_fp32", L, 2000, 1024 * 1024, "f32", 72,
               "75 MB of state: L2-resident; autotuned tiling", tune=True)
-    # c3: 2048 x 512 splash with walls, step viscosity, Re = 200, ratio 15
+    # 2048 x 512 splash with walls, step viscosity, Re = 200, ratio 15
     e = Eos(a=0.25, T=0.5 * wl.t_crit(0.25))
     rl, rv = maxwell(e)
     nu_l = 0.05 * 160 / 200
@@ -642,25 +643,25 @@ def other_workloads(stream):
                  stream=stream) as L:
         rho, ux, uy = wl.splash(2048, 512, rl, rv, 4.0, 32, 160, 0.05)
         L.init_fields(rho, ux, uy)
-        timed("c3_splash_2048x512_walls_fp32", L, 2000, 2048 * 512, "f32", 72,
+        timed("splash_2048x512_walls_fp32", L, 2000, 2048 * 512, "f32", 72,
               "75 MB of state: L2-resident; autotuned tiling", tune=True)
-    # c5 field, FP32 storage with psi of Eq. 24 evaluated in FP64 (the psi_fp64 option)
+    # the 4096^2 field, FP32 storage with psi of Eq. 24 evaluated in FP64 (psi_fp64 option)
     e = Eos(a=A, T=eos_T(), b=B, R=R)
     rl, rv = maxwell(e)
     with Lattice(NX, NY, e, sigma=SIGMA, s=RATES, nu_l=NU_L, nu_v=NU_V, visc_mode="linear",
                  precision="fp32", psi_fp64=True, stream=stream) as L:
         L.init_fields(field(rl, rv))
-        timed("c5_droplets64_%dx%d_fp32_psi_fp64" % (NX, NY), L, 500, NX * NY, "f32", 72,
+        timed("droplets64_%dx%d_fp32_psi_fp64" % (NX, NY), L, 500, NX * NY, "f32", 72,
               "FP32 storage and arithmetic, psi in FP64")
-    # c5 field in the FP64 parity mode
+    # the 4096^2 field in the FP64 parity mode
     e = Eos(a=A, T=eos_T(), b=B, R=R)
     rl, rv = maxwell(e)
     with Lattice(NX, NY, e, sigma=SIGMA, s=RATES, nu_l=NU_L, nu_v=NU_V, visc_mode="linear",
                  precision="fp64", stream=stream) as L:
         L.init_fields(field(rl, rv))
-        timed("c5_droplets64_%dx%d_fp64" % (NX, NY), L, 200, NX * NY, "f64", 144,
+        timed("droplets64_%dx%d_fp64" % (NX, NY), L, 200, NX * NY, "f64", 144,
               "FP64 populations and arithmetic (the 1e-12 parity mode)")
-    # c4: the 256-instance batch (autotuned tiling), one GPU
+    # the 256-instance batch (autotuned tiling), one GPU
     from paper_1211_6932_gb300 import Batch
     insts, fields, n_total = batch256_instances()
     b = Batch(insts, precision="fp32", stream=stream)
@@ -679,7 +680,7 @@ def other_workloads(stream):
         ms = e0.elapsed_time(e1) / 640
         bad = sum(d["nonfinite"] for d in b.diagnostics())
         peak, kind = load_peak()
-        out.append({"workload": "c4_batch256_64to512_fp32", "nodes": n_total, "dtype": "f32",
+        out.append({"workload": "batch256_64to512_fp32", "nodes": n_total, "dtype": "f32",
                     "steps": 640, "ms_per_step": ms, "mlups": n_total / (ms * 1e-3) / 1e6,
                     "hbm_frac": 72 * n_total / (ms * 1e-3) / 1e9 / peak, "peak_source": kind,
                     "note": "256 ragged instances, %.2f GB of state" % (72 * n_total / 1e9),
@@ -842,7 +843,8 @@ def main():
     ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-workloads", action="store_true",
-                    help="skip the MLUPS of configurations c1-c3 and of the FP64 mode")
+                    help="skip the MLUPS of the other workloads (droplet, ellipse, splash, "
+                         "batch) and of the FP64 mode")
     ap.add_argument("--no-warm-start", action="store_true",
                     help="skip the learned warm-start comparison (4096^2, 1 GPU only)")
     ap.add_argument("--workload", default="field4096", choices=["field4096", "batch256"],

@@ -119,7 +119,7 @@ class Spread:
 
 def splash_spread(nx=2048, ny=512, film=32, d=160.0, u=0.05, re=200.0, ratio=15.0, a=0.25,
                   t_over_tc=0.5, sigma=0.114, t_max=1.0, samples=20, stream=None):
-    """The splash of the c3 workload (walls, step viscosity, s_e = s_zeta = 0.8): the
+    """The 2048 x 512 splash workload (walls, step viscosity, s_e = s_zeta = 0.8): the
     spread radius r(t), half the x-extent of liquid (rho above the mean of the phase
     densities) on the row one film thickness plus one above the wall, against t* = U t / D
     from the first contact; C by least squares of r/D on sqrt(t*)."""

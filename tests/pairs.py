@@ -7,7 +7,7 @@ from oracle import thermo
 from paper_1211_6932_gb300 import workloads as wl
 
 B, R = 4.0, 1.0
-RATES_C1 = (1.0, 1.0, 1.1, 1.0, 1.1, 1.0, 1.1, 1.0, 1.0)
+RATES_TAU1 = (1.0, 1.0, 1.1, 1.0, 1.1, 1.0, 1.1, 1.0, 1.0)
 
 
 def case(nx, ny, a=0.25, tr=0.7, sigma=0.114, s=None, visc="const", nu_l=0.0, nu_v=0.0,

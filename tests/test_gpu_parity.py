@@ -121,11 +121,11 @@ def test_fp32_psi_fp64_option_matches():
         assert ok, err
 
 
-def test_fp64_config1_full_run():
-    """Config 1 in full: the 128^2 droplet (a = 0.25, T = 0.7 T_c, sigma = 0.114, r0 = 30,
+def test_fp64_droplet_128_full_run():
+    """The 128^2 stationary droplet in full (a = 0.25, T = 0.7 T_c, sigma = 0.114, r0 = 30,
     W = 4, tau = 1) for 5000 steps in FP64 against the oracle: the per-step bound of
     1e-12 leaves the whole run within 1e-10 relative (measured far below)."""
-    c = pairs.case(128, 128, a=0.25, tr=0.7, sigma=0.114, s=pairs.RATES_C1)
+    c = pairs.case(128, 128, a=0.25, tr=0.7, sigma=0.114, s=pairs.RATES_TAU1)
     p = pairs.oracle_params(c)
     f = pairs.droplet_state(c, r0=30, W=4.0)
     ref = oracle.run(p, f, 5000)
@@ -140,7 +140,7 @@ def test_fp32_droplet_run_density_and_coexistence():
     """128^2 stationary droplet (a = 0.25, T = 0.7 T_c, sigma = 0.114, tau = 1): after
     3000 steps the FP32 density is within 1e-4 (max relative) of the FP64 oracle and the
     liquid/vapour densities within 1e-3."""
-    c = pairs.case(128, 128, a=0.25, tr=0.7, sigma=0.114, s=pairs.RATES_C1)
+    c = pairs.case(128, 128, a=0.25, tr=0.7, sigma=0.114, s=pairs.RATES_TAU1)
     p = pairs.oracle_params(c)
     f = pairs.droplet_state(c, r0=30, W=4.0)
     steps = 3000
