@@ -1,23 +1,35 @@
 // Launchers of the step and helper kernels for one storage type (included once per type).
 #pragma once
+#include <atomic>
+
 #include "lbm_aux.cuh"
 #include "lbm_internal.h"
 
 namespace lbm {
+
+// Set a kernel's dynamic shared-memory limit once per device: the attribute belongs to the
+// current device's context, so `done` keeps one bit per device ordinal (below 64; others
+// are set on every launch).
+template <typename F>
+static cudaError_t ensure_smem_attr(F* fn, size_t smem, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+  if (bit && (done.load(std::memory_order_relaxed) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && bit) done.fetch_or(bit);
+  return e;
+}
 
 template <typename S, int NT, int MODE>
 static cudaError_t launch_sweep_cfg(const S* fin, S* fout, const InstParams* d_inst,
                                     const WorkItem* d_items, int n_items, const MomArgs<S>& mo,
                                     int* d_status, cudaStream_t st) {
   constexpr size_t smem = SweepCfg<S, NT>::BYTES;
-  static bool configured = false;  // one attribute call per instantiation and process
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<S, NT, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static std::atomic<unsigned long long> done{0};
+  cudaError_t e = ensure_smem_attr(sweep_kernel<S, NT, MODE>, smem, done);
+  if (e != cudaSuccess) return e;
   if (n_items <= 0) return cudaSuccess;
   sweep_kernel<S, NT, MODE><<<n_items, NT, smem, st>>>(fin, fout, d_inst, d_items, n_items,
                                                        mo, d_status);
@@ -41,14 +53,9 @@ static cudaError_t launch_sweep2_cfg(const float* fin, float* fout, const InstPa
                                      const WorkItem* d_items, int n_items,
                                      const MomArgs<float>& mo, int* d_status, cudaStream_t st) {
   constexpr size_t smem = Sweep2Cfg<NT>::BYTES;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(sweep2_kernel<NT, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static std::atomic<unsigned long long> done{0};
+  cudaError_t e = ensure_smem_attr(sweep2_kernel<NT, MODE>, smem, done);
+  if (e != cudaSuccess) return e;
   if (n_items <= 0) return cudaSuccess;
   sweep2_kernel<NT, MODE><<<n_items, NT, smem, st>>>(fin, fout, d_inst, d_items, n_items, mo,
                                                      d_status);
