@@ -386,6 +386,12 @@ int lbm_batch_check_guards(lbm_batch* b);
  */
 int lbm_debug_fail_alloc(int n);
 
+/* 1 in the bounds-check build of the library (kernels compiled with LBM_BOUNDS_CHECK:
+ * every global and shared-memory access of the step kernels is index-checked; an access
+ * that fails its check is skipped and the next status check returns LBM_ECORRUPT), 0 in
+ * the normal build. */
+int lbm_bounds_checked(void);
+
 /* Device allocations made by lattice and batch handles and not yet released
  * (process-wide): returns to its earlier value once every handle created since is
  * destroyed, whether or not its calls failed. */

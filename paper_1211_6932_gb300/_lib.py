@@ -4,6 +4,9 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblbm_gb300.so")
+# the bounds-check build (kernels compiled with -DLBM_BOUNDS_CHECK), selected by
+# LBM_LIBRARY=check in the environment
+CHECK_LIB_PATH = os.path.join(HERE, "liblbm_gb300_check.so")
 
 c_int, c_double, c_void_p, c_size_t, c_longlong = (ctypes.c_int, ctypes.c_double,
                                                    ctypes.c_void_p, ctypes.c_size_t,
@@ -114,6 +117,7 @@ SIGNATURES = {
     "lbm_batch_init_fields_f32": (c_int, [c_void_p, c_int, fptr, fptr, fptr]),
     "lbm_batch_moments_f32": (c_int, [c_void_p, c_int, fptr, fptr, fptr]),
     "lbm_check_guards": (c_int, [c_void_p]),
+    "lbm_bounds_checked": (c_int, []),
     "lbm_batch_check_guards": (c_int, [c_void_p]),
     "lbm_debug_fail_alloc": (c_int, [c_int]),
     "lbm_debug_live_allocs": (ctypes.c_longlong, []),
@@ -147,9 +151,12 @@ SIGNATURES = {
 _LIB = None
 
 
-def load(path: str = LIB_PATH):
-    """Load the library (no build, no fallback: a missing library is an error)."""
+def load(path: str = None):
+    """Load the library (no build, no fallback: a missing library is an error).  The
+    default is the normal build, or the bounds-check build when LBM_LIBRARY=check."""
     global _LIB
+    if path is None:
+        path = CHECK_LIB_PATH if os.environ.get("LBM_LIBRARY") == "check" else LIB_PATH
     if _LIB is None:
         if not os.path.exists(path):
             raise RuntimeError("CUDA library %s is missing; run __graft_entry__.build() or "

@@ -13,6 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbm_gb300.so")
+CHECK_LIB = os.path.join(HERE, "liblbm_gb300_check.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"]
@@ -44,20 +45,26 @@ def _headers():
     return hs
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile (only what changed) and link; returns the library path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, check: bool = False) -> str:
+    """Compile (only what changed) and link; returns the library path.  check=True builds
+    the bounds-check variant (kernels compiled with -DLBM_BOUNDS_CHECK: every global and
+    shared-memory access of the step kernels is index-checked and a failure is reported as
+    LBM_ECORRUPT) into liblbm_gb300_check.so, beside the normal library."""
+    build_dir = BUILD + ("_check" if check else "")
+    lib = CHECK_LIB if check else LIB
+    flags = NVCC_FLAGS + (["-DLBM_BOUNDS_CHECK"] if check else [])
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
     hdrs = _headers()
     jobs = []
     objs = []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + hdrs):
-            cmd = [cc] + ARCH + NVCC_FLAGS + ["-c", src, "-o", obj]
+            cmd = [cc] + ARCH + flags + ["-c", src, "-o", obj]
             if src.endswith(".cpp"):
-                cmd = [cc] + NVCC_FLAGS + ["-x", "c++", "-c", src, "-o", obj]
+                cmd = [cc] + flags + ["-x", "c++", "-c", src, "-o", obj]
             jobs.append(cmd)
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
@@ -69,13 +76,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
                     print(res.stdout + res.stderr)
                 if res.returncode != 0:
                     raise RuntimeError("nvcc failed on %s" % cmd[-3])
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + ".tmp%d" % os.getpid()
         subprocess.run([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static"],
                        check=True)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose=True))
+    import sys
+    print(build(verbose=True, check="--check" in sys.argv[1:]))

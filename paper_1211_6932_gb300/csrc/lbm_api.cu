@@ -697,6 +697,10 @@ int sync_status(Batch* b) {
   CK(b, cudaStreamSynchronize(b->stream));
   int st = 0;
   CK(b, cudaMemcpy(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st & lbm::STATUS_BOUNDS)
+    return set_err(b->err, LBM_ECORRUPT,
+                   "a kernel index check failed (bounds-check build): an access outside its "
+                   "buffer was skipped");
   if (st & lbm::STATUS_TIMEOUT)
     return set_err(b->err, LBM_ETIMEOUT,
                    "a bounded wait for a shared-memory copy ran out in the step kernel");
@@ -1867,6 +1871,14 @@ int lbm_batch_check_guards(lbm_batch* b) {
 int lbm_debug_fail_alloc(int n) { return g_fail_after.exchange(n < 0 ? -1 : n); }
 
 long long lbm_debug_live_allocs(void) { return g_live_allocs.load(); }
+
+int lbm_bounds_checked(void) {
+#ifdef LBM_BOUNDS_CHECK
+  return 1;
+#else
+  return 0;
+#endif
+}
 
 int lbm_debug_corrupt_guard(lbm_handle* h, int which) {
   DeviceGuard g_(h ? &h->b : nullptr);

@@ -54,7 +54,21 @@ __host__ __device__ constexpr double tw_of(int q) {
 enum { VISC_CONST = 0, VISC_STEP = 1, VISC_LINEAR = 2 };
 enum { MODE_STEP = 0, MODE_MOMENTS = 1 };
 enum { MOM_FIELDS = 1, MOM_DIAG = 2, MOM_UPDATE_PREV = 4 };
-enum { STATUS_NONFINITE = 1, STATUS_TIMEOUT = 2 };
+enum { STATUS_NONFINITE = 1, STATUS_TIMEOUT = 2, STATUS_BOUNDS = 4 };
+
+// Index checks of the bounds-check build (-DLBM_BOUNDS_CHECK, a stand-in for a memory
+// sanitizer): LBM_IN(ok) is ok, and a false ok sets STATUS_BOUNDS in the kernel's status
+// word; the caller skips the access it guards.  In the normal build LBM_IN(ok) is true and
+// the checks compile away.
+#ifdef LBM_BOUNDS_CHECK
+__device__ __forceinline__ bool lbm_in_bounds(bool ok, int* status) {
+  if (!ok) atomicOr(status, STATUS_BOUNDS);
+  return ok;
+}
+#define LBM_IN(ok) ::lbm::lbm_in_bounds((ok), status)
+#else
+#define LBM_IN(ok) true
+#endif
 
 // Physical parameters in the arithmetic type of a kernel, prepared on the host so the
 // kernels convert nothing (double-to-float conversions run on the slow FP64 pipe).
@@ -504,7 +518,10 @@ __global__ void __launch_bounds__(NT, MinBlocks<S, NT>::value) sweep_kernel(
     const int r = rstart + j * dir;
     const int rp = walls ? (r < 0 ? 0 : (r >= ny ? ny - 1 : r)) : wrapi(r, ny);
     const S* src = gsrc + (long long)rp * pitch;
-    mbar_arrive_expect_tx(&bars[slot], plane_bytes * Q);
+    const bool ok = LBM_IN(rp >= 0 && rp < ny && seg0 >= 0 && len > 0 && len <= SEG &&
+                           seg0 + len <= pitch);  // bounds-check build
+    mbar_arrive_expect_tx(&bars[slot], ok ? plane_bytes * Q : 0u);
+    if (!ok) return;
 #pragma unroll
     for (int q = 0; q < Q; ++q)
       bulk_g2s(ring + ((size_t)slot * Q + q) * SEG, src + (long long)q * plane, plane_bytes,
@@ -513,6 +530,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<S, NT>::value) sweep_kernel(
   // Bulk store of the staged output row of centre row yc (out slot k).
   auto store_row = [&](int k, int yc) {
     if (n_bulk <= 0) return;
+    if (!LBM_IN(yc >= 0 && yc < ny && x0 >= 0 && GHOST + x0 + n_bulk <= pitch)) return;
     S* dst = fout + P.off + (long long)yc * pitch + GHOST + x0;
 #pragma unroll
     for (int q = 0; q < Q; ++q)
@@ -628,12 +646,15 @@ __global__ void __launch_bounds__(NT, MinBlocks<S, NT>::value) sweep_kernel(
           // Columns past the last full group of four, and the ghost copies -2, -1, nx,
           // nx+1 of the columns they mirror, are written directly.
           S* dst = fout + P.off + (long long)yc * pitch + GHOST;
-          if (c >= n_bulk) {
+          auto col_ok = [&](int col) {  // bounds-check build
+            return LBM_IN(yc >= 0 && yc < ny && col >= -GHOST && col < pitch - GHOST);
+          };
+          if (c >= n_bulk && col_ok(x)) {
 #pragma unroll
             for (int q = 0; q < Q; ++q) dst[(long long)q * plane + x] = (S)h[q];
           }
           auto put = [&](int g) {
-            if (wrapi(g, nx) == x) {
+            if (wrapi(g, nx) == x && col_ok(g)) {
 #pragma unroll
               for (int q = 0; q < Q; ++q) dst[(long long)q * plane + g] = (S)h[q];
             }
@@ -653,12 +674,13 @@ __global__ void __launch_bounds__(NT, MinBlocks<S, NT>::value) sweep_kernel(
         const R ir = (R)1 / cur_rho;
         const R ux = px * ir, uy = py * ir;
         const long long di = P.dense_off + (long long)yc * nx + x;
-        if (mo.flags & MOM_FIELDS) {
+        const bool di_ok = LBM_IN(yc >= 0 && yc < ny && x >= 0 && x < nx);
+        if ((mo.flags & MOM_FIELDS) && di_ok) {
           if (mo.rho) mo.rho[di] = (S)cur_rho;
           if (mo.ux) mo.ux[di] = (S)ux;
           if (mo.uy) mo.uy[di] = (S)uy;
         }
-        if (mo.flags & MOM_DIAG) {
+        if ((mo.flags & MOM_DIAG) && di_ok) {
           if (!(isfinite(cur_rho) && isfinite(ux) && isfinite(uy))) {
             ++bad;
           } else {
@@ -669,7 +691,7 @@ __global__ void __launch_bounds__(NT, MinBlocks<S, NT>::value) sweep_kernel(
             if (mo.rho_prev) mx_d = fmaxf(mx_d, (float)fabs(cur_rho - mo.rho_prev[di]));
           }
         }
-        if ((mo.flags & MOM_UPDATE_PREV) && mo.rho_prev) mo.rho_prev[di] = (S)cur_rho;
+        if ((mo.flags & MOM_UPDATE_PREV) && mo.rho_prev && di_ok) mo.rho_prev[di] = (S)cur_rho;
       }
     }
 #pragma unroll
@@ -816,12 +838,20 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
   const uint32_t plane_bytes = (uint32_t)len * (uint32_t)sizeof(float);
   const float* gsrc = fin + P.off + seg0;
   const float2 rho_ref2 = N::k(ph.rho_ref);
+  // bounds-check build: this thread's psi pair, and an owner's psi neighbours -1 .. +2
+  const bool psi_ok = LBM_IN(2 + c0 >= 0 && 2 + c0 + 2 <= PSW);
+  const bool psi_nb_ok = !owner || LBM_IN(1 + c0 >= 0 && 2 + c0 + 3 <= PSW);
 
   auto issue_row = [&](int j, int slot) {
     const int r = rstart + j * dir;
     const int rp = walls ? (r < 0 ? 0 : (r >= ny ? ny - 1 : r)) : wrapi(r, ny);
     const float* src = gsrc + (long long)rp * pitch;
-    mbar_arrive_expect_tx(&bars[slot], plane_bytes * Q);
+    // source row inside the instance's planes, destination inside the ring
+    if (!LBM_IN(slot >= 0 && slot < NS)) return;
+    const bool ok = LBM_IN(rp >= 0 && rp < ny && seg0 >= 0 && len > 0 && len <= SEG &&
+                           seg0 + len <= pitch);
+    mbar_arrive_expect_tx(&bars[slot], ok ? plane_bytes * Q : 0u);
+    if (!ok) return;
 #pragma unroll
     for (int q = 0; q < Q; ++q)
       bulk_g2s(ring + ((size_t)slot * Q + q) * SEG, src + (long long)q * plane, plane_bytes,
@@ -890,7 +920,10 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
         for (int q = 0; q < Q; ++q) {
           const int eyq = ey_of(q), exq = ex_of(q);
           const float* src = (eyq > 0 ? rowS : (eyq < 0 ? rowN : rowC)) + q * SEG - exq;
-          nxt[q] = exq == 0 ? pair_at(src) : make_float2(src[0], src[1]);
+          if (!LBM_IN(src >= ring && src + 2 <= ring + NS * Q * SEG))
+            nxt[q] = N::k(0.f);
+          else
+            nxt[q] = exq == 0 ? pair_at(src) : make_float2(src[0], src[1]);
         }
       } else {
 #pragma unroll
@@ -898,30 +931,37 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
           const int eyq = ey_of(q), exq = ex_of(q);
           const bool bb = (eyq > 0 && bb_low) || (eyq < 0 && bb_high);
           if (bb) {
-            nxt[q] = pair_at(rowC + opp_of(q) * SEG);
+            const float* src = rowC + opp_of(q) * SEG;
+            nxt[q] = LBM_IN(src >= ring && src + 2 <= ring + NS * Q * SEG) ? pair_at(src)
+                                                                          : N::k(0.f);
           } else {
             const float* src = (eyq > 0 ? rowS : (eyq < 0 ? rowN : rowC)) + q * SEG - exq;
-            nxt[q] = exq == 0 ? pair_at(src) : make_float2(src[0], src[1]);
+            if (!LBM_IN(src >= ring && src + 2 <= ring + NS * Q * SEG))
+              nxt[q] = N::k(0.f);
+            else
+              nxt[q] = exq == 0 ? pair_at(src) : make_float2(src[0], src[1]);
           }
         }
       }
       ndr = (nxt[0] + (nxt[1] + nxt[3])) + ((nxt[2] + nxt[4]) + ((nxt[5] + nxt[7]) + (nxt[6] + nxt[8])));
       nrho = rho_ref2 + ndr;
-      *reinterpret_cast<float2*>(ps_now + 2 + c0) = psi_t<float2, float>(nrho, ph);
-      if (walls && s == 2) {
-        const int rfirst = rstart + dir;
-        if (rfirst < 0 || rfirst >= ny)
-          *reinterpret_cast<float2*>(psis + (1 & (PSI_ROWS - 1)) * PSW + 2 + c0) =
-              *reinterpret_cast<const float2*>(ps_now + 2 + c0);
+      if (psi_ok) {
+        *reinterpret_cast<float2*>(ps_now + 2 + c0) = psi_t<float2, float>(nrho, ph);
+        if (walls && s == 2) {
+          const int rfirst = rstart + dir;
+          if (rfirst < 0 || rfirst >= ny)
+            *reinterpret_cast<float2*>(psis + (1 & (PSI_ROWS - 1)) * PSW + 2 + c0) =
+                *reinterpret_cast<const float2*>(ps_now + 2 + c0);
+        }
       }
-    } else if (s > 1) {
+    } else if (s > 1 && psi_ok) {
       *reinterpret_cast<float2*>(ps_now + 2 + c0) =
           *reinterpret_cast<const float2*>(psis + ((s - 1) & (PSI_ROWS - 1)) * PSW + 2 + c0);
     }
     __syncthreads();
     if (s_abort) break;
 
-    if (s >= 3 && owner) {
+    if (s >= 3 && owner && psi_nb_ok) {
       const int yc = rstart + (s - 1) * dir;
       const float* pa = psis + ((s - 2) & (PSI_ROWS - 1)) * PSW + 2 + c0;  // row yc - dir
       const float* pc = psis + ((s - 1) & (PSI_ROWS - 1)) * PSW + 2 + c0;  // row yc
@@ -947,12 +987,16 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
         const bool ok1 = cur_rho.y > 0.f && cur_rho.y < INFINITY;
         flag_bad |= !ok0 || (xa + 1 < xend && !ok1);
         float* dst = fout + P.off + (long long)yc * pitch + GHOST;
-        if (xa + 1 < xend) {
+        // bounds-check build: a storage column c of row yc lies in [-GHOST, pitch - GHOST)
+        auto col_ok = [&](int c, int n) {
+          return LBM_IN(yc >= 0 && yc < ny && c >= -GHOST && c + n <= pitch - GHOST);
+        };
+        if (xa + 1 < xend && col_ok(xa, 2)) {
           // both columns from registers: xa is even, so the pair is 8-byte aligned
 #pragma unroll
           for (int q = 0; q < Q; ++q)
             *reinterpret_cast<float2*>(dst + (long long)q * plane + xa) = h[q];
-          if (gpair != NO_GHOST) {
+          if (gpair != NO_GHOST && col_ok(gpair, 2)) {
             // the mirrored pair starts at an even column too (nx even)
 #pragma unroll
             for (int q = 0; q < Q; ++q)
@@ -971,13 +1015,13 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
             float v[Q];
 #pragma unroll
             for (int q = 0; q < Q; ++q) v[q] = k == 0 ? h[q].x : h[q].y;
-            if (tail) {
+            if (tail && col_ok(x, 1)) {
 #pragma unroll
               for (int q = 0; q < Q; ++q) dst[(long long)q * plane + x] = v[q];
             }
             if (!ghost_pairs && (x < 2 || x >= nx - 2)) {
               auto put = [&](int g) {
-                if (wrapi(g, nx) == x) {
+                if (wrapi(g, nx) == x && col_ok(g, 1)) {
 #pragma unroll
                   for (int q = 0; q < Q; ++q) dst[(long long)q * plane + g] = v[q];
                 }
@@ -997,7 +1041,7 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
           const int x = xa + k;
-          if (x >= xend) continue;
+          if (x >= xend || !LBM_IN(yc >= 0 && yc < ny && x >= 0 && x < nx)) continue;
           const float r = k == 0 ? cur_rho.x : cur_rho.y;
           const float mx = k == 0 ? px.x : px.y, my = k == 0 ? py.x : py.y;
           const float ux = mx / r, uy = my / r;
