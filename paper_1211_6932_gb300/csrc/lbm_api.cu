@@ -778,17 +778,15 @@ int init_instance(Batch* b, int i, const double* rho, const double* ux, const do
   if (e == cudaSuccess)
     e = b->fp64 ? lbm::launch_fill_ghosts<double>((double*)b->slab[b->cur], P, b->stream)
                 : lbm::launch_fill_ghosts<float>((float*)b->slab[b->cur], P, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream);
   int bad = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess)
     return set_err(b->err, LBM_ECUDA, "initialisation failed: %s", cudaGetErrorString(e));
-  // The other slab mirrors the state so frozen and active instances agree.
-  CK(b, cudaMemcpyAsync((char*)b->slab[b->cur ^ 1] + P.off * b->esz,
-                        (char*)b->slab[b->cur] + P.off * b->esz, 9 * P.plane * b->esz,
-                        cudaMemcpyDeviceToDevice, b->stream));
-  CK(b, cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream));
-  CK(b, cudaStreamSynchronize(b->stream));
+  // Nothing is copied into the other slab: the next step of an active instance writes
+  // every column it later reads there (the interior and the ghost pairs), and an instance
+  // is copied into both slabs when it is frozen (lbm_batch_run_to_equilibrium).
   b->steps[i] = 0;
   b->dinf_valid[i] = 0;
   if (!b->active[i]) {
