@@ -527,3 +527,59 @@ def test_x_uniform_film_is_independent_of_nx():
         f = oracle.run(p, oracle.equilibrium(wl.flat_film(nx, 40, rl, rv, 4.0, 20)), 100)
         outs.append(oracle.fields(p, f)["rho"])
     assert np.max(np.abs(outs[0][:, 0] - outs[1][:, 5])) < 1e-14
+
+
+# ---------------------------------------------------------------------- Eq. 32 (Lamb)
+def _energy_method_omega2(n, gamma, rho_l, r0, eps=1e-3, m=4096):
+    """omega^2 of mode n of an inviscid 2D liquid cylinder by Rayleigh's energy method,
+    computed by quadrature and finite differences, not from Eq. 32.
+
+    Shape r(theta) = c(e) (1 + e cos n theta), with c(e) chosen so the enclosed area stays
+    pi r0^2 exactly.  Potential energy = gamma * (perimeter - 2 pi r0), both integrals by
+    the periodic trapezoid rule (spectrally accurate); its second derivative in e at 0 by
+    central differences with Richardson extrapolation.  Kinetic energy = rho/2 * surface integral of phi dphi/dr for
+    the interior potential phi = (r0^2 de/dt / n) (r/r0)^n cos n theta whose normal
+    velocity at r = r0 is r0 de/dt cos n theta; its coefficient of (de/dt)^2 by the same
+    quadrature."""
+    th = 2.0 * np.pi * np.arange(m) / m
+    cosn, sinn = np.cos(n * th), np.sin(n * th)
+    dth = 2.0 * np.pi / m
+
+    def perimeter(e):
+        g = 1.0 + e * cosn
+        c = r0 / math.sqrt(0.5 * np.sum(g * g) * dth / math.pi)  # area = pi r0^2
+        r, dr = c * g, -c * e * n * sinn
+        return float(np.sum(np.sqrt(r * r + dr * dr)) * dth)
+
+    def d2(h):
+        return (perimeter(h) - 2.0 * perimeter(0.0) + perimeter(-h)) / (h * h)
+
+    d2pe = gamma * (4.0 * d2(eps / 2.0) - d2(eps)) / 3.0  # Richardson: O(eps^4) error
+    # KE = (rho/2) * int phi phi_r r0 dtheta with phi = (r0^2/n) cos, phi_r = r0 cos per
+    # unit de/dt: coefficient of (de/dt)^2 doubled gives the effective mass
+    mass = rho_l * float(np.sum((r0 * r0 / n) * cosn * r0 * cosn * r0) * dth)
+    return d2pe / mass
+
+
+@pytest.mark.parametrize("n", [2, 3, 5])
+def test_lamb_period_matches_energy_method(n):
+    """Eq. 32 against Rayleigh's energy method for the same cylinder, worked out by
+    numerical quadrature of the perimeter and of the flow's kinetic energy (no closed form
+    shared with the oracle): the periods agree to 1e-6 for modes 2, 3 and 5 at two
+    radii, tensions and densities."""
+    for gamma, rho_l, r0 in ((0.011, 0.4, 28.46), (0.0052, 0.2, 60.0)):
+        om2 = _energy_method_omega2(n, gamma, rho_l, r0)
+        expect = 2.0 * math.pi / math.sqrt(om2)
+        assert thermo.lamb_period(gamma, rho_l, r0, n) == pytest.approx(expect, rel=1e-6)
+
+
+def test_lamb_period_planar_capillary_limit():
+    """For large n the interface is locally flat: Eq. 32 must tend to the planar
+    capillary-wave dispersion omega^2 = gamma k^3 / rho_l with k = n / R0, the
+    relative difference falling like 1 / (2 n^2)."""
+    gamma, rho_l, r0 = 0.005, 0.41, 40.0
+    for n in (20, 200, 2000):
+        k = n / r0
+        planar = 2.0 * math.pi / math.sqrt(gamma * k ** 3 / rho_l)
+        rel = thermo.lamb_period(gamma, rho_l, r0, n) / planar - 1.0
+        assert rel == pytest.approx(0.5 / n ** 2, rel=0.02)
