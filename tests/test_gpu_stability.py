@@ -27,3 +27,34 @@ def test_stability_verdict_does_not_depend_on_precision():
     from paper_1211_6932_gb300 import stability as st
     trials = [(0.0045, 1.0), (0.006, 1.0), (0.0017, 20.0), (0.0025, 20.0)]
     assert st.stable_flags(trials, precision="fp32") == st.stable_flags(trials, precision="fp64")
+
+
+def test_stability_verdicts_match_oracle():
+    """The FP64 oracle, run on the host from its own initial state (Maxwell densities of
+    its quadrature rule, equilibrium populations of Eq. 3), gives the GPU's verdict at both
+    ends of the GPU's bracket for viscosity ratios 1 and 20 on the 600 x 250 splash at
+    t* = 3: stable at the bracket's upper end, unstable at its lower end.  This rules out
+    the GPU step as the cause of the distance between these brackets and Fig. 4."""
+    import numpy as np
+
+    import oracle
+    from oracle import thermo
+    from paper_1211_6932_gb300 import stability as st
+    from paper_1211_6932_gb300 import workloads as wl
+
+    br = st.lowest_stable_viscosity(ratios=(1.0, 20.0), rounds=2)
+    T = st.TR * st.TC
+    rl, rv, _ = thermo.maxwell(st.A, 4.0, 1.0, T)
+    rho, ux, uy = wl.splash(st.NX, st.NY, rl, rv, 4.0, st.FILM, st.D, st.U)
+    f0 = oracle.equilibrium(rho, ux, uy)
+    steps = int(round(3.0 * st.D / st.U))
+    for b in br:
+        assert b.unstable < b.stable
+        verdicts = []
+        for nu in (b.stable, b.unstable):
+            p = oracle.Params(nx=st.NX, ny=st.NY, a=st.A, T=T, sigma=st.SIGMA, s=st.RATES,
+                              visc_mode=oracle.VISC_STEP, nu_l=nu, nu_v=b.ratio * nu,
+                              rho_c=0.5218 / 4.0, walls=True)
+            d = oracle.fields(p, oracle.run(p, f0, steps))["rho"]
+            verdicts.append(bool(np.all(np.isfinite(d)) and d.min() > 0.0))
+        assert verdicts == [True, False], (b, verdicts)
