@@ -261,13 +261,35 @@ __device__ __forceinline__ float2 operator-(float2 a, float2 b) {
 }
 
 template <typename T> struct Num;
+// FP32 quotient and square root for psi (Eq. 24 with Eq. 30): the hardware approximations
+// (MUFU reciprocal and reciprocal square root) refined by one Newton-Raphson step each,
+// with the residual correction of Markstein.  The bare approximations are a few ulps off
+// with a consistent sign; psi enters the force of Eq. 7 as differences of neighbours, and
+// over 10^4 steps that bias moves interfaces measurably against FP64.  Refined, the
+// results are within about one ulp.  The collision keeps the bare reciprocal (1/rho and
+// 1/tau): refining those as well did not lower the long-run error (maximum relative
+// density error of the 1024^2 ellipse after 20000 steps: 8.8e-5 with, 6.3e-5 without).
+//   a/b:    r = ~1/b, r' = r + r (1 - b r), q = a r', q' = q + r' (a - b q)
+//   sqrt a: y = ~1/sqrt(a), s = a y, s' = s + (y/2) (a - s^2)
+__device__ __forceinline__ float div_nr(float a, float b) {
+  const float r0 = __fdividef(1.0f, b);
+  const float r = fmaf(r0, fmaf(-b, r0, 1.0f), r0);
+  const float q = a * r;
+  return fmaf(r, fmaf(-b, q, a), q);
+}
+__device__ __forceinline__ float sqrt_nr(float a) {  // a > 0
+  const float y = rsqrtf(a);
+  const float s = a * y;
+  return fmaf(0.5f * y, fmaf(-s, s, a), s);
+}
+
 template <> struct Num<float> {
   typedef float S;
   static __device__ __forceinline__ float k(float v) { return v; }
   static __device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
   static __device__ __forceinline__ float rcp(float a) { return __fdividef(1.0f, a); }
-  static __device__ __forceinline__ float div(float a, float b) { return a * __fdividef(1.0f, b); }
-  static __device__ __forceinline__ float sqrtp(float a) { return a > 0.f ? a * rsqrtf(a) : 0.f; }
+  static __device__ __forceinline__ float div(float a, float b) { return div_nr(a, b); }
+  static __device__ __forceinline__ float sqrtp(float a) { return a > 0.f ? sqrt_nr(a) : 0.f; }
   static __device__ __forceinline__ float clamp01(float a) { return fminf(fmaxf(a, 0.f), 1.f); }
   static __device__ __forceinline__ float sel_ge(float a, float t, float x, float y) {
     return a >= t ? x : y;
@@ -296,9 +318,19 @@ template <> struct Num<float2> {
   static __device__ __forceinline__ float2 rcp(float2 a) {
     return make_float2(__fdividef(1.0f, a.x), __fdividef(1.0f, a.y));
   }
-  static __device__ __forceinline__ float2 div(float2 a, float2 b) { return a * rcp(b); }
+  // div_nr and sqrt_nr on pairs (packed FFMA2 after the two scalar MUFU approximations)
+  static __device__ __forceinline__ float2 div(float2 a, float2 b) {
+    const float2 r0 = rcp(b);
+    const float2 nb = make_float2(-b.x, -b.y);
+    const float2 r = fma(r0, fma(nb, r0, k(1.f)), r0);
+    const float2 q = a * r;
+    return fma(r, fma(nb, q, a), q);
+  }
   static __device__ __forceinline__ float2 sqrtp(float2 a) {
-    return make_float2(Num<float>::sqrtp(a.x), Num<float>::sqrtp(a.y));
+    const float2 y = make_float2(rsqrtf(a.x), rsqrtf(a.y));
+    const float2 s = a * y;
+    const float2 t = fma(k(0.5f) * y, fma(make_float2(-s.x, -s.y), s, a), s);
+    return make_float2(a.x > 0.f ? t.x : 0.f, a.y > 0.f ? t.y : 0.f);
   }
   static __device__ __forceinline__ float2 clamp01(float2 a) {
     return make_float2(Num<float>::clamp01(a.x), Num<float>::clamp01(a.y));
