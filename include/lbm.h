@@ -213,22 +213,24 @@ int lbm_moments_device(lbm_handle* h, void* rho, void* ux, void* uy);
 int lbm_diagnostics(lbm_handle* h, lbm_diag* out);
 
 /*
- * Diagnostics for callers that must not allocate device memory: code that runs while a
- * CUDA graph is being captured (cudaMalloc is not allowed there), or code that lives
- * inside a fixed device-memory budget where allocation is forbidden or would fail.  The
- * paper has no counterpart; this is the lbm_diagnostics reduction with its per-CTA
- * partial sums held in one fixed device array compiled into the library (room for
- * LBM_NOALLOC_MAX_ITEMS work items, 36 bytes each, about 0.6 MB per GPU that loads the
- * library, kept until the process exits) instead of buffers owned by the handle.
+ * Diagnostics for callers that must not allocate device memory: a plug-in inside a host
+ * application that owns the whole device-memory budget (its pool has no room, or its
+ * rules forbid allocation), or a time-critical loop that cannot afford cudaMalloc and
+ * cudaFree, which may synchronise the device.  The paper has no counterpart; this is the
+ * lbm_diagnostics reduction with its per-CTA partial sums held in one fixed device array
+ * compiled into the library (room for LBM_NOALLOC_MAX_ITEMS work items, 36 bytes each,
+ * about 0.6 MB on every GPU that loads the library, kept until the process exits) instead
+ * of buffers owned by the handle.
  *   out_dev  caller-owned device memory for 6 doubles per instance: mass, mom_x, mom_y,
  *            max_u, 0 (dinf is not computed: the reference density of lbm_diagnostics
  *            is neither read nor updated), count of non-finite nodes.
  * Queued on the handle's stream and not synchronised; nothing is allocated, neither on
- * the device nor on the host.  The first call on a device looks up the array's device
- * address, so make that first call before any stream capture.  All calls in the process
- * share the one array and each call overwrites it (the part it uses is cleared first):
- * calls whose work can overlap on the GPU (other streams, other handles) race and must
- * be serialised by the caller.  Returns LBM_EINVAL if the lattice needs more work items
+ * the device nor on the host.  The first call on a device (and the first call after a
+ * device reset, in the new context) looks up the array's device address, so make that
+ * first call before any stream capture.  All calls in the process share the one array and
+ * each call overwrites it (the part it uses is cleared first): calls whose work can
+ * overlap on the GPU (other streams, other handles) race and must be serialised by the
+ * caller.  Returns LBM_EINVAL, with nothing queued, if the lattice needs more work items
  * than the array holds (see lbm_get_tiling; larger tiles need fewer items).
  */
 #define LBM_NOALLOC_MAX_ITEMS 16384
@@ -345,16 +347,36 @@ int lbm_batch_diagnostics(lbm_batch* b, lbm_diag* out);
 /*
  * Step until every instance is converged: an instance converges at the first check
  * where max |rho - rho 'check_every' steps earlier| < tol, after which it stops being
- * stepped (its state is frozen).  Checks run every check_every steps; at most max_steps
- * steps are taken.  steps_out (n entries, may be NULL) receives each instance's step
- * count at convergence, or -1 if it did not converge.  Returns the number of unconverged
- * instances (>= 0) or a negative error.
+ * stepped (its state is frozen).  An instance whose state turns non-finite or
+ * non-positive is retired at the next check the same way (it does not converge; its
+ * diagnostics keep reporting the non-finite nodes).  Checks run every check_every steps;
+ * at most max_steps steps are taken.  steps_out (n entries, may be NULL) receives each
+ * instance's step count at convergence, or -1 if it did not converge.  Returns the number
+ * of instances still being stepped (neither converged nor retired; >= 0) or a negative
+ * error.
  */
 int lbm_batch_run_to_equilibrium(lbm_batch* b, double tol, int check_every,
                                  long long max_steps, long long* steps_out);
 
 /* Number of instances still being stepped. */
 int lbm_batch_active(const lbm_batch* b);
+/* 1 if instance i is still being stepped, 0 if it is frozen (converged or retired),
+ * LBM_EINVAL for a bad handle or index. */
+int lbm_batch_instance_active(const lbm_batch* b, int i);
+
+/*
+ * Retirement of instances that are no longer to be stepped (a batch-runtime service; the
+ * paper has none).  lbm_batch_retire freezes instance i as convergence does: its state
+ * stays as it is, later steps and graph replays skip it, and lbm_batch_init_fields (or
+ * its float form) makes it active again.  lbm_batch_retire_nonfinite runs the
+ * diagnostics pass (as lbm_batch_diagnostics: synchronous, and it sets the reference of
+ * the next dinf) and retires every active instance that has a non-finite
+ * or non-positive density, so that the rest of the batch is stepped (and timed) without
+ * it; retired (n entries, may be NULL) receives 1 for each instance it retired, 0
+ * otherwise.  Returns the number retired (>= 0) or a negative error.
+ */
+int lbm_batch_retire(lbm_batch* b, int i);
+int lbm_batch_retire_nonfinite(lbm_batch* b, int* retired);
 
 /* lbm_autotune for a batch (all active instances are stepped together). */
 int lbm_batch_autotune(lbm_batch* b, int steps, const char* cache_path, int* threads,

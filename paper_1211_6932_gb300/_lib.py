@@ -107,6 +107,9 @@ SIGNATURES = {
     "lbm_batch_diagnostics": (c_int, [c_void_p, ctypes.POINTER(lbm_diag)]),
     "lbm_batch_run_to_equilibrium": (c_int, [c_void_p, c_double, c_int, c_longlong, llptr]),
     "lbm_batch_active": (c_int, [c_void_p]),
+    "lbm_batch_instance_active": (c_int, [c_void_p, c_int]),
+    "lbm_batch_retire": (c_int, [c_void_p, c_int]),
+    "lbm_batch_retire_nonfinite": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "lbm_batch_autotune": (c_int, [c_void_p, c_int, ctypes.c_char_p, ctypes.POINTER(c_int),
                                    ctypes.POINTER(c_int), ctypes.POINTER(c_int), dptr]),
     "lbm_batch_get_tiling": (c_int, [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int),

@@ -5,6 +5,7 @@
 // launch of the fused sweep kernel advances every active instance by one step (one launch
 // per kernel width under per-instance tiling, the widths as parallel graph branches), and
 // runs of steps are replayed from a captured CUDA graph.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <nvtx3/nvToolsExt.h>
@@ -1240,22 +1241,56 @@ static __device__ __align__(256) unsigned char
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
-void* g_noalloc_addr[kMaxDevices] = {};
+// Per device ordinal: the context that was current when the address was looked up, and
+// the address.  A device reset (cudaDeviceReset) destroys the primary context and a later
+// call runs in a new one, where the module is loaded again and the array may sit
+// elsewhere: a different current context triggers a fresh lookup.
+struct NoAllocSlot {
+  CUcontext ctx;
+  void* addr;
+};
+NoAllocSlot g_noalloc_slot[kMaxDevices] = {};
 
-// Device address of the array on the current device, looked up once per device.  Host
-// code must never use the symbol's name as a device pointer: it is a host-side stand-in.
+// cuCtxGetCurrent through the runtime's driver entry point (no link against libcuda);
+// it only reads the calling thread's current context and enqueues no work.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+
+int current_context(Batch* b, CUcontext* ctx) {
+  static std::once_flag once;
+  static CtxGetCurrentFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (CtxGetCurrentFn)p;
+  });
+  if (!fn) return set_err(b->err, LBM_ECUDA, "cuCtxGetCurrent is not available");
+  if (fn(ctx) != CUDA_SUCCESS) return set_err(b->err, LBM_ECUDA, "cuCtxGetCurrent failed");
+  return LBM_OK;
+}
+
+// Device address of the array on the current device, looked up once per device (and
+// again in a new context after a device reset).  Host code must never use the symbol's
+// name as a device pointer: it is a host-side stand-in.
 int noalloc_partials(Batch* b, unsigned char** out) {
   int dev = 0;
   CK(b, cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices)
     return set_err(b->err, LBM_EINVAL, "device %d beyond the %d supported", dev, kMaxDevices);
+  CUcontext ctx = nullptr;
+  int rc = current_context(b, &ctx);
+  if (rc) return rc;
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_addr[dev]) {
+  NoAllocSlot& slot = g_noalloc_slot[dev];
+  if (!slot.addr || slot.ctx != ctx) {
     void* p = nullptr;
     CK(b, cudaGetSymbolAddress(&p, g_noalloc_partials));
-    g_noalloc_addr[dev] = p;
+    slot.addr = p;
+    slot.ctx = ctx;
   }
-  *out = (unsigned char*)g_noalloc_addr[dev];
+  *out = (unsigned char*)slot.addr;
   return LBM_OK;
 }
 
@@ -1828,6 +1863,48 @@ int lbm_batch_active(const lbm_batch* b) {
   if (!b) return LBM_EINVAL;
   int n = 0;
   for (int a : b->b.active) n += a;
+  return n;
+}
+
+int lbm_batch_instance_active(const lbm_batch* b, int i) {
+  if (!b || i < 0 || i >= b->b.n_inst) return LBM_EINVAL;
+  return b->b.active[i] ? 1 : 0;
+}
+
+int lbm_batch_retire(lbm_batch* bb, int i) {
+  Range r_("lbm_batch_retire");
+  DeviceGuard g_(bb ? &bb->b : nullptr);
+  if (!bb) return LBM_EINVAL;
+  Batch* b = &bb->b;
+  if (i < 0 || i >= b->n_inst) return set_err(b->err, LBM_EINVAL, "instance %d out of range", i);
+  if (!b->active[i]) return LBM_OK;
+  int rc = freeze(b, i);
+  if (rc) return rc;
+  return rebuild_items(b);
+}
+
+int lbm_batch_retire_nonfinite(lbm_batch* bb, int* retired) {
+  Range r_("lbm_batch_retire_nonfinite");
+  DeviceGuard g_(bb ? &bb->b : nullptr);
+  if (!bb) return LBM_EINVAL;
+  Batch* b = &bb->b;
+  if (retired)
+    for (int i = 0; i < b->n_inst; ++i) retired[i] = 0;
+  std::vector<lbm_diag> d(b->n_inst);
+  int rc = diagnostics(b, d.data());
+  if (rc) return rc;
+  int n = 0;
+  for (int i = 0; i < b->n_inst; ++i) {
+    if (!b->active[i] || d[i].nonfinite == 0) continue;
+    rc = freeze(b, i);
+    if (rc) return rc;
+    if (retired) retired[i] = 1;
+    ++n;
+  }
+  if (n) {
+    rc = rebuild_items(b);
+    if (rc) return rc;
+  }
   return n;
 }
 

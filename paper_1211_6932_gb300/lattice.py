@@ -504,6 +504,21 @@ class Batch:
     def active(self):
         return self._check(self._L.lbm_batch_active(self._h))
 
+    def is_active(self, i):
+        """Whether instance i is still being stepped (lbm_batch_instance_active)."""
+        return bool(self._check(self._L.lbm_batch_instance_active(self._h, int(i))))
+
+    def retire(self, i):
+        """Stop stepping instance i (lbm_batch_retire)."""
+        self._check(self._L.lbm_batch_retire(self._h, int(i)))
+
+    def retire_nonfinite(self):
+        """Retire every active instance with a non-finite or non-positive density
+        (lbm_batch_retire_nonfinite); returns the indices retired."""
+        flags = (ctypes.c_int * len(self.instances))()
+        self._check(self._L.lbm_batch_retire_nonfinite(self._h, flags))
+        return [i for i in range(len(self.instances)) if flags[i]]
+
     def autotune(self, steps=20, cache=None):
         """As Lattice.autotune, for all active instances together."""
         t, v, r, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()

@@ -3,8 +3,9 @@ memory sanitizer): every global and shared-memory access of the step kernels is 
 against its buffer, and a failed check is reported as LBM_ECORRUPT.  The library is built
 in that variant and a child process (LBM_LIBRARY=check) runs both precisions and every
 kernel family over degenerate, odd, even and ragged widths, walls, graph replays and
-single launches, the moments and diagnostics passes, and a batch under per-instance
-widths: every check must pass."""
+single launches, the moments and diagnostics passes (including the allocation-free
+diagnostics, whose partial sums sit in the library's fixed array), and a batch under
+per-instance widths: every check must pass."""
 import os
 import subprocess
 import sys
@@ -18,6 +19,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 SCRIPT = textwrap.dedent('''
     import numpy as np
+    import torch
     from paper_1211_6932_gb300 import _lib, Batch, Eos, Instance, Lattice, maxwell
     from paper_1211_6932_gb300 import workloads as wl
     from paper_1211_6932_gb300.lattice import TILE_PER_INSTANCE
@@ -31,6 +33,7 @@ SCRIPT = textwrap.dedent('''
                         (256, 1, 0), (TILE_PER_INSTANCE, 2, 0)],
                "fp64": [(0, 0, 0), (64, 1, 2), (128, 1, 7)]}
     n = 0
+    out = torch.empty(6, dtype=torch.float64, device="cuda")
     for prec, tl in tilings.items():
         for nx, ny, walls in sizes:
             rho = wl.droplet(nx, ny, rl, rv, 0.3 * min(nx, ny), 4.0)
@@ -42,6 +45,7 @@ SCRIPT = textwrap.dedent('''
                     L.step(67)
                     L.moments()
                     L.diagnostics()
+                    L.diagnostics_noalloc(out)
                     L.step(2)
                     L.sync()
                     L.check_guards()
