@@ -297,23 +297,20 @@ def run_reference(args):
 
 
 def batch256_instances():
-    from paper_1211_6932_gb300 import Eos, Instance, maxwell, workloads as wl
-    insts, fields, nodes = [], [], 0
-    for d in wl.batch_draws(256, seed=4):
-        T = d["T_over_Tc"] * wl.t_crit(d["a"])
-        eos = Eos(a=d["a"], T=T)
-        rl, rv = maxwell(eos)
-        nu_l = 0.1
-        insts.append(Instance(nx=d["nx"], ny=d["ny"], eos=eos, sigma=d["sigma"],
-                              s=(1.0, 1.1, 1.1, 1.0, 1.1, 1.0, 1.1, 1.25, 1.25), nu_l=nu_l,
-                              nu_v=nu_l * d["visc_ratio"], visc_mode="linear", rho_l=rl,
-                              rho_v=rv))
-        if d["kind"] == "film":
-            fields.append(wl.flat_film(d["nx"], d["ny"], rl, rv, 4.0, d["ny"] / 2))
-        else:
-            fields.append(wl.droplet(d["nx"], d["ny"], rl, rv, min(d["nx"], d["ny"]) / 4, 4.0))
-        nodes += d["nx"] * d["ny"]
-    return insts, fields, nodes
+    """The batched-equilibria recipe with the instances that turn non-finite within 10^4
+    steps (a screen, untimed) left out: (instances, fields, total nodes, screen record)."""
+    from paper_1211_6932_gb300 import batched
+    insts, fields, draws = batched.instances(256, seed=4)
+    t0 = time.perf_counter()
+    bad = batched.screen(insts, fields, steps=10000)
+    keep = [i for i in range(len(insts)) if i not in bad]
+    rec = {"screen_steps": 10000, "retired_unstable": bad,
+           "retired_draws": [{k: draws[i][k] for k in ("nx", "ny", "a", "T_over_Tc", "sigma",
+                                                        "visc_ratio", "kind")} for i in bad],
+           "screen_s": time.perf_counter() - t0}
+    insts = [insts[i] for i in keep]
+    fields = [fields[i] for i in keep]
+    return insts, fields, sum(i.nx * i.ny for i in insts), rec
 
 
 def run_batch(args):
@@ -327,7 +324,7 @@ def run_batch(args):
     world, rank, local = dist_setup()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    insts, fields, n_total = batch256_instances()
+    insts, fields, n_total, screen = batch256_instances()
     # the instances are independent: each rank advances its own share, no collective on
     # the data path (total work fixed: strong scaling)
     own = shard([i.nx * i.ny for i in insts], world, rank)
@@ -374,6 +371,7 @@ def run_batch(args):
     torch.cuda.synchronize()
     barrier(world)
     clocks = sampler.stop()
+    nonfinite = sum(d["nonfinite"] for d in b.diagnostics())
     total_ms = max_over_ranks(t0.elapsed_time(t1), world)
     peak, peak_kind = load_peak()
     avg = step_ms / K
@@ -385,6 +383,8 @@ def run_batch(args):
                 "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "strong",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": "batch256_64to512_fp32", "instances": 256,
+                           "instances_timed": 256 - len(screen["retired_unstable"]),
+                           "screen": screen, "nonfinite_nodes_after": nonfinite,
                            "nodes": n_total, "nodes_rank0": n_nodes,
                            "tile_threads": "per_instance" if nt < 0 else nt,
                            "launches_per_step": per_step, "tile_vec": vec,
@@ -561,6 +561,20 @@ def run_gpu(args):
                 line["dynamics"] = dynamics_summary(stream)
             except Exception as exc:  # reported, never hidden
                 line["dynamics"] = {"error": repr(exc)}
+        if not args.no_other_workloads and world == 1 and NX == 4096:
+            try:
+                line["batch_equilibrium"] = batch_equilibrium_summary(stream)
+            except Exception as exc:  # reported, never hidden
+                line["batch_equilibrium"] = {"error": repr(exc)}
+            print("batch equilibrium: %s" % json.dumps(line["batch_equilibrium"]),
+                  file=sys.stderr, flush=True)
+        if not args.no_precision and world == 1 and NX == 4096:
+            try:
+                line["precision_error"] = precision_summary(stream)
+            except Exception as exc:  # reported, never hidden
+                line["precision_error"] = {"error": repr(exc)}
+            print("precision: %s" % json.dumps(line["precision_error"]), file=sys.stderr,
+                  flush=True)
         if not args.no_warm_start and world == 1 and NX == 4096:
             try:
                 line["warm_start"] = warm_start_ab(stream)
@@ -664,7 +678,7 @@ def other_workloads(stream):
               "FP64 populations and arithmetic (the 1e-12 parity mode)")
     # the 256-instance batch (autotuned tiling), one GPU
     from paper_1211_6932_gb300 import Batch
-    insts, fields, n_total = batch256_instances()
+    insts, fields, n_total, screen = batch256_instances()
     b = Batch(insts, precision="fp32", stream=stream)
     try:
         for i, rho in enumerate(fields):
@@ -684,7 +698,10 @@ def other_workloads(stream):
         out.append({"workload": "batch256_64to512_fp32", "nodes": n_total, "dtype": "f32",
                     "steps": 640, "ms_per_step": ms, "mlups": n_total / (ms * 1e-3) / 1e6,
                     "hbm_frac": 72 * n_total / (ms * 1e-3) / 1e9 / peak, "peak_source": kind,
-                    "note": "256 ragged instances, %.2f GB of state" % (72 * n_total / 1e9),
+                    "note": "%d of 256 ragged instances (the ones that stay finite over a "
+                            "10^4-step screen), %.2f GB of state"
+                            % (len(insts), 72 * n_total / 1e9),
+                    "retired_unstable": screen["retired_unstable"],
                     "tiling": ["per_instance" if nt < 0 else nt, vec, rows],
                     "launches_per_step": b.launches_per_step, "nonfinite_nodes": bad})
     finally:
@@ -768,6 +785,81 @@ def dynamics_summary(stream):
             "splash_C": {"re200": c200, "re1000": c1000, "printed": 1.3}}
 
 
+def batch_equilibrium_summary(stream):
+    """The batched-equilibria recipe run as specified: all 256 instances in one batch until
+    each meets max |d rho| < tol per 100 steps (FP32: 1e-6, the float reading of the
+    1e-9 tolerance; unstable instances are retired on the way), at most 60000 steps; and
+    the 24 smallest stable instances in the FP64 mode at the stated 1e-9 (at most 150000
+    steps), with their FP32 (1e-6) phase densities compared against the FP64 (1e-9)
+    ones."""
+    import numpy as np
+
+    from paper_1211_6932_gb300 import batched
+    insts, fields, draws = batched.instances(256, seed=4)
+    t0 = time.perf_counter()
+    e32 = batched.run_to_equilibrium(insts, fields, tol=1e-6, max_steps=60000, stream=stream)
+    t32 = time.perf_counter() - t0
+    st = e32.steps
+    conv = st[st >= 0]
+    films = [i for i in range(256) if draws[i]["kind"] == "film"]
+    out = {"fp32": {"tol": 1e-6, "max_steps": 60000, "seconds": t32,
+                    "converged": int(len(conv)), "unstable": e32.unstable,
+                    "unconverged": len(e32.unconverged),
+                    "unconverged_films": len([i for i in e32.unconverged if i in films]),
+                    "steps_median": float(np.median(conv)) if len(conv) else None,
+                    "steps_p90": float(np.percentile(conv, 90)) if len(conv) else None,
+                    "steps_max": int(conv.max()) if len(conv) else None,
+                    "node_steps": e32.node_steps,
+                    "mlups_run": e32.node_steps / t32 / 1e6}}
+    stable = [i for i in range(256) if i not in e32.unstable]
+    sub = sorted(stable, key=lambda i: insts[i].nx * insts[i].ny)[:24]
+    si, sf = [insts[i] for i in sub], [fields[i] for i in sub]
+    t0 = time.perf_counter()
+    e64 = batched.run_to_equilibrium(si, sf, tol=1e-9, max_steps=150000, precision="fp64",
+                                     stream=stream, keep_fields=True)
+    t64 = time.perf_counter() - t0
+    e32s = batched.run_to_equilibrium(si, sf, tol=1e-6, max_steps=150000, stream=stream,
+                                      keep_fields=True)
+    dl, dv = [], []
+    for k, i in enumerate(sub):
+        if e64.rho[k] is None or e32s.rho[k] is None:
+            continue
+        rl, rv = insts[i].rho_l, insts[i].rho_v
+        l64, v64 = batched.phase_densities(e64.rho[k], rl, rv)
+        l32, v32 = batched.phase_densities(e32s.rho[k], rl, rv)
+        dl.append(abs(l32 / l64 - 1))
+        dv.append(abs(v32 / v64 - 1))
+    out["fp64_subset"] = {"instances": sub, "tol": 1e-9, "seconds": t64,
+                          "converged": int((e64.steps >= 0).sum()),
+                          "steps": e64.steps.tolist(),
+                          "fp32_1e-6_steps": e32s.steps.tolist(),
+                          "max_rel_diff_liquid_fp32_vs_fp64": max(dl) if dl else None,
+                          "max_rel_diff_vapour_fp32_vs_fp64": max(dv) if dv else None}
+    return out
+
+
+def precision_summary(stream):
+    """Error of the FP32 path against the FP64 mode (oracle-matched per step) after the
+    stated step counts: the 1024^2 ellipse (20000 steps), the 2048 x 512 splash (30000
+    steps, density ratio > 500; step viscosity as in Sec. IV C, and tau linear in rho) and
+    the 4096^2 field (2000 steps); per workload the
+    maximum relative density error, the coexistence (bulk liquid / vapour mean) errors and
+    the sensitivity floor of the flow (FP64 from the float-rounded start against FP64),
+    at evenly spaced checkpoints."""
+    from paper_1211_6932_gb300 import precision as pr
+    t0 = time.perf_counter()
+    out = {"bounds": {"max_rel_density": 1e-4, "coexistence": 1e-3}, "workloads": []}
+    for name, steps, cps in (("ellipse_1024", 20000, 4), ("splash_2048", 30000, 6),
+                             ("splash_2048_linear", 30000, 6), ("field_4096", 2000, 2)):
+        r = pr.fp32_error(name, steps=steps, checkpoints=cps, floor=True, stream=stream)
+        keep = ("step", "max_rel_density", "liquid_rel", "vapour_rel", "mass_rel",
+                "fp64_floor")
+        r["history"] = [{k: h.get(k) for k in keep} for h in r["history"]]
+        out["workloads"].append(r)
+    out["seconds"] = time.perf_counter() - t0
+    return out
+
+
 def warm_start_ab(stream):
     """Learned warm start against Eq. 31 on the 4096^2 field: the training set from the
     batched equilibria (256 draws, one film and two droplets each), the network trained on
@@ -775,6 +867,8 @@ def warm_start_ab(stream):
     densities recorded every 100 steps.  Steps-to-equilibrium: the first check after
     which the vapour and liquid phase densities stay within the tolerances of the plain
     run's final values (mean over its last 20 % of checks)."""
+    import numpy as np
+
     from paper_1211_6932_gb300 import Lattice, workloads as wl
     from paper_1211_6932_gb300 import warmstart as ws
     t0 = time.perf_counter()
@@ -813,11 +907,23 @@ def warm_start_ab(stream):
         a, b = row["plain"], row["warm"]
         row["saved"] = (a - b) if a is not None and b is not None else None
         settle.append(row)
+    # size of the start-up ringing of each arm: the largest relative departure of the
+    # liquid and vapour phase densities from the plain run's final values over early
+    # (steps 500-5000) and late (10000-30000) windows
+    def ringing(r, lo, hi):
+        m = (r.steps >= lo) & (r.steps <= hi)
+        return {"liquid": float(np.max(np.abs(r.liq[m] / ref_l - 1.0))),
+                "vapour": float(np.max(np.abs(r.vap[m] / ref_v - 1.0)))}
+    ring = {name: {"early": ringing(r, 500, 5000), "late": ringing(r, 10000, 30000),
+                   "start_vapour": float(r.vap[0] / ref_v - 1.0),
+                   "start_liquid": float(r.liq[0] / ref_l - 1.0)}
+            for name, r in rel.items()}
     return {
         "metric": "warm-start steps saved (4096^2, 64 droplets, phase densities within "
                   "1 % vapour / 0.2 % liquid)",
         "value": settle[0]["saved"], "unit": "steps",
         "settling": settle,
+        "ringing": ring,
         "start_error": {"plain_vapour": rp.vap[0] / ref_v - 1, "warm_vapour": rw.vap[0] / ref_v - 1},
         "final": {"plain_vapour": ref_v, "plain_liquid": ref_l,
                   "warm_vapour": ws.tail_mean(rw.vap), "warm_liquid": ws.tail_mean(rw.liq),
@@ -846,6 +952,8 @@ def main():
     ap.add_argument("--no-other-workloads", action="store_true",
                     help="skip the MLUPS of the other workloads (droplet, ellipse, splash, "
                          "batch) and of the FP64 mode")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the FP32-against-FP64 error over the stated runs (1 GPU only)")
     ap.add_argument("--no-warm-start", action="store_true",
                     help="skip the learned warm-start comparison (4096^2, 1 GPU only)")
     ap.add_argument("--workload", default="field4096", choices=["field4096", "batch256"],
