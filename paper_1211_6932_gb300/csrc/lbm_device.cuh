@@ -804,14 +804,34 @@ __global__ void __launch_bounds__(NT, MinBlocks<S, NT>::value) sweep_kernel(
 // columns -1 and WO (their other column is unused); thread 0 issues the bulk copies.
 // Owners write their post-collision pair straight from registers (one 8-byte store per
 // population).
-template <int NT, int NS_ = 4>
+//
+// Shared-memory ring by plane group.  A node of row y pulls the planes with e_y = -dir
+// (three of them) from the row ahead in the sweep, the e_y = 0 planes from its own row and
+// the e_y = +dir planes from the row behind, so each plane of a loaded row is read exactly
+// once, one, two or three sweep steps after the row is needed first.  The three groups
+// therefore live in rings of 3, 4 and 5 rows ("ahead", "centre", "behind"): 36 plane
+// rows, as many as a ring of 4 whole rows, but with two rows in flight instead of one.
+// Row j (in sweep order) is issued after the row barrier of step j - 3 and waited for at
+// step j - 1; the ahead planes of row j are read at steps j - 1 (pull of row j - 1) and j
+// (bounce-back at a wall row j), the centre planes at step j, the behind planes at steps
+// j (bounce-back) and j + 1, so each slot is free again when the next row issued into it
+// is issued (ring depth 3, 4, 5 and issue lead 3).  The ahead planes of row 0 are never
+// read and not copied (their slot is row 3's).
+__host__ __device__ constexpr int kidx_of(int q) {  // index of plane q inside its group
+  return q == 0 || q == 2 || q == 4 ? 0 : (q == 1 || q == 5 || q == 7 ? 1 : 2);
+}
+
+template <int NT>
 struct Sweep2Cfg {
   static constexpr int WO = 2 * NT - 4;      // owned columns per CTA (a multiple of 4)
   static constexpr int SEG = WO + 8;         // ring row: columns x0-4 .. x0+WO+3
-  static constexpr int NSLOT = NS_;          // ring rows (NSLOT - 3 rows in flight)
+  static constexpr int DA = 3, DC = 4, DB = 5;  // ring depths: ahead, centre, behind
+  static constexpr int NBAR = 5;             // row barriers (rows issued and not retired)
+  static constexpr int LEAD = 3;             // row j is issued at step j - LEAD
+  static constexpr int PLANE_ROWS = 3 * (DA + DC + DB);
   static constexpr int PSW = 2 * NT;         // psi ring row: CTA columns -2 .. WO+1
   static constexpr size_t BARS = 128;
-  static constexpr size_t POP = (size_t)NSLOT * Q * SEG * sizeof(float);
+  static constexpr size_t POP = (size_t)PLANE_ROWS * SEG * sizeof(float);
   static constexpr size_t PSI = (size_t)PSI_ROWS * PSW * sizeof(float);
   static constexpr size_t BYTES = BARS + POP + PSI;
 };
@@ -823,17 +843,21 @@ constexpr int sweep2_min_blocks(int nt) {
   return nt == 64 ? 10 : nt == 96 ? 6 : nt == 128 ? 5 : 65536 / (nt * 128);
 }
 
-template <int NT, int MODE, int NS_ = 4>
+template <int NT, int MODE>
 __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
     const float* __restrict__ fin, float* __restrict__ fout, const InstParams* __restrict__ insts,
     const WorkItem* __restrict__ items, int n_items, MomArgs<float> mo,
     int* __restrict__ status) {
-  typedef Sweep2Cfg<NT, NS_> C;
+  typedef Sweep2Cfg<NT> C;
   typedef Num<float2> N;
-  constexpr int WO = C::WO, SEG = C::SEG, NS = C::NSLOT, PSW = C::PSW;
+  constexpr int WO = C::WO, SEG = C::SEG, PSW = C::PSW, NB = C::NBAR;
+  constexpr int DA = C::DA, DC = C::DC, DB = C::DB, RING = C::PLANE_ROWS * SEG;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
   float* ring = reinterpret_cast<float*>(smem_raw + C::BARS);
+  float* ringA = ring;                    // ahead planes, DA rows of 3 planes
+  float* ringC = ring + 3 * DA * SEG;     // centre planes, DC rows
+  float* ringB = ring + 3 * (DA + DC) * SEG;  // behind planes, DB rows
   float* psis = reinterpret_cast<float*>(smem_raw + C::BARS + C::POP);
   __shared__ int s_abort;
   __shared__ double red_d[NT / 32][3];
@@ -874,34 +898,43 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
   const bool psi_ok = LBM_IN(2 + c0 >= 0 && 2 + c0 + 2 <= PSW);
   const bool psi_nb_ok = !owner || LBM_IN(1 + c0 >= 0 && 2 + c0 + 3 <= PSW);
 
-  auto issue_row = [&](int j, int slot) {
+  // Row j of the sweep: the planes of each group into that group's ring (see Sweep2Cfg),
+  // completion on row barrier j % NB.
+  auto issue_row = [&](int j) {
     const int r = rstart + j * dir;
     const int rp = walls ? (r < 0 ? 0 : (r >= ny ? ny - 1 : r)) : wrapi(r, ny);
     const float* src = gsrc + (long long)rp * pitch;
-    // source row inside the instance's planes, destination inside the ring
-    if (!LBM_IN(slot >= 0 && slot < NS)) return;
     const bool ok = LBM_IN(rp >= 0 && rp < ny && seg0 >= 0 && len > 0 && len <= SEG &&
                            seg0 + len <= pitch);
-    mbar_arrive_expect_tx(&bars[slot], ok ? plane_bytes * Q : 0u);
+    const bool ahead = j >= 1;  // the ahead planes of row 0 are never read
+    uint64_t* bar = &bars[j % NB];
+    mbar_arrive_expect_tx(bar, ok ? plane_bytes * (ahead ? 9u : 6u) : 0u);
     if (!ok) return;
+    float* dA = ringA + (j % DA) * 3 * SEG;
+    float* dC = ringC + (j % DC) * 3 * SEG;
+    float* dB = ringB + (j % DB) * 3 * SEG;
 #pragma unroll
-    for (int q = 0; q < Q; ++q)
-      bulk_g2s(ring + ((size_t)slot * Q + q) * SEG, src + (long long)q * plane, plane_bytes,
-               &bars[slot]);
+    for (int q = 0; q < Q; ++q) {
+      const int g = ey_of(q);
+      float* dst = g == 0 ? dC : ((g < 0) == (dir > 0) ? dA : dB);
+      if (dst == dA && !ahead) continue;
+      if (!LBM_IN(dst + kidx_of(q) * SEG >= ring && dst + (kidx_of(q) + 1) * SEG <= ring + RING))
+        continue;
+      bulk_g2s(dst + kidx_of(q) * SEG, src + (long long)q * plane, plane_bytes, bar);
+    }
   };
 
-  int issued = 0, islot = 0;  // rows issued and the slot of the next one (issuer only)
+  int issued = 0;  // rows issued (issuer only)
   if (issuer) {
     s_abort = 0;
-    for (int k = 0; k < NS; ++k) mbar_init(&bars[k], 1);
+    for (int k = 0; k < NB; ++k) mbar_init(&bars[k], 1);
     mbar_fence_init();
   }
   __syncthreads();
   if (issuer) {
-    const int n0 = min(nload, NS);
-    for (int j = 0; j < n0; ++j) issue_row(j, j);
+    const int n0 = min(nload, C::LEAD + 1);
+    for (int j = 0; j < n0; ++j) issue_row(j);
     issued = n0;
-    islot = n0 == NS ? 0 : n0;
   }
 
   float2 cur[Q], nxt[Q];
@@ -910,30 +943,23 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
   CompSum<float> acc_m, acc_x, acc_y;  // per-thread compensated sums (diagnostics)
   float mx_u = 0.f, mx_d = 0.f;        // max |v|^2, max |rho - rho_prev|
   int bad = 0;
-  // Ring bookkeeping without division: slot of row s, and the slot/phase of the next row
-  // to wait for (rows are waited for in order, one per iteration after the first).
+  // Ring bookkeeping without division: the row barrier and phase of the next row to wait
+  // for (rows are waited for in order, one per iteration after the first), and the ring
+  // slots of the rows an iteration reads.
   int waited = 0, wslot = 0;
   uint32_t wphase = 0;
-  int slot_s = 1;  // s % NS for s = 1
+  int sa = 2 % DA, sc = 1 % DC, sb = 0;  // slots: ahead of row s+1, centre of row s, behind of row s-1
   const int last = nload - 2;
   int s = 1;
   for (; s <= last; ++s) {
-    if (issuer && s >= 2 && issued < nload) {
-      fence_proxy_async_smem();  // our reads of the freed slot precede the new copy
-      issue_row(issued, islot);
-      ++issued;
-      islot = islot + 1 == NS ? 0 : islot + 1;
-    }
     while (waited <= s + 1) {
       if (!mbar_wait_bounded(&bars[wslot], wphase)) s_abort = 1;
       ++waited;
-      if (++wslot == NS) {
+      if (++wslot == NB) {
         wslot = 0;
         wphase ^= 1u;
       }
     }
-    const int slot_p = slot_s == 0 ? NS - 1 : slot_s - 1;  // row s - 1
-    const int slot_n = slot_s + 1 == NS ? 0 : slot_s + 1;  // row s + 1
     const int rpsi = rstart + s * dir;
     const bool ghost = walls && (rpsi < 0 || rpsi >= ny);
     float* ps_now = psis + (s & (PSI_ROWS - 1)) * PSW;
@@ -941,34 +967,47 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
     if (!ghost) {
       const bool bb_low = walls && rpsi == 0;
       const bool bb_high = walls && rpsi == ny - 1;
-      const float* rowC = ring + slot_s * (Q * SEG) + SEG_HALO + c0;
-      const float* rowS = ring + (dir > 0 ? slot_p : slot_n) * (Q * SEG) + SEG_HALO + c0;
-      const float* rowN = ring + (dir > 0 ? slot_n : slot_p) * (Q * SEG) + SEG_HALO + c0;
+      // group bases of this pull: e_y = -1 planes (from y + 1), e_y = 0 (row y), e_y = +1
+      // (from y - 1); ahead is y + dir
+      const float* pA = ringA + sa * 3 * SEG + SEG_HALO + c0;  // row s+1
+      const float* pC = ringC + sc * 3 * SEG + SEG_HALO + c0;  // row s
+      const float* pB = ringB + sb * 3 * SEG + SEG_HALO + c0;  // row s-1
+      const float* gm = dir > 0 ? pA : pB;
+      const float* gp = dir > 0 ? pB : pA;
       auto pair_at = [&](const float* p) -> float2 {  // columns c0, c0+1 (8-byte aligned)
         return *reinterpret_cast<const float2*>(p);
+      };
+      auto in_ring = [&](const float* p) {  // bounds-check build
+        return LBM_IN(p >= ring && p + 2 <= ring + RING);
       };
       if (!(bb_low || bb_high)) {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
           const int eyq = ey_of(q), exq = ex_of(q);
-          const float* src = (eyq > 0 ? rowS : (eyq < 0 ? rowN : rowC)) + q * SEG - exq;
-          if (!LBM_IN(src >= ring && src + 2 <= ring + NS * Q * SEG))
+          const float* src = (eyq < 0 ? gm : (eyq > 0 ? gp : pC)) + kidx_of(q) * SEG - exq;
+          if (!in_ring(src))
             nxt[q] = N::k(0.f);
           else
             nxt[q] = exq == 0 ? pair_at(src) : make_float2(src[0], src[1]);
         }
       } else {
+        // Halfway bounce-back: a plane that would come from beyond the wall is the
+        // opposite plane of this row; those are in the ahead or behind ring of row s.
+        const float* sA = ringA + (s % DA) * 3 * SEG + SEG_HALO + c0;
+        const float* sB = ringB + (s % DB) * 3 * SEG + SEG_HALO + c0;
+        const float* cm = dir > 0 ? sA : sB;  // e_y = -1 planes of row s
+        const float* cp = dir > 0 ? sB : sA;  // e_y = +1 planes of row s
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
           const int eyq = ey_of(q), exq = ex_of(q);
           const bool bb = (eyq > 0 && bb_low) || (eyq < 0 && bb_high);
           if (bb) {
-            const float* src = rowC + opp_of(q) * SEG;
-            nxt[q] = LBM_IN(src >= ring && src + 2 <= ring + NS * Q * SEG) ? pair_at(src)
-                                                                          : N::k(0.f);
+            const int o = opp_of(q);
+            const float* src = (ey_of(o) < 0 ? cm : cp) + kidx_of(o) * SEG;
+            nxt[q] = in_ring(src) ? pair_at(src) : N::k(0.f);
           } else {
-            const float* src = (eyq > 0 ? rowS : (eyq < 0 ? rowN : rowC)) + q * SEG - exq;
-            if (!LBM_IN(src >= ring && src + 2 <= ring + NS * Q * SEG))
+            const float* src = (eyq < 0 ? gm : (eyq > 0 ? gp : pC)) + kidx_of(q) * SEG - exq;
+            if (!in_ring(src))
               nxt[q] = N::k(0.f);
             else
               nxt[q] = exq == 0 ? pair_at(src) : make_float2(src[0], src[1]);
@@ -992,6 +1031,12 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
     }
     __syncthreads();
     if (s_abort) break;
+    if (issuer && s + C::LEAD < nload) {
+      // the slots of row s + LEAD were last read before this row barrier
+      fence_proxy_async_smem();  // our reads of the freed slots precede the new copies
+      issue_row(s + C::LEAD);
+      issued = s + C::LEAD + 1;
+    }
 
     if (s >= 3 && owner && psi_nb_ok) {
       const int yc = rstart + (s - 1) * dir;
@@ -1102,16 +1147,18 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
     for (int q = 0; q < Q; ++q) cur[q] = nxt[q];
     cur_rho = nrho;
     cur_dr = ndr;
-    slot_s = slot_n;
+    sa = sa + 1 == DA ? 0 : sa + 1;
+    sc = sc + 1 == DC ? 0 : sc + 1;
+    sb = sb + 1 == DB ? 0 : sb + 1;
   }
 
   if (s <= last) {
     if (issuer) {
       // The newest row issued into each slot: once its phase completed, every earlier
       // copy into that slot has too.
-      for (int k = 0; k < NS && k < issued; ++k) {
-        const int j = issued - 1 - ((issued - 1 - k) % NS);
-        mbar_wait_bounded(&bars[k], (uint32_t)((j / NS) & 1));
+      for (int k = 0; k < NB && k < issued; ++k) {
+        const int j = issued - 1 - ((issued - 1 - k) % NB);
+        mbar_wait_bounded(&bars[k], (uint32_t)((j / NB) & 1));
       }
       atomicOr(status, STATUS_TIMEOUT);
     }
