@@ -72,15 +72,18 @@ struct Batch {
   cudaStream_t cap_stream = nullptr;
   int nt = 0, vec = 0, rows_req = 0, rows = 0;  // threads and columns/thread per CTA, rows per sweep
   // Step launches: group g runs items [grp_begin[g], grp_begin[g+1]) with grp_nt[g]
-  // threads.  One group, unless nt == LBM_TILE_PER_INSTANCE: then one per pair-kernel
-  // width, each instance in the group of the width inst_nt[i].
-  static constexpr int kMaxGroups = 4;
+  // threads, in full-width strips if grp_full[g] (pair kernel).  One group per kernel
+  // width (one width, unless nt == LBM_TILE_PER_INSTANCE: then each instance has the width
+  // inst_nt[i]), split into strip and full-width instances.
+  static constexpr int kMaxWidths = 4;
+  static constexpr int kMaxGroups = 2 * kMaxWidths;
   std::vector<int> inst_nt;
   int n_groups = 0;
-  int grp_nt[kMaxGroups] = {0, 0, 0, 0};
-  int grp_begin[kMaxGroups + 1] = {0, 0, 0, 0, 0};
-  cudaStream_t grp_stream[kMaxGroups - 1] = {nullptr, nullptr, nullptr};  // graph branches
-  cudaEvent_t grp_fork = nullptr, grp_join[kMaxGroups - 1] = {nullptr, nullptr, nullptr};
+  int grp_nt[kMaxGroups] = {};
+  int grp_full[kMaxGroups] = {};
+  int grp_begin[kMaxGroups + 1] = {};
+  cudaStream_t grp_stream[kMaxGroups - 1] = {};  // graph branches
+  cudaEvent_t grp_fork = nullptr, grp_join[kMaxGroups - 1] = {};
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   // Buffers allocated with guard bands (lbm_check_guards): base pointer, user bytes, name.
   struct Guarded {
@@ -300,7 +303,7 @@ bool tiling_ok(bool fp64, int nt, int vec) {
 // Threads per CTA of the moments/diagnostics pass (one uniform tiling over all instances).
 int mom_nt(const Batch* b) { return per_instance(b) ? 128 : b->nt; }
 
-constexpr int kPairThreads[Batch::kMaxGroups] = {32, 64, 96, 128};
+constexpr int kPairThreads[Batch::kMaxWidths] = {32, 64, 96, 128};
 
 // Pair-kernel width for an instance of nx columns: the least strip time, where a strip row
 // of 2 nt - 4 owned columns costs its 2 nt computed columns plus a fixed 57
@@ -311,10 +314,9 @@ constexpr int kPairThreads[Batch::kMaxGroups] = {32, 64, 96, 128};
 int pair_threads_for(int nx) {
   int best = 128;
   long long best_cost = -1;
-  for (int g = Batch::kMaxGroups - 1; g >= 0; --g) {
+  for (int g = Batch::kMaxWidths - 1; g >= 0; --g) {
     const int nt = kPairThreads[g];
-    const int W = lbm::strip_width(nt, 2);
-    const long long cost = (long long)((nx + W - 1) / W) * (2 * nt + 57);
+    const long long cost = (long long)lbm::strips_for(nx, nt, 2) * (2 * nt + 57);
     if (best_cost < 0 || cost < best_cost) {
       best_cost = cost;
       best = nt;
@@ -337,10 +339,10 @@ int default_rows(const Batch* b) {
   for (int i = 0; i < b->n_inst; ++i)
     if (b->active[i]) {
       const int nt = step_nt(b, i);
-      const int W = lbm::strip_width(nt, b->vec);
       const int occ = b->fp64 ? lbm::sweep_occupancy<double>(nt, b->vec)
                               : lbm::sweep_occupancy<float>(nt, b->vec);
-      sm_rows += (double)((b->inst[i].nx + W - 1) / W) * b->inst[i].ny / std::max(occ, 1);
+      sm_rows += (double)lbm::strips_for(b->inst[i].nx, nt, b->vec) * b->inst[i].ny /
+                 std::max(occ, 1);
     }
   const double target = (double)std::max(b->sms, 1) * 6.0;
   const long long r = (long long)std::ceil(sm_rows / target);
@@ -348,8 +350,10 @@ int default_rows(const Batch* b) {
 }
 
 // Work items of instance i: strips of W owned columns by chunks of `rows` rows.
-void append_items(const InstParams& P, int i, int W, int rows, std::vector<WorkItem>& out) {
-  const int strips = (P.nx + W - 1) / W;
+void append_items(const InstParams& P, int i, int nt, int vec, int rows,
+                  std::vector<WorkItem>& out) {
+  const int W = lbm::strip_width(nt, vec);
+  const int strips = lbm::strips_for(P.nx, nt, vec);
   const int chunks = (P.ny + rows - 1) / rows;
   for (int c = 0; c < chunks; ++c)
     for (int s = 0; s < strips; ++s) {
@@ -363,20 +367,25 @@ void append_items(const InstParams& P, int i, int W, int rows, std::vector<WorkI
     }
 }
 
-// Step items of the active instances, grouped by kernel width (b->items, b->grp_*).
+// Step items of the active instances, grouped by kernel width and, within a width, by
+// strip and full-width instances (b->items, b->grp_*).
 void make_step_items(Batch* b) {
   b->items.clear();
   b->n_groups = 0;
   b->grp_begin[0] = 0;
-  for (int g = 0; g < Batch::kMaxGroups; ++g) {
+  for (int g = 0; g < Batch::kMaxWidths; ++g) {
     const int nt = per_instance(b) ? kPairThreads[g] : b->nt;
-    const size_t before = b->items.size();
-    for (int i = 0; i < b->n_inst; ++i)
-      if (b->active[i] && step_nt(b, i) == nt)
-        append_items(b->inst[i], i, lbm::strip_width(nt, b->vec), b->rows, b->items);
-    if (b->items.size() > before) {
-      b->grp_nt[b->n_groups] = nt;
-      b->grp_begin[++b->n_groups] = (int)b->items.size();
+    for (int full = 0; full < 2; ++full) {
+      const size_t before = b->items.size();
+      for (int i = 0; i < b->n_inst; ++i)
+        if (b->active[i] && step_nt(b, i) == nt &&
+            (int)lbm::full_width(b->inst[i].nx, nt, b->vec) == full)
+          append_items(b->inst[i], i, nt, b->vec, b->rows, b->items);
+      if (b->items.size() > before) {
+        b->grp_nt[b->n_groups] = nt;
+        b->grp_full[b->n_groups] = full;
+        b->grp_begin[++b->n_groups] = (int)b->items.size();
+      }
     }
     if (!per_instance(b)) break;
   }
@@ -384,11 +393,10 @@ void make_step_items(Batch* b) {
 
 // Items of every instance for the moments/diagnostics pass, with per-instance ranges.
 void make_all_items(const Batch* b, std::vector<WorkItem>& out, std::vector<int>& begin) {
-  const int W = lbm::strip_width(mom_nt(b), b->vec);
   out.clear();
   begin.assign(1, 0);
   for (int i = 0; i < b->n_inst; ++i) {
-    append_items(b->inst[i], i, W, b->rows, out);
+    append_items(b->inst[i], i, mom_nt(b), b->vec, b->rows, out);
     begin.push_back((int)out.size());
   }
 }
@@ -434,6 +442,12 @@ int rebuild_items(Batch* b) {
   if (!b->d_item_begin) CK(b, dev_malloc(&b->d_item_begin, sizeof(int) * (b->n_inst + 1)));
   CK(b, cudaMemcpy(b->d_item_begin, b->item_begin.data(), sizeof(int) * (b->n_inst + 1),
                    cudaMemcpyHostToDevice));
+  // Full-width strips of the pair kernel neither read nor write the ghost columns, so
+  // after steps under one set of work lists they may be stale; a pass under the new lists
+  // may use strips that read them.
+  if (!b->fp64 && b->slab[b->cur])
+    for (int i = 0; i < b->n_inst; ++i)
+      CK(b, lbm::launch_fill_ghosts<float>((float*)b->slab[b->cur], b->inst[i], b->stream));
   return LBM_OK;
 }
 
@@ -573,12 +587,12 @@ int launch_group(Batch* b, int g, int c, cudaStream_t st) {
   cudaError_t e;
   if (b->fp64) {
     MomArgs<double> mo{};
-    e = lbm::launch_sweep<double>(b->grp_nt[g], b->vec, lbm::MODE_STEP,
+    e = lbm::launch_sweep<double>(b->grp_nt[g], b->vec, lbm::MODE_STEP, 0,
                                   (const double*)b->slab[c], (double*)b->slab[c ^ 1], b->d_inst,
                                   items, n, mo, b->d_status, st);
   } else {
     MomArgs<float> mo{};
-    e = lbm::launch_sweep<float>(b->grp_nt[g], b->vec, lbm::MODE_STEP,
+    e = lbm::launch_sweep<float>(b->grp_nt[g], b->vec, lbm::MODE_STEP, b->grp_full[g],
                                  (const float*)b->slab[c], (float*)b->slab[c ^ 1], b->d_inst,
                                  items, n, mo, b->d_status, st);
   }
@@ -871,15 +885,28 @@ int get_pops(Batch* b, int i, double* f) {
   return LBM_OK;
 }
 
+// Launch the moments/diagnostics kernel over a device list of n items on the batch's
+// stream.  The pair kernel has strip and full-width instantiations: both are launched over
+// the whole list, and each CTA works only on an item of its own kind.
+template <typename S>
+cudaError_t launch_moments(const Batch* b, const WorkItem* d_items, int n,
+                           const MomArgs<S>& mo) {
+  const int kinds = (!b->fp64 && b->vec == 2) ? 2 : 1;
+  cudaError_t e = cudaSuccess;
+  for (int full = 0; full < kinds && e == cudaSuccess; ++full)
+    e = lbm::launch_sweep<S>(mom_nt(b), b->vec, lbm::MODE_MOMENTS, full,
+                             (const S*)b->slab[b->cur], nullptr, b->d_inst, d_items, n, mo,
+                             b->d_status, b->stream);
+  return e;
+}
+
 // Moments/diagnostics pass over `items` (device list of n entries).
 template <typename S>
 int moments_pass(Batch* b, const WorkItem* d_items, int n, MomArgs<S> mo) {
   mo.part_sum = b->d_part_sum;
   mo.part_max = b->d_part_max;
   mo.part_bad = b->d_part_bad;
-  cudaError_t e = lbm::launch_sweep<S>(mom_nt(b), b->vec, lbm::MODE_MOMENTS, (const S*)b->slab[b->cur],
-                                       nullptr, b->d_inst, d_items, n, mo, b->d_status,
-                                       b->stream);
+  cudaError_t e = launch_moments<S>(b, d_items, n, mo);
   if (e != cudaSuccess)
     return set_err(b->err, LBM_ECUDA, "moments kernel launch failed: %s", cudaGetErrorString(e));
   return LBM_OK;
@@ -1301,9 +1328,7 @@ int noalloc_diag_pass(Batch* b, double* part_sum, float* part_max, int* part_bad
   mo.part_max = part_max;
   mo.part_bad = part_bad;
   mo.flags = lbm::MOM_DIAG;  // no fields, no reference density
-  cudaError_t e = lbm::launch_sweep<S>(mom_nt(b), b->vec, lbm::MODE_MOMENTS,
-                                       (const S*)b->slab[b->cur], nullptr, b->d_inst,
-                                       b->d_all_items, b->n_all, mo, b->d_status, b->stream);
+  cudaError_t e = launch_moments<S>(b, b->d_all_items, b->n_all, mo);
   if (e != cudaSuccess)
     return set_err(b->err, LBM_ECUDA, "diagnostics pass launch failed: %s",
                    cudaGetErrorString(e));

@@ -829,28 +829,33 @@ struct Sweep2Cfg {
   static constexpr int NBAR = 5;             // row barriers (rows issued and not retired)
   static constexpr int LEAD = 3;             // row j is issued at step j - LEAD
   static constexpr int PLANE_ROWS = 3 * (DA + DC + DB);
-  static constexpr int PSW = 2 * NT;         // psi ring row: CTA columns -2 .. WO+1
+  static constexpr int PSW = 2 * NT + 4;     // psi ring row: CTA columns -2 .. 2 NT + 1
+  static constexpr int PSW_STRIP = 2 * NT;   // rows of the strip instantiation: -2 .. WO+1
   static constexpr size_t BARS = 128;
   static constexpr size_t POP = (size_t)PLANE_ROWS * SEG * sizeof(float);
   static constexpr size_t PSI = (size_t)PSI_ROWS * PSW * sizeof(float);
   static constexpr size_t BYTES = BARS + POP + PSI;
 };
 
-// Resident CTAs per SM the pair kernel is compiled for (the register cap follows): with
-// direct stores shared memory allows 10 / 7 / 5 CTAs of 64 / 96 / 128 threads, and these
-// targets are the largest that compile without spills (92-96 registers).
+// Resident CTAs per SM the pair kernel is compiled for (the register cap follows): shared
+// memory allows 19 / 10 / 7 / 5 CTAs of 32 / 64 / 96 / 128 threads, and these targets are
+// the largest that compile without spills (94-96 registers).
 constexpr int sweep2_min_blocks(int nt) {
-  return nt == 64 ? 10 : nt == 96 ? 6 : nt == 128 ? 5 : 65536 / (nt * 128);
+  return nt == 32 ? 20 : nt == 64 ? 10 : nt == 96 ? 6 : nt == 128 ? 5 : 65536 / (nt * 128);
 }
 
-template <int NT, int MODE>
+// FULL selects the full-width strip at compile time (its own instantiation, so that the
+// strip-mode code keeps constant load offsets); a CTA whose instance does not match the
+// instantiation returns at once (the moments pass launches both over one item list).
+template <int NT, int MODE, bool FULL>
 __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
     const float* __restrict__ fin, float* __restrict__ fout, const InstParams* __restrict__ insts,
     const WorkItem* __restrict__ items, int n_items, MomArgs<float> mo,
     int* __restrict__ status) {
   typedef Sweep2Cfg<NT> C;
   typedef Num<float2> N;
-  constexpr int WO = C::WO, SEG = C::SEG, PSW = C::PSW, NB = C::NBAR;
+  constexpr int WO = C::WO, SEG = C::SEG, NB = C::NBAR;
+  constexpr int PSW = FULL ? C::PSW : C::PSW_STRIP;
   constexpr int DA = C::DA, DC = C::DC, DB = C::DB, RING = C::PLANE_ROWS * SEG;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
@@ -867,6 +872,8 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
   if ((int)blockIdx.x >= n_items) return;
   const WorkItem it = items[blockIdx.x];
   const InstParams& P = insts[it.inst];
+  // the step launches hold items of one kind only (the host groups them, strips_for)
+  if (MODE == MODE_MOMENTS && (P.nx <= 2 * NT) != FULL) return;
   const Phys<float> ph = load_phys<float>(P);
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -874,29 +881,47 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
   const int nx = P.nx, ny = P.ny, pitch = P.pitch, walls = P.walls;
   const long long plane = P.plane;
   const int x0 = it.x0;
-  const int c0 = 2 * tid - 2;             // first CTA column of this thread
+  // Full-width strip (nx <= 2 NT, one strip per row, x0 = 0): thread t owns columns 2t,
+  // 2t + 1, the row is loaded from its first column, the periodic neighbours of the two
+  // edge columns are read across the row in shared memory, and the ghost columns are
+  // neither read nor written.  Otherwise threads 1 .. NT-2 own WO columns from x0 and
+  // threads 0 and NT-1 evaluate psi of the halo columns.
+  constexpr bool full = FULL;
+  const int c0 = full ? 2 * tid : 2 * tid - 2;  // first CTA column of this thread
   const int xa = x0 + c0;                 // its global column (xa, xa + 1)
-  const int xend = min(x0 + WO, nx);
-  const bool owner = tid >= 1 && tid <= NT - 2 && xa < xend;
-  // Ghost columns (periodic copies at -2, -1, nx, nx+1).  For even nx >= 4 the owners of
-  // the pairs (0, 1) and (nx-2, nx-1) mirror them as pairs to (nx, nx+1) and (-2, -1);
-  // every other case (odd nx, nx < 4) takes the general per-column path.
+  const int xend = full ? nx : min(x0 + WO, nx);
+  const bool owner = full ? xa < nx : (tid >= 1 && tid <= NT - 2 && xa < xend);
+  // Columns the pull and the force read besides c0 (the pair's left neighbour, its second
+  // column and right neighbour), wrapped across the row in a full-width strip: only the
+  // first thread (left) and the last one or two (right) wrap.  For nx = 1 the second and
+  // right columns are not wrapped onto the row; they only feed the unused second column.
+  const int cL = c0 - 1 + (full && c0 == 0 ? nx : 0);
+  const int cR1 = c0 + 1 - (full && c0 + 1 >= nx ? nx : 0);
+  const int cR2 = c0 + 2 - (full && c0 + 2 >= nx ? nx : 0);
+  // Ghost columns (periodic copies at -2, -1, nx, nx+1), kept current by strip-mode
+  // sweeps.  For even nx >= 4 the owners of the pairs (0, 1) and (nx-2, nx-1) mirror them
+  // as pairs to (nx, nx+1) and (-2, -1); every other case (odd nx, nx < 4) takes the
+  // general per-column path.
   const bool ghost_pairs = (nx & 1) == 0 && nx >= 4;
   constexpr int NO_GHOST = -(1 << 30);
-  const int gpair = !ghost_pairs ? NO_GHOST : xa == 0 ? nx : xa == nx - 2 ? -2 : NO_GHOST;
-  const bool ghost_slow = !ghost_pairs && (xa < 2 || xa + 1 >= nx - 2);
+  const int gpair = full || !ghost_pairs ? NO_GHOST
+                                         : xa == 0 ? nx : xa == nx - 2 ? -2 : NO_GHOST;
+  const bool ghost_slow = !full && !ghost_pairs && (xa < 2 || xa + 1 >= nx - 2);
   const int dir = it.dir < 0 ? -1 : 1;
   const int y0 = it.y0, y1 = it.y1;
   const int nload = y1 - y0 + 4;
   const int rstart = dir > 0 ? y0 - 2 : y1 + 1;
-  const int seg0 = GHOST + x0 - SEG_HALO;
-  const int len = min(SEG, pitch - seg0);
+  // copy of a plane row: storage columns [seg0, seg0 + len) into ring columns from dst0
+  const int seg0 = full ? GHOST : GHOST + x0 - SEG_HALO;
+  const int dst0 = full ? SEG_HALO : 0;
+  const int len = full ? (nx + 3) & ~3 : min(SEG, pitch - seg0);
   const uint32_t plane_bytes = (uint32_t)len * (uint32_t)sizeof(float);
   const float* gsrc = fin + P.off + seg0;
   const float2 rho_ref2 = N::k(ph.rho_ref);
-  // bounds-check build: this thread's psi pair, and an owner's psi neighbours -1 .. +2
+  // bounds-check build: this thread's psi pair, and an owner's psi neighbours
   const bool psi_ok = LBM_IN(2 + c0 >= 0 && 2 + c0 + 2 <= PSW);
-  const bool psi_nb_ok = !owner || LBM_IN(1 + c0 >= 0 && 2 + c0 + 3 <= PSW);
+  const bool psi_nb_ok =
+      !owner || LBM_IN(2 + cL >= 0 && 2 + cL < PSW && 2 + cR1 < PSW && 2 + cR2 < PSW);
 
   // Row j of the sweep: the planes of each group into that group's ring (see Sweep2Cfg),
   // completion on row barrier j % NB.
@@ -904,7 +929,7 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
     const int r = rstart + j * dir;
     const int rp = walls ? (r < 0 ? 0 : (r >= ny ? ny - 1 : r)) : wrapi(r, ny);
     const float* src = gsrc + (long long)rp * pitch;
-    const bool ok = LBM_IN(rp >= 0 && rp < ny && seg0 >= 0 && len > 0 && len <= SEG &&
+    const bool ok = LBM_IN(rp >= 0 && rp < ny && seg0 >= 0 && len > 0 && dst0 + len <= SEG &&
                            seg0 + len <= pitch);
     const bool ahead = j >= 1;  // the ahead planes of row 0 are never read
     uint64_t* bar = &bars[j % NB];
@@ -920,7 +945,7 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
       if (dst == dA && !ahead) continue;
       if (!LBM_IN(dst + kidx_of(q) * SEG >= ring && dst + (kidx_of(q) + 1) * SEG <= ring + RING))
         continue;
-      bulk_g2s(dst + kidx_of(q) * SEG, src + (long long)q * plane, plane_bytes, bar);
+      bulk_g2s(dst + kidx_of(q) * SEG + dst0, src + (long long)q * plane, plane_bytes, bar);
     }
   };
 
@@ -969,48 +994,44 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
       const bool bb_high = walls && rpsi == ny - 1;
       // group bases of this pull: e_y = -1 planes (from y + 1), e_y = 0 (row y), e_y = +1
       // (from y - 1); ahead is y + dir
-      const float* pA = ringA + sa * 3 * SEG + SEG_HALO + c0;  // row s+1
-      const float* pC = ringC + sc * 3 * SEG + SEG_HALO + c0;  // row s
-      const float* pB = ringB + sb * 3 * SEG + SEG_HALO + c0;  // row s-1
+      const float* pA = ringA + sa * 3 * SEG + SEG_HALO;  // row s+1 (ring column of CTA column 0)
+      const float* pC = ringC + sc * 3 * SEG + SEG_HALO;  // row s
+      const float* pB = ringB + sb * 3 * SEG + SEG_HALO;  // row s-1
       const float* gm = dir > 0 ? pA : pB;
       const float* gp = dir > 0 ? pB : pA;
-      auto pair_at = [&](const float* p) -> float2 {  // columns c0, c0+1 (8-byte aligned)
-        return *reinterpret_cast<const float2*>(p);
-      };
       auto in_ring = [&](const float* p) {  // bounds-check build
-        return LBM_IN(p >= ring && p + 2 <= ring + RING);
+        return LBM_IN(p >= ring && p < ring + RING);
+      };
+      // plane row p: the pair of columns (c0, c0+1) shifted by -e_x (8-byte aligned load
+      // when e_x = 0)
+      auto pull = [&](const float* p, int exq) -> float2 {
+        const float* a = p + (exq > 0 ? cL : (exq < 0 ? cR1 : c0));
+        const float* b = p + (exq > 0 ? c0 : (exq < 0 ? cR2 : c0 + 1));
+        if (!(in_ring(a) && in_ring(b))) return N::k(0.f);
+        return exq == 0 ? *reinterpret_cast<const float2*>(a) : make_float2(*a, *b);
       };
       if (!(bb_low || bb_high)) {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-          const int eyq = ey_of(q), exq = ex_of(q);
-          const float* src = (eyq < 0 ? gm : (eyq > 0 ? gp : pC)) + kidx_of(q) * SEG - exq;
-          if (!in_ring(src))
-            nxt[q] = N::k(0.f);
-          else
-            nxt[q] = exq == 0 ? pair_at(src) : make_float2(src[0], src[1]);
+          const int eyq = ey_of(q);
+          nxt[q] = pull((eyq < 0 ? gm : (eyq > 0 ? gp : pC)) + kidx_of(q) * SEG, ex_of(q));
         }
       } else {
         // Halfway bounce-back: a plane that would come from beyond the wall is the
         // opposite plane of this row; those are in the ahead or behind ring of row s.
-        const float* sA = ringA + (s % DA) * 3 * SEG + SEG_HALO + c0;
-        const float* sB = ringB + (s % DB) * 3 * SEG + SEG_HALO + c0;
+        const float* sA = ringA + (s % DA) * 3 * SEG + SEG_HALO;
+        const float* sB = ringB + (s % DB) * 3 * SEG + SEG_HALO;
         const float* cm = dir > 0 ? sA : sB;  // e_y = -1 planes of row s
         const float* cp = dir > 0 ? sB : sA;  // e_y = +1 planes of row s
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-          const int eyq = ey_of(q), exq = ex_of(q);
+          const int eyq = ey_of(q);
           const bool bb = (eyq > 0 && bb_low) || (eyq < 0 && bb_high);
           if (bb) {
             const int o = opp_of(q);
-            const float* src = (ey_of(o) < 0 ? cm : cp) + kidx_of(o) * SEG;
-            nxt[q] = in_ring(src) ? pair_at(src) : N::k(0.f);
+            nxt[q] = pull((ey_of(o) < 0 ? cm : cp) + kidx_of(o) * SEG, 0);
           } else {
-            const float* src = (eyq < 0 ? gm : (eyq > 0 ? gp : pC)) + kidx_of(q) * SEG - exq;
-            if (!in_ring(src))
-              nxt[q] = N::k(0.f);
-            else
-              nxt[q] = exq == 0 ? pair_at(src) : make_float2(src[0], src[1]);
+            nxt[q] = pull((eyq < 0 ? gm : (eyq > 0 ? gp : pC)) + kidx_of(q) * SEG, ex_of(q));
           }
         }
       }
@@ -1040,19 +1061,25 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
 
     if (s >= 3 && owner && psi_nb_ok) {
       const int yc = rstart + (s - 1) * dir;
-      const float* pa = psis + ((s - 2) & (PSI_ROWS - 1)) * PSW + 2 + c0;  // row yc - dir
-      const float* pc = psis + ((s - 1) & (PSI_ROWS - 1)) * PSW + 2 + c0;  // row yc
-      const float* pb = ps_now + 2 + c0;                                    // row yc + dir
+      const float* pa = psis + ((s - 2) & (PSI_ROWS - 1)) * PSW + 2;  // row yc - dir
+      const float* pc = psis + ((s - 1) & (PSI_ROWS - 1)) * PSW + 2;  // row yc
+      const float* pb = ps_now + 2;                                    // row yc + dir
       const float* pn = dir > 0 ? pb : pa;
       const float* pso = dir > 0 ? pa : pb;
-      // psi at columns c0-1 .. c0+2 of the three rows, as pairs for columns (c0, c0+1)
-      const float2 cC = *reinterpret_cast<const float2*>(pc);
-      const float2 cN = *reinterpret_cast<const float2*>(pn);
-      const float2 cS = *reinterpret_cast<const float2*>(pso);
-      const float cWm = pc[-1], cEp = pc[2], nWm = pn[-1], nEp = pn[2], sWm = pso[-1], sEp = pso[2];
-      const float2 pE = make_float2(cC.y, cEp), pW = make_float2(cWm, cC.x);
-      const float2 pNE = make_float2(cN.y, nEp), pNW = make_float2(nWm, cN.x);
-      const float2 pSE = make_float2(cS.y, sEp), pSW = make_float2(sWm, cS.x);
+      // psi at the columns left of, in and right of the pair (c0, c0+1) in the three rows.
+      // The east neighbour of column c0 is column c0+1 except for the odd last column of
+      // a full-width strip, whose neighbour is column 0.
+      const bool wrap_e = cR1 != c0 + 1;
+      const float2 cC = *reinterpret_cast<const float2*>(pc + c0);
+      const float2 cN = *reinterpret_cast<const float2*>(pn + c0);
+      const float2 cS = *reinterpret_cast<const float2*>(pso + c0);
+      const float cWm = pc[cL], cEp = pc[cR2], nWm = pn[cL], nEp = pn[cR2], sWm = pso[cL],
+                  sEp = pso[cR2];
+      const float cE1 = wrap_e ? pc[cR1] : cC.y, nE1 = wrap_e ? pn[cR1] : cN.y,
+                  sE1 = wrap_e ? pso[cR1] : cS.y;
+      const float2 pE = make_float2(cE1, cEp), pW = make_float2(cWm, cC.x);
+      const float2 pNE = make_float2(nE1, nEp), pNW = make_float2(nWm, cN.x);
+      const float2 pSE = make_float2(sE1, sEp), pSW = make_float2(sWm, cS.x);
       float2 fpx, fpy;
       force_t<float2, float>(pE, pW, cN, cS, pNE, pNW, pSE, pSW, ph, fpx, fpy);
       float2 h[Q];
@@ -1096,7 +1123,7 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
 #pragma unroll
               for (int q = 0; q < Q; ++q) dst[(long long)q * plane + x] = v[q];
             }
-            if (!ghost_pairs && (x < 2 || x >= nx - 2)) {
+            if (!full && !ghost_pairs && (x < 2 || x >= nx - 2)) {
               auto put = [&](int g) {
                 if (wrapi(g, nx) == x && col_ok(g, 1)) {
 #pragma unroll

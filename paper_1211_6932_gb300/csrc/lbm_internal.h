@@ -7,10 +7,12 @@
 namespace lbm {
 
 // Launch the fused sweep (MODE_STEP) or the moments/diagnostics pass (MODE_MOMENTS) over
-// n_items work items; nt (threads per CTA) and vec (columns per thread) select the
-// instantiation.
+// n_items work items; nt (threads per CTA), vec (columns per thread) and, for the pair
+// kernel (vec 2), full (full-width strips, see strips_for) select the instantiation.  A
+// pair-kernel CTA whose instance is not of the launched kind returns at once.
 template <typename S>
-cudaError_t launch_sweep(int nt, int vec, int mode, const S* fin, S* fout, const InstParams* d_inst,
+cudaError_t launch_sweep(int nt, int vec, int mode, int full, const S* fin, S* fout,
+                         const InstParams* d_inst,
                          const WorkItem* d_items, int n_items, const MomArgs<S>& mo,
                          int* d_status, cudaStream_t st);
 template <typename S>
@@ -80,5 +82,15 @@ inline bool cfg_supported(bool fp64, int nt, int vec) {
 
 // Columns owned by one CTA of a configuration.
 inline int strip_width(int nt, int vec) { return vec == 2 ? 2 * nt - 4 : nt - 4; }
+// CTA strips across an instance of nx columns.  The pair kernel (vec 2) covers an
+// instance with nx <= 2 nt in one full-width strip: every thread owns two columns, the
+// periodic wrap in x is taken inside shared memory and the ghost columns are neither
+// read nor written.  Otherwise strips of strip_width owned columns.
+inline bool full_width(int nx, int nt, int vec) { return vec == 2 && nx <= 2 * nt; }
+inline int strips_for(int nx, int nt, int vec) {
+  if (full_width(nx, nt, vec)) return 1;
+  const int W = strip_width(nt, vec);
+  return (nx + W - 1) / W;
+}
 
 }  // namespace lbm

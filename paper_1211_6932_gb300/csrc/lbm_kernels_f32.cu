@@ -4,16 +4,16 @@
 namespace lbm {
 
 template <>
-cudaError_t launch_sweep<float>(int nt, int vec, int mode, const float* fin, float* fout,
+cudaError_t launch_sweep<float>(int nt, int vec, int mode, int full, const float* fin, float* fout,
                              const InstParams* d_inst, const WorkItem* d_items, int n_items,
                              const MomArgs<float>& mo, int* d_status, cudaStream_t st) {
   if (nt == 64 && vec == 1) return launch_sweep_mode<float, 64>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
   if (nt == 128 && vec == 1) return launch_sweep_mode<float, 128>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
   if (nt == 256 && vec == 1) return launch_sweep_mode<float, 256>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
-  if (nt == 32 && vec == 2) return launch_sweep2_mode<32>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
-  if (nt == 64 && vec == 2) return launch_sweep2_mode<64>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
-  if (nt == 96 && vec == 2) return launch_sweep2_mode<96>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
-  if (nt == 128 && vec == 2) return launch_sweep2_mode<128>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
+  if (nt == 32 && vec == 2) return launch_sweep2_mode<32>(mode, full, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
+  if (nt == 64 && vec == 2) return launch_sweep2_mode<64>(mode, full, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
+  if (nt == 96 && vec == 2) return launch_sweep2_mode<96>(mode, full, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
+  if (nt == 128 && vec == 2) return launch_sweep2_mode<128>(mode, full, fin, fout, d_inst, d_items, n_items, mo, d_status, st);
   return cudaErrorInvalidValue;
 }
 

@@ -4,7 +4,7 @@
 namespace lbm {
 
 template <>
-cudaError_t launch_sweep<double>(int nt, int vec, int mode, const double* fin, double* fout,
+cudaError_t launch_sweep<double>(int nt, int vec, int mode, int full, const double* fin, double* fout,
                              const InstParams* d_inst, const WorkItem* d_items, int n_items,
                              const MomArgs<double>& mo, int* d_status, cudaStream_t st) {
   if (nt == 64 && vec == 1) return launch_sweep_mode<double, 64>(mode, fin, fout, d_inst, d_items, n_items, mo, d_status, st);

@@ -47,41 +47,46 @@ static cudaError_t launch_sweep_mode(int mode, const S* fin, S* fout, const Inst
                                                d_status, st);
 }
 
-// FP32 pair kernel (two columns per thread, packed float2 arithmetic).
-template <int NT, int MODE>
+// FP32 pair kernel (two columns per thread, packed float2 arithmetic), strip or
+// full-width instantiation.
+template <int NT, int MODE, bool FULL>
 static cudaError_t launch_sweep2_cfg(const float* fin, float* fout, const InstParams* d_inst,
                                      const WorkItem* d_items, int n_items,
                                      const MomArgs<float>& mo, int* d_status, cudaStream_t st) {
   constexpr size_t smem = Sweep2Cfg<NT>::BYTES;
   static std::atomic<unsigned long long> done{0};
-  cudaError_t e = ensure_smem_attr(sweep2_kernel<NT, MODE>, smem, done);
+  cudaError_t e = ensure_smem_attr(sweep2_kernel<NT, MODE, FULL>, smem, done);
   if (e != cudaSuccess) return e;
   if (n_items <= 0) return cudaSuccess;
-  sweep2_kernel<NT, MODE><<<n_items, NT, smem, st>>>(fin, fout, d_inst, d_items, n_items, mo,
-                                                     d_status);
+  sweep2_kernel<NT, MODE, FULL><<<n_items, NT, smem, st>>>(fin, fout, d_inst, d_items, n_items,
+                                                           mo, d_status);
   return cudaGetLastError();
 }
 
 template <int NT>
-static cudaError_t launch_sweep2_mode(int mode, const float* fin, float* fout,
+static cudaError_t launch_sweep2_mode(int mode, int full, const float* fin, float* fout,
                                       const InstParams* d_inst, const WorkItem* d_items,
                                       int n_items, const MomArgs<float>& mo, int* d_status,
                                       cudaStream_t st) {
   if (mode == MODE_STEP)
-    return launch_sweep2_cfg<NT, MODE_STEP>(fin, fout, d_inst, d_items, n_items, mo, d_status,
-                                            st);
-  return launch_sweep2_cfg<NT, MODE_MOMENTS>(fin, fout, d_inst, d_items, n_items, mo,
-                                             d_status, st);
+    return full ? launch_sweep2_cfg<NT, MODE_STEP, true>(fin, fout, d_inst, d_items, n_items,
+                                                         mo, d_status, st)
+                : launch_sweep2_cfg<NT, MODE_STEP, false>(fin, fout, d_inst, d_items, n_items,
+                                                          mo, d_status, st);
+  return full ? launch_sweep2_cfg<NT, MODE_MOMENTS, true>(fin, fout, d_inst, d_items, n_items,
+                                                          mo, d_status, st)
+              : launch_sweep2_cfg<NT, MODE_MOMENTS, false>(fin, fout, d_inst, d_items, n_items,
+                                                           mo, d_status, st);
 }
 
 template <int NT>
 static int occupancy2_cfg() {
   constexpr size_t smem = Sweep2Cfg<NT>::BYTES;
-  cudaFuncSetAttribute(sweep2_kernel<NT, MODE_STEP>,
+  cudaFuncSetAttribute(sweep2_kernel<NT, MODE_STEP, false>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int occ = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &occ, sweep2_kernel<NT, MODE_STEP>, NT, smem);
+      &occ, sweep2_kernel<NT, MODE_STEP, false>, NT, smem);
   return (e == cudaSuccess && occ > 0) ? occ : 1;
 }
 

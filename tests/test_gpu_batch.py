@@ -70,8 +70,8 @@ def test_fp32_batch_equals_single_lattices_bitwise():
 
 
 def test_per_instance_widths_equal_uniform_tiling_bitwise():
-    """Per-instance kernel widths (one launch per width, graph branches per width) give
-    the populations and diagnostics of the uniform tiling bit for bit, through graph
+    """Per-instance kernel widths (one launch per width and kind of strip, graph branches)
+    give the populations and diagnostics of the uniform tiling bit for bit, through graph
     replays (64 steps) and single launches."""
     from paper_1211_6932_gb300 import Batch
     from paper_1211_6932_gb300.lattice import TILE_PER_INSTANCE
@@ -84,8 +84,10 @@ def test_per_instance_widths_equal_uniform_tiling_bitwise():
         for i, fl in enumerate(fields):
             b.init_fields(i, *fl)
         b.step(70)
-        # widths 32 (nx 5), 64 (70, 64), 96 (130, 257) and 128 (220, 400)
-        assert b.launches_per_step == (1 if threads == 0 else 4)
+        # uniform 128 threads: strips (400, 257) and full-width strips (the rest, nx <= 256);
+        # per instance: widths 32 (nx 5, full), 64 (70, 64, full), 96 (130 full, 257 strips)
+        # and 128 (220 full, 400 strips)
+        assert b.launches_per_step == (2 if threads == 0 else 6)
         pops = [b.get_populations(i) for i in range(len(cs))]
         diags = b.diagnostics()
         b.step(3)
