@@ -746,9 +746,21 @@ def stability_summary(stream):
     from paper_1211_6932_gb300 import stability as st
     t0 = time.perf_counter()
     br = st.lowest_stable_viscosity(stream=stream)
-    return {"seconds": time.perf_counter() - t0, "t_star": 3.0,
-            "brackets": [{"ratio": b.ratio, "unstable_nu_l": b.unstable, "stable_nu_l": b.stable}
-                         for b in br]}
+    out = {"seconds": time.perf_counter() - t0, "t_star": 3.0,
+           "brackets": [{"ratio": b.ratio, "unstable_nu_l": b.unstable, "stable_nu_l": b.stable}
+                        for b in br]}
+    # the same search at the printed ratios under other readings of the paper's setup
+    readings = {"finite_t6": {"t_star": 6.0}, "psi_real": {"criterion": "psi_real"},
+                "umax_0.3": {"criterion": "umax"}, "sharp_velocity": {"velocity": "sharp"},
+                "gap_0": {"gap": 0.0}, "gap_40": {"gap": 40.0}}
+    out["readings"] = {}
+    for name, kw in readings.items():
+        rb = st.lowest_stable_viscosity(ratios=(1.0, 20.0, 50.0), stream=stream, **kw)
+        out["readings"][name] = [{"ratio": b.ratio, "unstable_nu_l": b.unstable,
+                                  "stable_nu_l": b.stable} for b in rb]
+    out["printed"] = {"1": 0.075, "20": 0.009, "50": 0.0039}
+    out["seconds_total"] = time.perf_counter() - t0
+    return out
 
 
 def calibration_summary(stream):

@@ -280,6 +280,12 @@ void* lbm_stream(const lbm_handle* h);
  */
 int lbm_maxwell(lbm_eos eos, double* rho_l, double* rho_v);
 
+/* The argument of the square root of Eq. 24 with the pressure of Eq. 30 (c = 1):
+ * 2 (p_EOS(rho) - rho/3) / G, in double on the host.  psi is real where it is >= 0; the
+ * kernels clamp a negative argument to zero.  LBM_EINVAL unless 0 < rho < 4/b, G != 0 and
+ * the EOS parameters are positive. */
+int lbm_eos_psi2(lbm_eos eos, double G, double rho, double* out);
+
 /*
  * The coexistence densities the model selects for a flat interface: the mechanical-
  * stability condition of Eq. 21 with psi of Eq. 24 and eps = -16 G sigma (Eq. 29 with

@@ -94,6 +94,7 @@ SIGNATURES = {
     "lbm_autotune": (c_int, [c_void_p, c_int, ctypes.c_char_p, ctypes.POINTER(c_int),
                              ctypes.POINTER(c_int), ctypes.POINTER(c_int), dptr]),
     "lbm_maxwell": (c_int, [lbm_eos, dptr, dptr]),
+    "lbm_eos_psi2": (c_int, [lbm_eos, c_double, c_double, dptr]),
     "lbm_mechanical_stability": (c_int, [lbm_eos, c_double, c_double, dptr, dptr]),
     "lbm_sigma_consistent": (c_int, [lbm_eos, c_double, dptr]),
     "lbm_batch_create": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(lbm_instance),

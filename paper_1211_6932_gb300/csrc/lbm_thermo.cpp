@@ -35,6 +35,15 @@ double bisect(F f, double lo, double hi, int iters = 200) {
 
 }  // namespace
 
+extern "C" int lbm_eos_psi2(lbm_eos eos, double G, double rho, double* out) {
+  if (!out || !(eos.a > 0) || !(eos.b > 0) || !(eos.R > 0) || !(eos.T > 0) || !(G != 0) ||
+      !(rho > 0) || !(rho < 4.0 / eos.b))
+    return LBM_EINVAL;
+  const Cs c{eos.a, eos.b, eos.R, eos.T};
+  *out = 2.0 * (c.p(rho) - rho / 3.0) / G;
+  return LBM_OK;
+}
+
 extern "C" int lbm_maxwell(lbm_eos eos, double* rho_l, double* rho_v) {
   if (!rho_l || !rho_v || !(eos.a > 0) || !(eos.b > 0) || !(eos.R > 0) || !(eos.T > 0))
     return LBM_EINVAL;

@@ -35,27 +35,82 @@ class Bracket:
     unstable: float  # largest nu_l seen unstable (below `stable`)
 
 
-def stable_flags(trials, t_star=3.0, precision="fp32", stream=None):
-    """trials: list of (nu_l, ratio); one bool per trial (all run in one batch)."""
+# Criteria of a stable run (the paper states none):
+#   "finite"     density finite and positive everywhere at t* (the default)
+#   "umax"       also the largest |v| (Eq. 6) stays below U_MAX_RUN at every check
+#   "psi_real"   also no node ever reaches the density where 2 (p_EOS - rho/3) / G turns
+#                negative (so psi of Eq. 24 stays real without the clamp at zero)
+U_MAX_RUN = 0.3  # about half the lattice speed of sound
+CHECK_EVERY = 100
+
+
+def psi_real_limit(eos, G=-1.0):
+    """Smallest density above the liquid density where 2 (p_EOS - rho/3) / G < 0 (Eqs. 24,
+    30), by bisection on the library's psi evaluation."""
+    import ctypes
+    from . import _lib as C
+    rl, _ = maxwell(eos)
+    lo, hi = rl, 4.0 / eos.b * (1.0 - 1e-9)
+
+    def psi2(r):
+        out = ctypes.c_double()
+        rc = C.lib().lbm_eos_psi2(eos.c(), float(G), float(r), ctypes.byref(out))
+        if rc != 0:
+            raise RuntimeError("lbm_eos_psi2 failed")
+        return out.value
+
+    if psi2(hi) >= 0:
+        return hi
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        if psi2(mid) >= 0:
+            lo = mid
+        else:
+            hi = mid
+    return hi
+
+
+def stable_flags(trials, t_star=3.0, precision="fp32", stream=None, criterion="finite",
+                 velocity="fraction", gap=None):
+    """trials: list of (nu_l, ratio); one bool per trial (all run in one batch).
+    criterion, velocity and gap select the readings described above and in
+    workloads.splash."""
     eos = Eos(a=A, T=TR * TC)
     rl, rv = maxwell(eos)
-    rho, ux, uy = wl.splash(NX, NY, rl, rv, 4.0, FILM, D, U)
+    rho, ux, uy = wl.splash(NX, NY, rl, rv, 4.0, FILM, D, U, velocity=velocity, gap=gap)
     insts = [Instance(nx=NX, ny=NY, eos=eos, sigma=SIGMA, s=RATES, nu_l=nu, nu_v=r * nu,
                       visc_mode="step", bc="walls", rho_l=rl, rho_v=rv) for nu, r in trials]
     steps = int(round(t_star * D / U))
+    rho_lim = psi_real_limit(eos) if criterion == "psi_real" else None
+    ok = [True] * len(insts)
     b = Batch(insts, precision=precision, stream=stream)
     try:
         for i in range(len(insts)):
             b.init_fields(i, rho, ux, uy)
-        b.step(steps)
+        if criterion == "finite":
+            b.step(steps)
+        else:
+            done = 0
+            while done < steps:
+                n = min(CHECK_EVERY, steps - done)
+                b.step(n)
+                done += n
+                diag = b.diagnostics()
+                for i in range(len(insts)):
+                    if not ok[i]:
+                        continue
+                    if criterion == "umax" and not diag[i]["max_u"] < U_MAX_RUN:
+                        ok[i] = False
+                    elif criterion == "psi_real" and not float(b.density(i).max()) < rho_lim:
+                        ok[i] = False
         diag = b.diagnostics()
         out = []
         for i in range(len(insts)):
-            ok = diag[i]["nonfinite"] == 0
-            if ok:
+            good = ok[i] and diag[i]["nonfinite"] == 0
+            if good:
                 d = b.density(i)
-                ok = bool(np.all(np.isfinite(d)) and d.min() > 0.0)
-            out.append(ok)
+                good = bool(np.all(np.isfinite(d)) and d.min() > 0.0)
+            out.append(good)
     finally:
         b.close()
     return out
@@ -63,14 +118,15 @@ def stable_flags(trials, t_star=3.0, precision="fp32", stream=None):
 
 def lowest_stable_viscosity(ratios=(1.0, 2.0, 5.0, 10.0, 15.0, 20.0, 35.0, 50.0),
                             nu_lo=1e-3, nu_hi=0.3, nu_v_max=1.0, k=4, rounds=4, t_star=3.0,
-                            stream=None):
+                            stream=None, **reading):
     """Returns a Bracket per ratio: the boundary lies between `unstable` and `stable`.
     The search starts from [nu_lo, min(nu_hi, nu_v_max / ratio)]: a vapour viscosity far
-    above 1 (tau_v > 3.5) is a different instability, outside the question."""
+    above 1 (tau_v > 3.5) is a different instability, outside the question.  `reading`
+    passes criterion / velocity / gap to stable_flags."""
     br = [Bracket(r, min(nu_hi, nu_v_max / r), nu_lo) for r in ratios]
     # the ends of the search interval, once
     flags = stable_flags([(b.stable, b.ratio) for b in br] + [(nu_lo, r) for r in ratios],
-                         t_star, stream=stream)
+                         t_star, stream=stream, **reading)
     n = len(ratios)
     for j, b in enumerate(br):
         if not flags[j]:
@@ -86,7 +142,7 @@ def lowest_stable_viscosity(ratios=(1.0, 2.0, 5.0, 10.0, 15.0, 20.0, 35.0, 50.0)
         for b in live:
             lo, hi = math.log(b.unstable), math.log(b.stable)
             trials += [(math.exp(lo + (hi - lo) * (i + 1) / (k + 1)), b.ratio) for i in range(k)]
-        flags = stable_flags(trials, t_star, stream=stream)
+        flags = stable_flags(trials, t_star, stream=stream, **reading)
         for j, b in enumerate(live):
             pts = trials[j * k:(j + 1) * k]
             ok = flags[j * k:(j + 1) * k]

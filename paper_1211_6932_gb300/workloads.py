@@ -65,17 +65,24 @@ def ellipse(nx, ny, rho_l, rho_v, ax, ay, W, noise=0.0, seed=0):
     return rho
 
 
-def splash(nx, ny, rho_l, rho_v, W, film_h, D, U):
+def splash(nx, ny, rho_l, rho_v, W, film_h, D, U, velocity="fraction", gap=None):
     """Droplet of diameter D moving down at speed U above a liquid film of thickness
     film_h lying on the bottom wall (rows 0..film_h-1).  Returns rho, ux, uy.  The droplet
-    velocity is weighted by its liquid fraction; its centre is D/2 + 2W above the film."""
+    velocity is weighted by its liquid fraction (velocity="fraction"), or is U on the nodes
+    denser than the mean of the phase densities and zero elsewhere (velocity="sharp").
+    The droplet's centre is D/2 + gap above the film, gap = 2W unless given."""
     x, y = grid(nx, ny)
     film = tanh_profile(y - (film_h - 0.5), rho_l, rho_v, W)
     cx = (nx - 1) / 2.0
-    cy = film_h + D / 2.0 + 2.0 * W
+    cy = film_h + D / 2.0 + (2.0 * W if gap is None else gap)
     drop = tanh_profile(np.hypot(x - cx, y - cy) - D / 2.0, rho_l, rho_v, W)
     rho = np.maximum(film, drop)
-    frac = np.clip((drop - rho_v) / (rho_l - rho_v), 0.0, 1.0)
+    if velocity == "fraction":
+        frac = np.clip((drop - rho_v) / (rho_l - rho_v), 0.0, 1.0)
+    elif velocity == "sharp":
+        frac = (drop > 0.5 * (rho_l + rho_v)).astype(np.float64)
+    else:
+        raise ValueError("velocity must be 'fraction' or 'sharp'")
     ux = np.zeros_like(rho)
     uy = -U * frac
     return rho, ux, uy

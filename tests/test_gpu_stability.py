@@ -58,3 +58,16 @@ def test_stability_verdicts_match_oracle():
             d = oracle.fields(p, oracle.run(p, f0, steps))["rho"]
             verdicts.append(bool(np.all(np.isfinite(d)) and d.min() > 0.0))
         assert verdicts == [True, False], (b, verdicts)
+
+
+def test_psi_clamp_does_not_decide_stability():
+    """Reading check for Fig. 4: at both ends of the ratio-1 bracket, a run that must also
+    keep the argument of Eq. 24's square root non-negative everywhere at every check (no
+    use of the clamp at zero) gets the same verdict as the finite-density criterion; the
+    splash blows up before any node is compressed to the density where the clamp would
+    act."""
+    from paper_1211_6932_gb300 import stability as st
+    br = st.lowest_stable_viscosity(ratios=(1.0,), rounds=2)[0]
+    trials = [(br.stable, 1.0), (br.unstable, 1.0)]
+    assert st.stable_flags(trials) == [True, False]
+    assert st.stable_flags(trials, criterion="psi_real") == [True, False]
