@@ -296,15 +296,19 @@ def run_reference(args):
     return 0
 
 
+BATCH_SCREEN = 10000  # --batch-screen
+
+
 def batch256_instances():
-    """The batched-equilibria recipe with the instances that turn non-finite within 10^4
-    steps (a screen, untimed) left out: (instances, fields, total nodes, screen record)."""
+    """The batched-equilibria recipe with the instances that turn non-finite within
+    BATCH_SCREEN steps (a screen, untimed) left out: (instances, fields, total nodes,
+    screen record)."""
     from paper_1211_6932_gb300 import batched
     insts, fields, draws = batched.instances(256, seed=4)
     t0 = time.perf_counter()
-    bad = batched.screen(insts, fields, steps=10000)
+    bad = batched.screen(insts, fields, steps=BATCH_SCREEN) if BATCH_SCREEN > 0 else []
     keep = [i for i in range(len(insts)) if i not in bad]
-    rec = {"screen_steps": 10000, "retired_unstable": bad,
+    rec = {"screen_steps": BATCH_SCREEN, "retired_unstable": bad,
            "retired_draws": [{k: draws[i][k] for k in ("nx", "ny", "a", "T_over_Tc", "sigma",
                                                         "visc_ratio", "kind")} for i in bad],
            "screen_s": time.perf_counter() - t0}
@@ -353,6 +357,10 @@ def run_batch(args):
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
+    # the diagnostics pass: one moments launch per kind of strip present (full-width for
+    # instances of at most two columns per thread of its 128-thread CTAs) and the reduction
+    mom_nt = 128 if nt < 0 else nt
+    diag_launches = 1 + len({i.nx <= 2 * mom_nt for i in insts}) if vec == 2 else 2
     k = 0
     launches = 0
     while k < K:
@@ -365,7 +373,7 @@ def run_batch(args):
         launches += n * per_step
         if n == DIAG_EVERY:
             b.diagnostics()
-            launches += 2
+            launches += diag_launches
         k += n
     t1.record(stream)
     torch.cuda.synchronize()
@@ -971,14 +979,18 @@ def main():
     ap.add_argument("--workload", default="field4096", choices=["field4096", "batch256"],
                     help="field4096 (default): the 4096^2 droplet field; batch256: the "
                          "256-instance batched-equilibria recipe")
+    ap.add_argument("--batch-screen", type=int, default=10000,
+                    help="steps of the untimed instability screen of the 256-instance "
+                         "batch (0: none; for short profiling runs)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="fp32 (default; the headline) or fp64 (the parity mode)")
     ap.add_argument("--grid", type=int, default=4096,
                     help="square grid side (default 4096; smaller grids for profiling)")
     args = ap.parse_args()
-    global NX, NY, PREC
+    global NX, NY, PREC, BATCH_SCREEN
     NX = NY = args.grid
     PREC = args.precision
+    BATCH_SCREEN = args.batch_screen
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -891,12 +891,15 @@ int get_pops(Batch* b, int i, double* f) {
 template <typename S>
 cudaError_t launch_moments(const Batch* b, const WorkItem* d_items, int n,
                            const MomArgs<S>& mo) {
-  const int kinds = (!b->fp64 && b->vec == 2) ? 2 : 1;
+  bool kind[2] = {false, false};  // strips, full-width strips present
+  for (int i = 0; i < b->n_inst; ++i)
+    kind[lbm::full_width(b->inst[i].nx, mom_nt(b), b->vec) ? 1 : 0] = true;
   cudaError_t e = cudaSuccess;
-  for (int full = 0; full < kinds && e == cudaSuccess; ++full)
-    e = lbm::launch_sweep<S>(mom_nt(b), b->vec, lbm::MODE_MOMENTS, full,
-                             (const S*)b->slab[b->cur], nullptr, b->d_inst, d_items, n, mo,
-                             b->d_status, b->stream);
+  for (int full = 0; full < 2 && e == cudaSuccess; ++full)
+    if (kind[full])
+      e = lbm::launch_sweep<S>(mom_nt(b), b->vec, lbm::MODE_MOMENTS, full,
+                               (const S*)b->slab[b->cur], nullptr, b->d_inst, d_items, n, mo,
+                               b->d_status, b->stream);
   return e;
 }
 
