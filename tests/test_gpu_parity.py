@@ -315,3 +315,35 @@ def test_fp32_deviation_reference_choice():
             m = L.moments()
         errs.append(float(np.max(np.abs(m["rho"] - ref["rho"]) / ref["rho"])))
     assert errs[0] <= 1e-4 and errs[0] <= 1.5 * errs[1], errs
+
+
+@pytest.mark.parametrize("nt", [32, 64, 96, 128])
+@pytest.mark.parametrize("dx", [-1, 0, 1])
+@pytest.mark.parametrize("walls", [False, True])
+def test_fp32_full_width_and_strip_boundary(nt, dx, walls):
+    """Widths at the switch between a full-width strip (nx <= 2 NT: one CTA across the row,
+    x wrapped in shared memory, no ghost columns) and strips (nx = 2 NT + 1), for every
+    pair-kernel width, periodic and with walls: two steps against the oracle, a 64-step
+    graph replay and a single launch after it, then two more steps against the oracle."""
+    nx = 2 * nt + dx
+    c = pairs.case(nx, 11, tr=0.65, sigma=0.114, walls=walls, visc="linear", nu_l=0.05,
+                   nu_v=0.4)
+    p = pairs.oracle_params(c)
+    rl, rv = pairs.maxwell(c)
+    rng = np.random.default_rng(nx * 7 + int(walls))
+    rho = rv + (rl - rv) * rng.uniform(0.0, 1.0, (11, nx))
+    f = oracle.equilibrium(rho, 0.01 * rng.uniform(-1, 1, rho.shape),
+                           0.01 * rng.uniform(-1, 1, rho.shape))
+    with pairs.gpu_lattice(c, "fp32", tile_threads=nt, tile_vec=2, tile_rows=4) as L:
+        L.set_populations(f)
+        for phase in range(2):
+            for k in range(2):
+                f_in = L.get_populations()
+                L.step(1)
+                ok, err = fp32_close(L.get_populations(), oracle.run(p, f_in, 1),
+                                     oracle.fields(p, f_in)["rho"])
+                assert ok, (phase, k, err)
+            if phase == 0:
+                L.step(65)  # one graph replay of 64 steps and one single launch
+                assert L.diagnostics()["nonfinite"] == 0
+        L.check_guards()
