@@ -1790,6 +1790,10 @@ int lbm_load(lbm_handle* h, const char* path) {
   for (int k = 0; k < 2; ++k)
     CK(b, cudaMemcpyAsync((char*)b->slab[k] + P.off * b->esz, buf.data(), buf.size(),
                           cudaMemcpyHostToDevice, b->stream));
+  // A state saved after full-width sweeps carries stale ghost columns; this handle's
+  // tiling may sweep the lattice in strips, which read them.
+  CK(b, b->fp64 ? lbm::launch_fill_ghosts<double>((double*)b->slab[b->cur], P, b->stream)
+                : lbm::launch_fill_ghosts<float>((float*)b->slab[b->cur], P, b->stream));
   CK(b, cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream));
   CK(b, cudaStreamSynchronize(b->stream));
   b->steps[0] = hd.step;

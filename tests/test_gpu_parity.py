@@ -267,6 +267,28 @@ def test_save_load_resume_is_bitwise(tmp_path):
         assert ei.value.code == -7
 
 
+def test_save_load_across_full_width_and_strip_tilings(tmp_path):
+    """A state saved after full-width sweeps (nx = 100 <= 2 x 128: ghost columns not kept)
+    and loaded into a handle that sweeps the same lattice in 32-thread strips (which read
+    the ghost columns) continues like the original: against the oracle, step by step."""
+    c = pairs.case(100, 40, tr=0.65, sigma=0.114)
+    p = pairs.oracle_params(c)
+    f = pairs.droplet_state(c, vel=0.01, seed=5)
+    path = os.path.join(tmp_path, "state.lbm")
+    with pairs.gpu_lattice(c, "fp32") as L:  # default tiling: one full-width strip
+        L.set_populations(f)
+        L.step(30)
+        L.save(path)
+    with pairs.gpu_lattice(c, "fp32", tile_threads=32, tile_vec=2) as L2:
+        L2.load(path)
+        for k in range(2):
+            f_in = L2.get_populations()
+            L2.step(1)
+            ok, err = fp32_close(L2.get_populations(), oracle.run(p, f_in, 1),
+                                 oracle.fields(p, f_in)["rho"])
+            assert ok, (k, err)
+
+
 def test_nonfinite_state_is_reported():
     """A NaN placed in the input populations (on the host) is reported by lbm_sync."""
     from paper_1211_6932_gb300 import LbmError
