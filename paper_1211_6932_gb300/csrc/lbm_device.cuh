@@ -226,7 +226,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 // Wait for the completion of phase `parity` of bar; false after `limit` polls.
 __device__ __forceinline__ bool mbar_wait_polls(uint64_t* bar, uint32_t parity, long long limit) {
-  for (long long i = 0; i < limit; ++i)
+  if (mbar_try_wait(bar, parity)) return true;  // the common case: the phase has completed
+  const int n = limit < (1LL << 30) ? (int)limit : (1 << 30);  // a 32-bit loop counter
+  for (int i = 1; i < n; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
