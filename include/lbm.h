@@ -80,11 +80,15 @@ typedef struct {
   int tile_threads; /* threads per CTA of the step kernel; 0 (default): 128.
                        LBM_TILE_PER_INSTANCE (FP32_DEV with tile_vec 2 only): each
                        instance gets the pair-kernel width (32, 64, 96 or 128 threads)
-                       that wastes least of its columns; one launch per width per step */
+                       that wastes least of its columns; one launch per width and kind of
+                       strip per step */
   int tile_vec;     /* adjacent columns per thread: 1, or 2 (FP32 only: packed float2
                        arithmetic); available (threads, vec) pairs: FP32 (64|128|256, 1),
                        (32|64|96|128, 2); FP64 (64|128, 1).  0 (default): 2 for FP32_DEV,
-                       1 for FP64.  A CTA owns threads*vec - 4 columns. */
+                       1 for FP64.  A CTA owns threads*vec - 4 columns; with vec 2 a
+                       lattice of at most 2*threads columns is swept in one full-width
+                       strip per row (all threads own columns, x wraps in shared memory,
+                       no ghost columns read or written). */
   int tile_rows;  /* rows per CTA sweep; 0 (default): sized to fill the GPU */
 } lbm_options;
 
@@ -336,8 +340,8 @@ const char* lbm_batch_last_error(const lbm_batch* b);
 /* Equilibrium initialisation of instance i from host fields, as lbm_init_fields. */
 int lbm_batch_init_fields(lbm_batch* b, int i, const double* rho, const double* ux,
                           const double* uy);
-/* Advance every active instance n steps (one launch per step and kernel width, CUDA-graph
- * replay; see lbm_batch_launches_per_step). */
+/* Advance every active instance n steps (one launch per step, kernel width and kind of
+ * strip, CUDA-graph replay; see lbm_batch_launches_per_step). */
 int lbm_batch_step(lbm_batch* b, int n);
 /* Float host variant of lbm_batch_init_fields, as lbm_init_fields_f32. */
 int lbm_batch_init_fields_f32(lbm_batch* b, int i, const float* rho, const float* ux,
@@ -389,8 +393,10 @@ int lbm_batch_autotune(lbm_batch* b, int steps, const char* cache_path, int* thr
                        int* vec, int* rows, double* ms_per_step);
 /* Tiling in use by a batch (threads is LBM_TILE_PER_INSTANCE for per-instance widths). */
 int lbm_batch_get_tiling(const lbm_batch* b, int* threads, int* vec, int* rows);
-/* Step-kernel launches per step of lbm_batch_step (0 when nothing is active; with
- * LBM_TILE_PER_INSTANCE one per pair-kernel width in use, else 1). */
+/* Step-kernel launches per step of lbm_batch_step (0 when nothing is active): one per
+ * kernel width in use (several only with LBM_TILE_PER_INSTANCE) and kind of strip
+ * (full-width strips for instances of at most 2 * threads columns, strips for wider
+ * ones; pair kernel only). */
 int lbm_batch_launches_per_step(const lbm_batch* b);
 
 /*
