@@ -360,7 +360,8 @@ def run_batch(args):
     # the diagnostics pass: one moments launch per kind of strip present (full-width for
     # instances of at most two columns per thread of its 128-thread CTAs) and the reduction
     mom_nt = 128 if nt < 0 else nt
-    diag_launches = 1 + len({i.nx <= 2 * mom_nt for i in insts}) if vec == 2 else 2
+    stored_nx = [i.ny if b.is_transposed(k) else i.nx for k, i in enumerate(insts)]
+    diag_launches = 1 + len({nx <= 2 * mom_nt for nx in stored_nx}) if vec == 2 else 2
     k = 0
     launches = 0
     while k < K:
@@ -396,6 +397,7 @@ def run_batch(args):
                            "nodes": n_total, "nodes_rank0": n_nodes,
                            "tile_threads": "per_instance" if nt < 0 else nt,
                            "launches_per_step": per_step, "tile_vec": vec,
+                           "transposed_instances": sum(map(b.is_transposed, range(len(insts)))),
                            "tile_rows": rows, "autotuned_ms": tuned_ms,
                            "diag_every": DIAG_EVERY,
                            "l2": "state %.2f GB > 129 MB L2, no flush" % (72 * n_nodes / 1e9),
@@ -902,6 +904,7 @@ def warm_start_ab(stream):
     eos = ws.eos_of(A, TR)
     plain = ws.plain_params(eos)
     warm = sur.predict(A, TR, SIGMA, NU_V / NU_L)
+    members = len(sur.nets)
     sur.close()
     cs, rs = wl.droplet_layout(NX, NY, n_droplets(), 40.0, 200.0, seed=5, gap=4 * ws.W_PLAIN)
     drops = ws.drops_array(cs, rs)
@@ -951,7 +954,8 @@ def warm_start_ab(stream):
                   "rel_diff_liquid": ws.tail_mean(rw.liq) / ref_l - 1},
         "horizon": WARM_HORIZON, "thresholds": list(thr),
         "params": {"plain": plain.__dict__, "warm": warm.__dict__},
-        "network": {"updates": int(len(losses)), "loss_first": float(losses[0]),
+        "network": {"members": members, "updates": int(len(losses)),
+                    "loss_first": float(losses[0]),
                     "loss_last": float(losses[-1]), "train_s": t_train},
         "dataset": {"draws": len(draws), "rows": int(len(ds.x)), "dropped": len(ds.dropped),
                     "unconverged": [int(v) for v in (ds.steps < 0).sum(axis=0)],

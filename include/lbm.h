@@ -57,6 +57,17 @@ extern "C" {
                              bounce-back, Sec. IV C); psi at a ghost row equals psi of the
                              adjacent fluid row */
 
+/* Storage orientation of a batch instance (lbm_instance.layout).  The update of Eqs. 2-7
+ * and 25 on a periodic lattice is symmetric under the exchange x <-> y (D2Q9 velocities,
+ * force stencil weights and the moment basis map onto themselves, with j_x <-> j_y,
+ * q_x <-> q_y and p_xx -> -p_xx under equal rates), so an instance may be stored and
+ * swept with its axes exchanged; every host transfer of the batch converts back. */
+#define LBM_LAYOUT_AUTO 0       /* transposed when that needs fewer strip rows at the
+                                   batch's creation tiling (periodic instances of at least
+                                   8 x 8 nodes); as given otherwise */
+#define LBM_LAYOUT_ROWS 1       /* as given: rows of nx nodes */
+#define LBM_LAYOUT_TRANSPOSED 2 /* axes exchanged: rows of ny nodes (periodic only) */
+
 /* Carnahan-Starling equation of state, Eq. 30:
  *   p = rho R T (1 + x + x^2 - x^3) / (1 - x)^3 - a rho^2,  x = b rho / 4. */
 typedef struct {
@@ -327,10 +338,24 @@ typedef struct {
   double rho_l;    /* <= 0: Maxwell */
   double rho_v;
   double rho_ref;  /* < 0: Maxwell vapour density (FP32_DEV only) */
+  int layout;      /* LBM_LAYOUT_* (0, the zero-initialised value, is AUTO).  A transposed
+                      instance is stepped as the ny x nx lattice with the axes exchanged;
+                      lbm_batch_init_fields*, lbm_batch_moments*,
+                      lbm_batch_get_populations and lbm_batch_diagnostics take and return
+                      its fields, populations and momentum in the given (nx, ny)
+                      orientation, so the layout is visible only through
+                      lbm_batch_instance_transposed and the rounding of the results (a
+                      transposed instance equals, bit for bit, the ny x nx lattice started
+                      from the transposed fields).  TRANSPOSED with LBM_BC_WALLS_Y is
+                      LBM_EINVAL. */
 } lbm_instance;
 
 /* Create a batch of n >= 1 instances in one precision; stream may be NULL; device,
- * tile_threads, tile_vec and tile_rows as in lbm_options (-1, 0, 0, 0 = defaults). */
+ * tile_threads, tile_vec and tile_rows as in lbm_options (-1, 0, 0, 0 = defaults).  The
+ * orientation of each LBM_LAYOUT_AUTO instance is fixed here, from the strip rows of its
+ * two orientations at this tiling (a strip row of w computed columns costing w + 57
+ * column-equivalents; the pair-kernel width rule under LBM_TILE_PER_INSTANCE), and kept
+ * through later tiling changes. */
 int lbm_batch_create(lbm_batch** out, int n, const lbm_instance* inst, int precision,
                      void* stream, int device, int tile_threads, int tile_vec,
                      int tile_rows);
@@ -370,6 +395,9 @@ int lbm_batch_run_to_equilibrium(lbm_batch* b, double tol, int check_every,
 
 /* Number of instances still being stepped. */
 int lbm_batch_active(const lbm_batch* b);
+/* 1 if instance i is stored transposed (lbm_instance.layout), 0 if as given, LBM_EINVAL
+ * for a bad handle or index. */
+int lbm_batch_instance_transposed(const lbm_batch* b, int i);
 /* 1 if instance i is still being stepped, 0 if it is frozen (converged or retired),
  * LBM_EINVAL for a bad handle or index. */
 int lbm_batch_instance_active(const lbm_batch* b, int i);

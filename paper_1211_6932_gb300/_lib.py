@@ -19,6 +19,7 @@ llptr = ctypes.POINTER(ctypes.c_longlong)
 LBM_FP64, LBM_FP32_DEV = 0, 1
 LBM_VISC_CONST, LBM_VISC_STEP, LBM_VISC_LINEAR = 0, 1, 2
 LBM_BC_PERIODIC, LBM_BC_WALLS_Y = 0, 1
+LBM_LAYOUT_AUTO, LBM_LAYOUT_ROWS, LBM_LAYOUT_TRANSPOSED = 0, 1, 2
 LBM_TILE_PER_INSTANCE = -1
 
 
@@ -43,7 +44,8 @@ class lbm_instance(ctypes.Structure):
     _fields_ = [("nx", c_int), ("ny", c_int), ("eos", lbm_eos), ("G", c_double),
                 ("sigma", c_double), ("s", c_double * 9), ("nu_l", c_double),
                 ("nu_v", c_double), ("visc_mode", c_int), ("bc", c_int), ("rho_c", c_double),
-                ("rho_l", c_double), ("rho_v", c_double), ("rho_ref", c_double)]
+                ("rho_l", c_double), ("rho_v", c_double), ("rho_ref", c_double),
+                ("layout", c_int)]
 
 
 class lbm_adam(ctypes.Structure):
@@ -109,6 +111,7 @@ SIGNATURES = {
     "lbm_batch_run_to_equilibrium": (c_int, [c_void_p, c_double, c_int, c_longlong, llptr]),
     "lbm_batch_active": (c_int, [c_void_p]),
     "lbm_batch_instance_active": (c_int, [c_void_p, c_int]),
+    "lbm_batch_instance_transposed": (c_int, [c_void_p, c_int]),
     "lbm_batch_retire": (c_int, [c_void_p, c_int]),
     "lbm_batch_retire_nonfinite": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "lbm_batch_autotune": (c_int, [c_void_p, c_int, ctypes.c_char_p, ctypes.POINTER(c_int),

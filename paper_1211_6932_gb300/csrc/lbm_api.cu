@@ -39,7 +39,8 @@ struct Batch {
   bool fp64 = false;
   size_t esz = 4;
   int n_inst = 0;
-  std::vector<InstParams> inst;
+  std::vector<InstParams> inst;  // storage dimensions (axes exchanged where tr[i])
+  std::vector<char> tr;          // instance stored transposed (lbm_instance.layout)
   std::vector<int> active;
   std::vector<long long> steps;
   std::vector<char> dinf_valid;
@@ -61,6 +62,8 @@ struct Batch {
   double* staging = nullptr;  // 3 x (largest instance) doubles: host uploads and downloads
   size_t staging_elems = 0;
   float* staging32 = nullptr;  // 3 x (largest instance) floats: float host transfers
+  double* staging_t = nullptr;  // 3 x (largest transposed instance) doubles
+  size_t staging_t_elems = 0;
   int* d_flag = nullptr;      // one int for the initialisation's validity check
   double* d_part_sum = nullptr;
   float* d_part_max = nullptr;
@@ -275,6 +278,7 @@ void destroy_batch(Batch* b) {
   for (auto& f : b->fields) f = nullptr;
   b->staging = nullptr;
   b->staging32 = nullptr;
+  b->staging_t = nullptr;
   free_guarded(b);
   free_dev(b->d_part_sum);
   free_dev(b->d_part_max);
@@ -304,6 +308,7 @@ bool tiling_ok(bool fp64, int nt, int vec) {
 int mom_nt(const Batch* b) { return per_instance(b) ? 128 : b->nt; }
 
 constexpr int kPairThreads[Batch::kMaxWidths] = {32, 64, 96, 128};
+constexpr int kRowFixedCols = 57;  // per-row work of a strip row, in computed columns
 
 // Pair-kernel width for an instance of nx columns: the least strip time, where a strip row
 // of 2 nt - 4 owned columns costs its 2 nt computed columns plus a fixed 57
@@ -316,13 +321,35 @@ int pair_threads_for(int nx) {
   long long best_cost = -1;
   for (int g = Batch::kMaxWidths - 1; g >= 0; --g) {
     const int nt = kPairThreads[g];
-    const long long cost = (long long)lbm::strips_for(nx, nt, 2) * (2 * nt + 57);
+    const long long cost = (long long)lbm::strips_for(nx, nt, 2) * (2 * nt + kRowFixedCols);
     if (best_cost < 0 || cost < best_cost) {
       best_cost = cost;
       best = nt;
     }
   }
   return best;
+}
+
+// Modelled time of one lattice row of nx columns at a tiling (threads nt, columns per
+// thread vec, or the per-instance pair width): its strips' computed columns plus the fixed
+// per-row work of each strip.
+long long row_cost(int nx, int nt, int vec) {
+  if (nt == LBM_TILE_PER_INSTANCE) {
+    nt = pair_threads_for(nx);
+    vec = 2;
+  }
+  return (long long)lbm::strips_for(nx, nt, vec) * (nt * vec + kRowFixedCols);
+}
+
+// Orientation of an instance: LBM_LAYOUT_AUTO stores a periodic instance of at least 8 x 8
+// nodes transposed when its ny-column rows cost less in total than its nx-column rows
+// (ties keep the given orientation).  The update is symmetric under x <-> y only without
+// walls, which are along y.
+bool transposed_layout(const lbm_instance& in, int nt, int vec) {
+  if (in.layout == LBM_LAYOUT_TRANSPOSED) return true;
+  if (in.layout != LBM_LAYOUT_AUTO || in.bc != LBM_BC_PERIODIC || in.nx < 8 || in.ny < 8)
+    return false;
+  return row_cost(in.ny, nt, vec) * in.nx < row_cost(in.nx, nt, vec) * in.ny;
 }
 
 // Step-kernel threads per CTA of instance i under the current tiling.
@@ -524,12 +551,23 @@ int create_batch(Batch* b, int n, const lbm_instance* in, bool fp64, int psi_fp6
   b->esz = fp64 ? sizeof(double) : sizeof(float);
   b->n_inst = n;
   b->inst.resize(n);
+  b->tr.assign(n, 0);
   b->active.assign(n, 1);
   b->steps.assign(n, 0);
   b->dinf_valid.assign(n, 0);
   size_t off = 0, dense = 0;
   for (int i = 0; i < n; ++i) {
-    int rc = fill_params(b->err, b->inst[i], in[i], fp64, psi_fp64);
+    lbm_instance li = in[i];
+    if (li.layout < LBM_LAYOUT_AUTO || li.layout > LBM_LAYOUT_TRANSPOSED)
+      return set_err(b->err, LBM_EINVAL, "instance %d: unknown layout %d", i, li.layout);
+    if (li.layout == LBM_LAYOUT_TRANSPOSED && li.bc != LBM_BC_PERIODIC)
+      return set_err(b->err, LBM_EINVAL,
+                     "instance %d: an instance with walls cannot be stored transposed", i);
+    if (transposed_layout(li, nt_, vec_)) {
+      std::swap(li.nx, li.ny);
+      b->tr[i] = 1;
+    }
+    int rc = fill_params(b->err, b->inst[i], li, fp64, psi_fp64);
     if (rc) return rc;
     b->inst[i].off = (long long)off;
     b->inst[i].dense_off = (long long)dense;
@@ -752,6 +790,20 @@ int ensure_staging32(Batch* b) {
                        "float staging");
 }
 
+// Device doubles for 3 fields of the largest transposed instance (its initialisation
+// fields in the stored orientation).
+int ensure_staging_t(Batch* b) {
+  if (b->staging_t) return LBM_OK;
+  size_t m = 1;
+  for (int i = 0; i < b->n_inst; ++i)
+    if (b->tr[i]) m = std::max(m, (size_t)b->inst[i].nx * b->inst[i].ny);
+  int rc = guarded_alloc(b, (void**)&b->staging_t, 3 * m * sizeof(double),
+                         "transposed staging");
+  if (rc) return rc;
+  b->staging_t_elems = m;
+  return LBM_OK;
+}
+
 int ensure_flag(Batch* b) {
   if (!b->d_flag) CK(b, dev_malloc(&b->d_flag, sizeof(int)));
   return LBM_OK;
@@ -783,6 +835,24 @@ int init_instance(Batch* b, int i, const double* rho, const double* ux, const do
       cudaMemcpyAsync(t, uy, N * sizeof(double), cudaMemcpyHostToDevice, b->stream);
       dv = t;
     }
+  }
+  if (b->tr[i]) {
+    // Fields in the given orientation (P.nx rows of P.ny values) into the stored one; the
+    // stored x velocity is the given y velocity and vice versa.
+    rc = ensure_staging_t(b);
+    if (rc) return rc;
+    double* t = b->staging_t;
+    const double* src[3] = {dr, dv, du};
+    const double* dst[3] = {nullptr, nullptr, nullptr};
+    for (int k = 0; k < 3; ++k) {
+      if (!src[k]) continue;
+      double* d = t + k * b->staging_t_elems;
+      CK(b, (lbm::launch_transpose<double, double>(src[k], d, P.ny, P.nx, b->stream)));
+      dst[k] = d;
+    }
+    dr = dst[0];
+    du = dst[1];
+    dv = dst[2];
   }
   cudaMemsetAsync(dbad, 0, sizeof(int), b->stream);
   cudaError_t e;
@@ -866,18 +936,32 @@ int set_pops(Batch* b, int i, const double* f) {
   return LBM_OK;
 }
 
+// Direction of D2Q9 velocity q with its components exchanged (x <-> y): 1 <-> 2, 3 <-> 4,
+// 6 <-> 8.
+constexpr int kSwapXY[9] = {0, 2, 1, 4, 3, 5, 8, 7, 6};
+
 int get_pops(Batch* b, int i, double* f) {
   if (!f) return set_err(b->err, LBM_EINVAL, "f must not be NULL");
   const InstParams& P = b->inst[i];
   const size_t N = (size_t)P.nx * P.ny;
+  const bool t = b->tr[i];
   void* tmp = nullptr;
-  int rc = dev_alloc(b, &tmp, 9 * N * sizeof(double));
+  int rc = dev_alloc(b, &tmp, (t ? 18 : 9) * N * sizeof(double));
   if (rc) return rc;
   cudaError_t e = b->fp64
       ? lbm::launch_get_pops<double>((const double*)b->slab[b->cur], (double*)tmp, P, b->stream)
       : lbm::launch_get_pops<float>((const float*)b->slab[b->cur], (double*)tmp, P, b->stream);
+  const double* out = (const double*)tmp;
+  if (t) {
+    // plane q of the given orientation is the stored plane of q's mirror image, transposed
+    double* g = (double*)tmp + 9 * N;
+    for (int q = 0; q < 9 && e == cudaSuccess; ++q)
+      e = lbm::launch_transpose<double, double>((const double*)tmp + kSwapXY[q] * N, g + q * N,
+                                                P.nx, P.ny, b->stream);
+    out = g;
+  }
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(f, tmp, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+    e = cudaMemcpyAsync(f, out, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   dev_free(tmp);
   if (e != cudaSuccess)
@@ -946,23 +1030,52 @@ int moments_device(Batch* b, int i, void* rho, void* ux, void* uy, bool caller_p
   return moments_pass<float>(b, b->d_all_items + lo, hi - lo, mo);
 }
 
+// Stored field of each host output (rho, ux, uy) of instance i: a transposed instance's
+// x velocity is its stored y velocity.
+void stored_fields(const Batch* b, int i, int sk[3]) {
+  sk[0] = 0;
+  sk[1] = b->tr[i] ? 2 : 1;
+  sk[2] = b->tr[i] ? 1 : 2;
+}
+
+// moments_device into the batch's own fields for the requested host outputs.
+int moments_for_outputs(Batch* b, int i, const void* const outs[3], int sk[3]) {
+  stored_fields(b, i, sk);
+  void* want[3] = {nullptr, nullptr, nullptr};
+  for (int k = 0; k < 3; ++k)
+    if (outs[k]) want[sk[k]] = b->fields[sk[k]];
+  return moments_device(b, i, want[0], want[1], want[2], false);
+}
+
 int moments_host(Batch* b, int i, double* rho, double* ux, double* uy) {
   int rc = ensure_fields(b);
   if (rc) return rc;
-  rc = moments_device(b, i, rho ? b->fields[0] : nullptr, ux ? b->fields[1] : nullptr,
-                      uy ? b->fields[2] : nullptr, false);
+  double* outs[3] = {rho, ux, uy};
+  const void* const req[3] = {rho, ux, uy};
+  int sk[3];
+  rc = moments_for_outputs(b, i, req, sk);
   if (rc) return rc;
   const InstParams& P = b->inst[i];
   const size_t N = (size_t)P.nx * P.ny;
-  double* outs[3] = {rho, ux, uy};
-  if (!b->fp64) {
+  const bool t = b->tr[i];
+  if (!b->fp64 || t) {
     rc = ensure_staging(b);
     if (rc) return rc;
   }
   for (int k = 0; k < 3; ++k) {
     if (!outs[k]) continue;
-    const char* src = (const char*)b->fields[k] + P.dense_off * b->esz;
-    if (b->fp64) {
+    const char* src = (const char*)b->fields[sk[k]] + P.dense_off * b->esz;
+    if (t) {
+      // back to the given orientation (P.ny rows of P.nx values stored), as doubles
+      double* w = b->staging + k * b->staging_elems;
+      if (b->fp64)
+        CK(b, (lbm::launch_transpose<double, double>((const double*)src, w, P.nx, P.ny,
+                                                    b->stream)));
+      else
+        CK(b, (lbm::launch_transpose<float, double>((const float*)src, w, P.nx, P.ny,
+                                                   b->stream)));
+      CK(b, cudaMemcpyAsync(outs[k], w, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    } else if (b->fp64) {
       CK(b, cudaMemcpyAsync(outs[k], src, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
     } else {
       // widen on the device, then one transfer of doubles into the caller's buffer
@@ -980,21 +1093,32 @@ int moments_host(Batch* b, int i, double* rho, double* ux, double* uy) {
 int moments_host_f32(Batch* b, int i, float* rho, float* ux, float* uy) {
   int rc = ensure_fields(b);
   if (rc) return rc;
-  rc = moments_device(b, i, rho ? b->fields[0] : nullptr, ux ? b->fields[1] : nullptr,
-                      uy ? b->fields[2] : nullptr, false);
+  float* outs[3] = {rho, ux, uy};
+  const void* const req[3] = {rho, ux, uy};
+  int sk[3];
+  rc = moments_for_outputs(b, i, req, sk);
   if (rc) return rc;
-  if (b->fp64) {
+  const bool t = b->tr[i];
+  if (b->fp64 || t) {
     rc = ensure_staging32(b);
     if (rc) return rc;
   }
   const InstParams& P = b->inst[i];
   const size_t N = (size_t)P.nx * P.ny;
-  float* outs[3] = {rho, ux, uy};
   for (int k = 0; k < 3; ++k) {
     if (!outs[k]) continue;
-    const char* src = (const char*)b->fields[k] + P.dense_off * b->esz;
+    const char* src = (const char*)b->fields[sk[k]] + P.dense_off * b->esz;
     const float* f = (const float*)src;
-    if (b->fp64) {
+    if (t) {
+      // back to the given orientation, as floats
+      float* w = b->staging32 + k * b->staging_elems;
+      if (b->fp64)
+        CK(b, (lbm::launch_transpose<double, float>((const double*)src, w, P.nx, P.ny,
+                                                   b->stream)));
+      else
+        CK(b, (lbm::launch_transpose<float, float>(f, w, P.nx, P.ny, b->stream)));
+      f = w;
+    } else if (b->fp64) {
       float* w = b->staging32 + k * b->staging_elems;
       CK(b, lbm::launch_narrow((const double*)src, w, (long long)N, b->stream));
       f = w;
@@ -1030,8 +1154,8 @@ int diagnostics(Batch* b, lbm_diag* out) {
   CK(b, cudaStreamSynchronize(b->stream));
   for (int i = 0; i < b->n_inst; ++i) {
     out[i].mass = h[6 * i];
-    out[i].mom_x = h[6 * i + 1];
-    out[i].mom_y = h[6 * i + 2];
+    out[i].mom_x = h[6 * i + (b->tr[i] ? 2 : 1)];  // stored axes of a transposed instance
+    out[i].mom_y = h[6 * i + (b->tr[i] ? 1 : 2)];
     out[i].max_u = h[6 * i + 3];
     out[i].dinf = b->dinf_valid[i] ? h[6 * i + 4] : -1.0;
     out[i].nonfinite = (long long)h[6 * i + 5];
@@ -1396,6 +1520,7 @@ int lbm_create(lbm_handle** out, int nx, int ny, lbm_eos eos, double G, double s
   in.rho_l = o.rho_l;
   in.rho_v = o.rho_v;
   in.rho_ref = o.rho_ref;
+  in.layout = LBM_LAYOUT_ROWS;  // a lattice handle is never transposed
   lbm_handle* h = new (std::nothrow) lbm_handle();
   if (!h) return set_err(g_thread_err, LBM_ENOMEM, "out of host memory");
   int rc = create_batch(&h->b, 1, &in, o.precision == LBM_FP64, o.psi_fp64, o.stream,
@@ -1896,6 +2021,11 @@ int lbm_batch_active(const lbm_batch* b) {
   int n = 0;
   for (int a : b->b.active) n += a;
   return n;
+}
+
+int lbm_batch_instance_transposed(const lbm_batch* b, int i) {
+  if (!b || i < 0 || i >= b->b.n_inst) return LBM_EINVAL;
+  return b->b.tr[i] ? 1 : 0;
 }
 
 int lbm_batch_instance_active(const lbm_batch* b, int i) {

@@ -65,6 +65,11 @@ cudaError_t launch_widen(const float* src, double* dst, long long n, cudaStream_
 // dst[i] = src[i] rounded to the nearest float, for n values.
 cudaError_t launch_narrow(const double* src, float* dst, long long n, cudaStream_t st);
 
+// dst = the transpose of src converted to D: src holds h rows of w values, dst w rows of
+// h values, dst[x * h + y] = src[y * w + x] (double to float rounds to nearest).
+template <typename S, typename D>
+cudaError_t launch_transpose(const S* src, D* dst, int w, int h, cudaStream_t st);
+
 // One-block kernel whose bounded mbarrier wait runs out after `polls` polls and sets
 // STATUS_TIMEOUT in *status (lbm_selftest_timeout).
 cudaError_t launch_wait_selftest(int* status, long long polls, cudaStream_t st);

@@ -101,6 +101,45 @@ cudaError_t launch_narrow(const double* src, float* dst, long long n, cudaStream
   return cudaGetLastError();
 }
 
+// Transpose through 32 x 32 tiles in shared memory (row-wise reads and writes); block
+// (32, 8), grid (tiles across w, up to 65535 tile rows, looped over the rest of h).
+template <typename S, typename D>
+__global__ void __launch_bounds__(256) transpose_kernel(const S* __restrict__ src,
+                                                        D* __restrict__ dst, int w, int h) {
+  __shared__ D tile[32][33];
+  const int bx = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int by = blockIdx.y * 32; by < h; by += gridDim.y * 32) {
+    for (int k = ty; k < 32; k += 8) {
+      const int x = bx + tx, y = by + k;
+      if (x < w && y < h) tile[k][tx] = (D)src[(long long)y * w + x];
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+      const int x = bx + k, y = by + tx;  // dst row x, column y
+      if (x < w && y < h) dst[(long long)x * h + y] = tile[tx][k];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename S, typename D>
+cudaError_t launch_transpose(const S* src, D* dst, int w, int h, cudaStream_t st) {
+  if (w <= 0 || h <= 0) return cudaSuccess;
+  const int gx = (w + 31) / 32, gy = std::min((h + 31) / 32, 65535);
+  transpose_kernel<S, D><<<dim3(gx, gy), dim3(32, 8), 0, st>>>(src, dst, w, h);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_transpose<float, double>(const float*, double*, int, int,
+                                                     cudaStream_t);
+template cudaError_t launch_transpose<double, double>(const double*, double*, int, int,
+                                                      cudaStream_t);
+template cudaError_t launch_transpose<float, float>(const float*, float*, int, int,
+                                                    cudaStream_t);
+template cudaError_t launch_transpose<double, float>(const double*, float*, int, int,
+                                                     cudaStream_t);
+
 cudaError_t launch_wait_selftest(int* status, long long polls, cudaStream_t st) {
   wait_selftest_kernel<<<1, 32, 0, st>>>(status, polls);
   return cudaGetLastError();

@@ -25,6 +25,8 @@ def debug_live_allocs():
     released (process-wide)."""
     return int(C.lib().lbm_debug_live_allocs())
 _BC = {"periodic": C.LBM_BC_PERIODIC, "walls": C.LBM_BC_WALLS_Y, "walls_y": C.LBM_BC_WALLS_Y}
+_LAYOUT = {"auto": C.LBM_LAYOUT_AUTO, "rows": C.LBM_LAYOUT_ROWS,
+           "transposed": C.LBM_LAYOUT_TRANSPOSED}
 
 
 class LbmError(RuntimeError):
@@ -395,6 +397,7 @@ class Instance:
     rho_l: float = 0.0
     rho_v: float = 0.0
     rho_ref: float = -1.0
+    layout: str = "auto"  # "auto", "rows" (as given) or "transposed" (lbm_instance.layout)
 
     def c(self):
         ci = C.lbm_instance()
@@ -408,6 +411,7 @@ class Instance:
         ci.bc = _BC[self.bc]
         ci.rho_c, ci.rho_l, ci.rho_v = float(self.rho_c), float(self.rho_l), float(self.rho_v)
         ci.rho_ref = float(self.rho_ref)
+        ci.layout = _LAYOUT[self.layout]
         return ci
 
 
@@ -503,6 +507,11 @@ class Batch:
     @property
     def active(self):
         return self._check(self._L.lbm_batch_active(self._h))
+
+    def is_transposed(self, i):
+        """Whether instance i is stored with its axes exchanged
+        (lbm_batch_instance_transposed; Instance.layout)."""
+        return bool(self._check(self._L.lbm_batch_instance_transposed(self._h, int(i))))
 
     def is_active(self, i):
         """Whether instance i is still being stepped (lbm_batch_instance_active)."""

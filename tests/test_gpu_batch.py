@@ -18,13 +18,21 @@ CASES = [
 ]
 
 
-def instance(c):
+def instance(c, layout="auto"):
     from paper_1211_6932_gb300 import Eos, Instance
     rl, rv = pairs.maxwell(c)
     return Instance(nx=c["nx"], ny=c["ny"], eos=Eos(a=c["a"], T=c["T"]), G=c["G"],
                     sigma=c["sigma"], s=c["s"], nu_l=c["nu_l"], nu_v=c["nu_v"],
                     visc_mode=c["visc"], bc="walls" if c["walls"] else "periodic",
-                    rho_c=0.5218 / 4.0, rho_l=rl, rho_v=rv)
+                    rho_c=0.5218 / 4.0, rho_l=rl, rho_v=rv, layout=layout)
+
+
+MIRROR = [0, 2, 1, 4, 3, 5, 8, 7, 6]  # D2Q9 velocity with its components exchanged
+
+
+def exchanged(f):
+    """Populations (9, ny, nx) of a lattice with x and y exchanged: (9, nx, ny)."""
+    return np.stack([f[MIRROR[a]].T for a in range(9)])
 
 
 def start_fields(c, seed):
@@ -50,23 +58,64 @@ def test_fp64_batch_matches_oracle_per_instance():
 
 
 def test_fp32_batch_equals_single_lattices_bitwise():
-    """Same kernel instantiation, so the batch and one-lattice runs are bitwise equal."""
+    """Same kernel instantiation, so the batch and one-lattice runs are bitwise equal.  The
+    64 x 200 instance is stored transposed (64 strip rows of 200 columns instead of 200 of
+    64, at the same cost per strip row): it equals the
+    200 x 64 lattice started from the transposed fields, with x and y exchanged in its
+    populations, moments and momentum."""
     from paper_1211_6932_gb300 import Batch
     b = Batch([instance(c) for c in CASES], precision="fp32")
+    assert [b.is_transposed(i) for i in range(len(CASES))] == [False] * 4 + [True]
     fields = [start_fields(c, 10 + i) for i, c in enumerate(CASES)]
     for i, fl in enumerate(fields):
         b.init_fields(i, *fl)
     b.step(70)
     diags = b.diagnostics()
     for i, c in enumerate(CASES):
-        with pairs.gpu_lattice(c, "fp32") as L:
-            L.init_fields(*fields[i])
+        t = b.is_transposed(i)
+        rho, ux, uy = fields[i]
+        with pairs.gpu_lattice(dict(c, nx=c["ny"], ny=c["nx"]) if t else c, "fp32") as L:
+            L.init_fields(*((rho.T, uy.T, ux.T) if t else (rho, ux, uy)))
             L.step(70)
-            assert np.array_equal(b.get_populations(i), L.get_populations()), i
+            f = L.get_populations()
+            assert np.array_equal(b.get_populations(i), exchanged(f) if t else f), i
             d = L.diagnostics()
             assert diags[i]["mass"] == d["mass"] and diags[i]["max_u"] == d["max_u"], i
+            assert diags[i]["mom_x"] == d["mom_y" if t else "mom_x"], i
+            assert diags[i]["mom_y"] == d["mom_x" if t else "mom_y"], i
             assert diags[i]["step"] == 70
+            for dt in (np.float64, np.float32):
+                m, ml = b.moments(i, dtype=dt), L.moments(dtype=dt)
+                if t:
+                    ml = {"rho": ml["rho"].T, "ux": ml["uy"].T, "uy": ml["ux"].T}
+                for k in ("rho", "ux", "uy"):
+                    assert m[k].dtype == dt and np.array_equal(m[k], ml[k]), (i, k, dt)
     b.close()
+
+
+def test_explicit_layouts():
+    """Instance.layout: "rows" keeps the given orientation, "transposed" exchanges the axes
+    (same physics: within FP32 rounding of the as-given run after a few steps, and the
+    host sees the given orientation); an instance with walls cannot be transposed."""
+    from paper_1211_6932_gb300 import Batch, LbmError
+    c = CASES[0]
+    b = Batch([instance(c, lay) for lay in ("rows", "transposed", "auto")], precision="fp32")
+    assert [b.is_transposed(i) for i in range(3)] == [False, True, False]
+    fl = start_fields(c, 50)
+    for i in range(3):
+        b.init_fields(i, *fl)
+    b.step(5)
+    f0, f1, f2 = (b.get_populations(i) for i in range(3))
+    assert f1.shape == (9, c["ny"], c["nx"])
+    assert np.array_equal(f0, f2)
+    assert pairs.rel_err(f1, f0) <= 2e-5
+    m0, m1 = b.moments(0), b.moments(1)
+    for k in ("rho", "ux", "uy"):
+        assert np.max(np.abs(m1[k] - m0[k])) <= 2e-5 * np.max(np.abs(m0["rho"])), k
+    b.close()
+    with pytest.raises(LbmError) as e:
+        Batch([instance(CASES[1], "transposed")], precision="fp32")
+    assert e.value.code == -1 and "walls" in str(e.value)
 
 
 def test_per_instance_widths_equal_uniform_tiling_bitwise():
@@ -85,9 +134,11 @@ def test_per_instance_widths_equal_uniform_tiling_bitwise():
             b.init_fields(i, *fl)
         b.step(70)
         # uniform 128 threads: strips (400, 257) and full-width strips (the rest, nx <= 256);
-        # per instance: widths 32 (nx 5, full), 64 (70, 64, full), 96 (130 full, 257 strips)
-        # and 128 (220 full, 400 strips)
+        # per instance: widths 32 (nx 5, full), 64 (70, full), 96 (130 full, 257 strips)
+        # and 128 (220 and the transposed 64 x 200 full, 400 strips)
         assert b.launches_per_step == (2 if threads == 0 else 6)
+        # both creation tilings store 64 x 200 transposed (200-column rows) and nothing else
+        assert [b.is_transposed(i) for i in range(len(cs))] == [False] * 4 + [True, False, False]
         pops = [b.get_populations(i) for i in range(len(cs))]
         diags = b.diagnostics()
         b.step(3)

@@ -319,6 +319,34 @@ def test_rotation_by_90_degrees():
     assert np.max(np.abs(a1 - a2)) < 1e-14
 
 
+@pytest.mark.parametrize("visc", ["const", "linear"])
+def test_axis_exchange_on_a_rectangular_lattice(visc):
+    """Exchanging x and y (node (x, y) -> (y, x), velocity e_a -> its mirror image in the
+    diagonal) maps the update of an nx x ny lattice onto that of the ny x nx lattice: the
+    symmetry that lets a batch store an instance transposed.  A reflection, not a
+    rotation: it flips the sign of p_xx, so a wrong sign or a mixed-up rate of the p_xx
+    row of Eqs. 3, 25 fails it where the quarter turn above would not."""
+    nx, ny = 11, 7
+    rho, ux, uy = smooth_field(nx, ny, 10)
+    s = (1.0, 1.1, 1.2, 1.0, 1.3, 1.0, 1.3, 1.25, 1.25)
+    kw = dict(a=A, b=B, R=R, T=0.7 * tc(A), sigma=0.114, s=s)
+    if visc == "linear":
+        rl, rv, _ = thermo.maxwell(A, B, R, 0.7 * tc(A))
+        kw.update(visc_mode=oracle.VISC_LINEAR, nu_l=0.05, nu_v=0.2, rho_l=rl, rho_v=rv)
+    p = oracle.Params(nx=nx, ny=ny, **kw)
+    pt = oracle.Params(nx=ny, ny=nx, **kw)
+    f = oracle.equilibrium(rho, ux, uy)
+    mirror = [0, 2, 1, 4, 3, 5, 8, 7, 6]  # (ex, ey) -> (ey, ex)
+
+    def exchange(g):
+        return np.stack([g[mirror[a]].T for a in range(9)])
+
+    a1 = exchange(oracle.run(p, f, 6))
+    a2 = oracle.run(pt, exchange(f), 6)
+    assert a2.shape == (9, nx, ny)
+    assert np.max(np.abs(a1 - a2)) < 1e-14
+
+
 @pytest.mark.parametrize("mode,rho0", [("const", 0.4), ("step", 0.4), ("step", 0.005),
                                        ("linear", 0.32), ("linear", 0.4)])
 def test_shear_wave_decay_gives_viscosity(mode, rho0):
