@@ -7,8 +7,9 @@
    rho_l, the width and the shift; the two droplets' far vapour densities give the vapour
    law rho_out(R) = rho_v (1 + curvature / R) (lbm_vapour_law).  Rows are encoded with
    lbm_warm_encode.
-2. ``Surrogate``: the network of lbm_mlp.h trained on those rows by full-batch Adam on
-   the GPU; its prediction decoded (lbm_warm_decode) gives the warm-start parameters.
+2. ``Surrogate``: networks of lbm_mlp.h trained on those rows by full-batch Adam on
+   the GPU; their mean prediction decoded (lbm_warm_decode) gives the warm-start
+   parameters.
 3. ``relax``: a droplet field initialised on the device (lbm_init_droplets), stepped,
    with the phase-averaged densities (lbm_phase_stats) recorded at every check.  The
    warm start uses the network's parameters with the vapour curvature law
@@ -112,23 +113,40 @@ def equilibria(draws, nu_l=0.05, tol=1e-6, check_every=100, max_steps=60000, avg
 
 
 class Surrogate:
-    """The warm-start network trained on a Dataset."""
+    """The warm-start networks trained on a Dataset: `members` networks of lbm_mlp.h,
+    initialised from seeds seed, seed + 1, ..., each trained by full-batch Adam on the
+    GPU; a prediction is the mean of their encoded outputs.  One network's prediction at a
+    given point moves by about 1 % in rho_v from one seed (or one rounding-level change of
+    the training rows) to the next; the mean over members takes that scatter out."""
 
-    def __init__(self, seed=0, max_rows=4096, stream=None):
-        self.net = Mlp(wl.mlp_init(seed), max_rows=max_rows, stream=stream)
+    def __init__(self, seed=0, max_rows=4096, stream=None, members=16):
+        self.nets = []
+        try:
+            for k in range(members):
+                self.nets.append(Mlp(wl.mlp_init(seed + k), max_rows=max_rows, stream=stream))
+        except Exception:
+            self.close()
+            raise
         self.losses = None
 
     def close(self):
-        self.net.close()
+        for n in self.nets:
+            n.close()
+        self.nets = []
 
     def fit(self, data: Dataset, steps=4000, lr=3e-3):
-        self.net.fit_scaling(data.x, data.y)
-        self.net.set_data(data.x, data.y)
-        self.losses = self.net.train(steps, lr=lr)
+        """Train every member; returns the members' mean loss before each update."""
+        curves = []
+        for n in self.nets:
+            n.fit_scaling(data.x, data.y)
+            n.set_data(data.x, data.y)
+            curves.append(n.train(steps, lr=lr))
+        self.losses = np.mean(curves, axis=0)
         return self.losses
 
     def predict(self, a, t_over_tc, sigma, visc_ratio) -> WarmParams:
-        y = self.net.predict(features(a, t_over_tc, sigma, visc_ratio)[None, :])[0]
+        x = features(a, t_over_tc, sigma, visc_ratio)[None, :]
+        y = np.mean([n.predict(x)[0] for n in self.nets], axis=0)
         return decode(eos_of(a, t_over_tc), y)
 
 
