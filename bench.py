@@ -155,16 +155,16 @@ def kernel_source_hash(precision="fp32"):
     return h.hexdigest()[:16]
 
 
-def load_traffic(n_nodes, block_size):
-    """DRAM bytes per launch from the committed ncu summary of the step kernel, scaled to
-    n_nodes, or None when the kernel source or its block size has changed since that
-    capture."""
-    path = os.path.join(ROOT, "profiles", "sweep2_kernel_fp32.md")
+def load_traffic(n_nodes, block_size, profile="sweep2_kernel_fp32.md", tile=None):
+    """DRAM bytes per step from a committed ncu summary of the step kernel, scaled to
+    n_nodes, or None when the kernel source, its block size or (for a batch) its tiling
+    has changed since that capture."""
+    path = os.path.join(ROOT, "profiles", profile)
     vals = {}
     try:
         with open(path) as fh:
             for line in fh:
-                for key in ("kernel_hash", "block_size", "dram_bytes_per_node"):
+                for key in ("kernel_hash", "block_size", "tile", "dram_bytes_per_node"):
                     if line.strip().startswith(key + ":"):
                         vals[key] = line.split(":", 1)[1].strip().strip("`")
     except OSError:
@@ -172,6 +172,8 @@ def load_traffic(n_nodes, block_size):
     if vals.get("kernel_hash") != kernel_source_hash() or "dram_bytes_per_node" not in vals:
         return None
     if vals.get("block_size") != str(block_size):
+        return None
+    if tile is not None and vals.get("tile") != tile:
         return None
     return float(vals["dram_bytes_per_node"]) * n_nodes
 
@@ -385,6 +387,8 @@ def run_batch(args):
     peak, peak_kind = load_peak()
     avg = step_ms / K
     achieved = BYTES_PER_LU * n_nodes / (avg * 1e-3) / 1e9
+    traffic = (load_traffic(n_nodes, nt, "sweep2_kernel_batch256.md", "%d,%d,%d" % (nt, vec, rows))
+               if nt > 0 else None)
     if rank == 0:
         line = {"metric": "MLUPS (D2Q9 MRT-pseudopotential step, 256-instance batch, FP32)",
                 "value": n_total * K / (total_ms * 1e-3) / 1e6, "unit": "MLUPS",
@@ -405,7 +409,8 @@ def run_batch(args):
                                            if world > 1 else "one GPU")},
                 "gpu_launches": launches,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
-                             "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                             "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                             "traffic_scope": "per step (every launch of one step)",
                              "peak_source": peak_kind, "avg_step_ms": avg},
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
