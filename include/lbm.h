@@ -181,8 +181,9 @@ int lbm_get_populations(lbm_handle* h, double* f);
  */
 int lbm_step(lbm_handle* h, int n);
 
-/* Wait for queued work; LBM_EUNSTABLE if any step met a non-finite or non-positive
- * density since the last init. */
+/* Wait for queued work, including asynchronous host transfers; LBM_EUNSTABLE if any
+ * step met a non-finite or non-positive density since the last init, LBM_EINVAL if the
+ * last (asynchronous) initialisation had invalid fields. */
 int lbm_sync(lbm_handle* h);
 
 /*
@@ -222,6 +223,30 @@ int lbm_moments_f32(lbm_handle* h, float* rho, float* ux, float* uy);
  * (double for LBM_FP64, float for LBM_FP32_DEV); any pointer may be NULL.  Queued on the
  * handle's stream, not synchronised. */
 int lbm_moments_device(lbm_handle* h, void* rho, void* ux, void* uy);
+
+/*
+ * Asynchronous host transfers (no counterpart in the paper), for a host loop that
+ * overlaps its uploads and read-backs with stepping.  The initialisation and the moments
+ * pass stay in order with the steps on the handle's stream; only the host copies run on
+ * two copy streams of the handle, so an upload or a read-back proceeds while earlier or
+ * later steps run.  Host arrays are (ny, nx) values of the storage type (float for
+ * LBM_FP32_DEV, double for LBM_FP64) and should be page-locked (cudaHostAlloc,
+ * cudaHostRegister); with pageable arrays the results are the same but the copies do not
+ * overlap.  Neither call waits: the caller keeps an uploaded array unchanged, and reads a
+ * read-back array, only after the next lbm_sync, which waits for the copy streams too.
+ *   lbm_init_fields_async: as lbm_init_fields (FP32_DEV: as lbm_init_fields_f32); ux, uy
+ *     may be NULL.  The upload starts once the previous asynchronous initialisation has
+ *     consumed the handle's staging buffer.  A density outside (0, 4/b), a negative psi^2
+ *     or a non-finite velocity is reported as LBM_EINVAL by the next lbm_sync (or any
+ *     synchronous call that reports status) unless a later initialisation replaced the
+ *     state first.  The result equals lbm_init_fields(_f32) bit for bit.
+ *   lbm_moments_async: as lbm_moments (FP32_DEV: as lbm_moments_f32) of the state after
+ *     every step queued before the call, for the non-NULL outputs.  The next read-back,
+ *     synchronous or not, waits until this one has left the handle's field buffers.
+ * LBM_EINVAL for a NULL handle or rho.
+ */
+int lbm_init_fields_async(lbm_handle* h, const void* rho, const void* ux, const void* uy);
+int lbm_moments_async(lbm_handle* h, void* rho, void* ux, void* uy);
 
 /* Global diagnostics of the current state (see lbm_diag).  Each call also stores rho as
  * the reference of the next call's dinf.  Synchronous. */

@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <initializer_list>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -65,6 +66,13 @@ struct Batch {
   double* staging_t = nullptr;  // 3 x (largest transposed instance) doubles
   size_t staging_t_elems = 0;
   int* d_flag = nullptr;      // one int for the initialisation's validity check
+  // Asynchronous host transfers (lbm_init_fields_async, lbm_moments_async): copy streams
+  // and the events that order them with the handle's stream.
+  cudaStream_t up_stream = nullptr, down_stream = nullptr;
+  cudaEvent_t ev_uploaded = nullptr;      // up_stream: the last upload is on the device
+  cudaEvent_t ev_staging_free = nullptr;  // stream: the last initialisation read its staging
+  cudaEvent_t ev_fields_ready = nullptr;  // stream: the last asynchronous moments pass ended
+  cudaEvent_t ev_fields_free = nullptr;   // down_stream: its read-back left the fields
   double* d_part_sum = nullptr;
   float* d_part_max = nullptr;
   int* d_part_bad = nullptr;
@@ -268,6 +276,8 @@ void destroy_batch(Batch* b) {
   if (!b) return;
   DeviceGuard g(b);
   if (b->stream) cudaStreamSynchronize(b->stream);
+  for (cudaStream_t s : {b->up_stream, b->down_stream})  // copies may still use buffers
+    if (s) cudaStreamSynchronize(s);
   drop_graphs(b);
   free_dev(b->d_inst);
   free_dev(b->d_items);
@@ -292,6 +302,10 @@ void destroy_batch(Batch* b) {
   for (auto& ev : b->grp_join)
     if (ev) cudaEventDestroy(ev);
   if (b->grp_fork) cudaEventDestroy(b->grp_fork);
+  for (cudaStream_t s : {b->up_stream, b->down_stream})
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t ev : {b->ev_uploaded, b->ev_staging_free, b->ev_fields_ready, b->ev_fields_free})
+    if (ev) cudaEventDestroy(ev);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   b->stream = nullptr;
 }
@@ -748,8 +762,14 @@ int do_steps(Batch* b, long long n) {
 
 int sync_status(Batch* b) {
   CK(b, cudaStreamSynchronize(b->stream));
+  if (b->up_stream) CK(b, cudaStreamSynchronize(b->up_stream));
+  if (b->down_stream) CK(b, cudaStreamSynchronize(b->down_stream));
   int st = 0;
   CK(b, cudaMemcpy(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st & lbm::STATUS_BADINIT)
+    return set_err(b->err, LBM_EINVAL,
+                   "the last initialisation had nodes with a density outside (0, 4/b), a "
+                   "negative psi^2 (Eq. 24) or a non-finite velocity");
   if (st & lbm::STATUS_BOUNDS)
     return set_err(b->err, LBM_ECORRUPT,
                    "a kernel index check failed (bounds-check build): an access outside its "
@@ -1013,6 +1033,8 @@ int ensure_fields(Batch* b) {
 // (or, with direct pointers, at offset 0 of the caller's arrays).
 int moments_device(Batch* b, int i, void* rho, void* ux, void* uy, bool caller_ptrs) {
   const int lo = b->item_begin[i], hi = b->item_begin[i + 1];
+  if (b->ev_fields_free && !caller_ptrs)  // an asynchronous read-back may still read them
+    CK(b, cudaStreamWaitEvent(b->stream, b->ev_fields_free, 0));
   const long long shift = caller_ptrs ? b->inst[i].dense_off : 0;
   if (b->fp64) {
     MomArgs<double> mo{};
@@ -1126,6 +1148,88 @@ int moments_host_f32(Batch* b, int i, float* rho, float* ux, float* uy) {
     CK(b, cudaMemcpyAsync(outs[k], f, N * sizeof(float), cudaMemcpyDeviceToHost, b->stream));
   }
   CK(b, cudaStreamSynchronize(b->stream));
+  return LBM_OK;
+}
+
+// Copy streams and events of the asynchronous host transfers (created on first use).
+int ensure_async(Batch* b) {
+  for (cudaStream_t* s : {&b->up_stream, &b->down_stream})
+    if (!*s) CK(b, cudaStreamCreateWithFlags(s, cudaStreamNonBlocking));
+  for (cudaEvent_t* ev : {&b->ev_uploaded, &b->ev_staging_free, &b->ev_fields_ready,
+                          &b->ev_fields_free})
+    if (!*ev) CK(b, cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+  return LBM_OK;
+}
+
+// Instance 0 initialised from host fields of the storage type, uploaded on up_stream; the
+// initialisation itself (FP32: widening, then the double path of init_instance) is queued
+// on the handle's stream, and its validity check sets STATUS_BADINIT.
+int init_async(Batch* b, const void* rho, const void* ux, const void* uy) {
+  if (!rho) return set_err(b->err, LBM_EINVAL, "rho must not be NULL");
+  int rc = ensure_async(b);
+  if (rc == LBM_OK) rc = ensure_flag(b);
+  if (rc == LBM_OK) rc = b->fp64 ? ensure_staging(b) : ensure_staging32(b);
+  if (rc) return rc;
+  const InstParams& P = b->inst[0];
+  const size_t N = (size_t)P.nx * P.ny;
+  const void* in[3] = {rho, ux, uy};
+  const double* dev[3] = {nullptr, nullptr, nullptr};
+  CK(b, cudaStreamWaitEvent(b->up_stream, b->ev_staging_free, 0));
+  for (int k = 0; k < 3; ++k) {
+    if (!in[k]) continue;
+    void* dst = b->fp64 ? (void*)(b->staging + k * b->staging_elems)
+                        : (void*)(b->staging32 + k * b->staging_elems);
+    CK(b, cudaMemcpyAsync(dst, in[k], N * b->esz, cudaMemcpyHostToDevice, b->up_stream));
+  }
+  CK(b, cudaEventRecord(b->ev_uploaded, b->up_stream));
+  CK(b, cudaStreamWaitEvent(b->stream, b->ev_uploaded, 0));
+  for (int k = 0; k < 3; ++k) {
+    if (!in[k]) continue;
+    double* d = b->staging + k * b->staging_elems;
+    if (!b->fp64)
+      CK(b, lbm::launch_widen(b->staging32 + k * b->staging_elems, d, (long long)N, b->stream));
+    dev[k] = d;
+  }
+  CK(b, cudaMemsetAsync(b->d_flag, 0, sizeof(int), b->stream));
+  CK(b, cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream));
+  cudaError_t e =
+      b->fp64 ? lbm::launch_init_eq<double>(dev[0], dev[1], dev[2], (double*)b->slab[b->cur], P,
+                                            b->d_flag, b->stream)
+              : lbm::launch_init_eq<float>(dev[0], dev[1], dev[2], (float*)b->slab[b->cur], P,
+                                           b->d_flag, b->stream);
+  if (e == cudaSuccess)
+    e = b->fp64 ? lbm::launch_fill_ghosts<double>((double*)b->slab[b->cur], P, b->stream)
+                : lbm::launch_fill_ghosts<float>((float*)b->slab[b->cur], P, b->stream);
+  if (e == cudaSuccess)
+    e = lbm::launch_flag_status(b->d_flag, b->d_status, lbm::STATUS_BADINIT, b->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev_staging_free, b->stream);
+  if (e != cudaSuccess)
+    return set_err(b->err, LBM_ECUDA, "initialisation failed: %s", cudaGetErrorString(e));
+  b->steps[0] = 0;
+  b->dinf_valid[0] = 0;
+  return LBM_OK;
+}
+
+// Moments of instance 0 into the handle's fields on its stream, copied to host arrays of
+// the storage type on down_stream.
+int moments_async(Batch* b, void* rho, void* ux, void* uy) {
+  if (!rho && !ux && !uy) return LBM_OK;
+  int rc = ensure_async(b);
+  if (rc == LBM_OK) rc = ensure_fields(b);
+  if (rc) return rc;
+  void* outs[3] = {rho, ux, uy};
+  rc = moments_device(b, 0, rho ? b->fields[0] : nullptr, ux ? b->fields[1] : nullptr,
+                      uy ? b->fields[2] : nullptr, false);  // waits for the last read-back
+  if (rc) return rc;
+  const InstParams& P = b->inst[0];
+  const size_t N = (size_t)P.nx * P.ny;
+  CK(b, cudaEventRecord(b->ev_fields_ready, b->stream));
+  CK(b, cudaStreamWaitEvent(b->down_stream, b->ev_fields_ready, 0));
+  for (int k = 0; k < 3; ++k)
+    if (outs[k])
+      CK(b, cudaMemcpyAsync(outs[k], (const char*)b->fields[k] + P.dense_off * b->esz,
+                            N * b->esz, cudaMemcpyDeviceToHost, b->down_stream));
+  CK(b, cudaEventRecord(b->ev_fields_free, b->down_stream));
   return LBM_OK;
 }
 
@@ -1595,6 +1699,21 @@ int lbm_moments(lbm_handle* h, double* rho, double* ux, double* uy) {
   int rc = moments_host(&h->b, 0, rho, ux, uy);
   if (rc) return rc;
   return sync_status(&h->b);
+}
+
+int lbm_init_fields_async(lbm_handle* h, const void* rho, const void* ux, const void* uy) {
+  Range r_("lbm_init_fields_async");
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  return init_async(&h->b, rho, ux, uy);
+}
+
+int lbm_moments_async(lbm_handle* h, void* rho, void* ux, void* uy) {
+  Range r_("lbm_moments_async");
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  if (!rho) return set_err(h->b.err, LBM_EINVAL, "rho must not be NULL");
+  return moments_async(&h->b, rho, ux, uy);
 }
 
 int lbm_moments_device(lbm_handle* h, void* rho, void* ux, void* uy) {

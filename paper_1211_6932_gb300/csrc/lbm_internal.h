@@ -60,6 +60,12 @@ template <typename S>
 cudaError_t launch_pressure(const S* rho, const InstParams& P, double sigma, double* pxx,
                             double* pyy, double* pxy, cudaStream_t st);
 
+// Status bit of an asynchronous initialisation whose fields failed the validity check
+// (host-side status only; distinct from the kernels' STATUS_* bits).
+constexpr int STATUS_BADINIT = 1 << 8;
+// *status |= bit if *flag != 0 (one thread).
+cudaError_t launch_flag_status(const int* flag, int* status, int bit, cudaStream_t st);
+
 // dst[i] = (double)src[i] for n values.
 cudaError_t launch_widen(const float* src, double* dst, long long n, cudaStream_t st);
 // dst[i] = src[i] rounded to the nearest float, for n values.

@@ -140,6 +140,16 @@ template cudaError_t launch_transpose<float, float>(const float*, float*, int, i
 template cudaError_t launch_transpose<double, float>(const double*, float*, int, int,
                                                      cudaStream_t);
 
+__global__ void flag_status_kernel(const int* __restrict__ flag, int* __restrict__ status,
+                                   int bit) {
+  if (*flag != 0) atomicOr(status, bit);
+}
+
+cudaError_t launch_flag_status(const int* flag, int* status, int bit, cudaStream_t st) {
+  flag_status_kernel<<<1, 1, 0, st>>>(flag, status, bit);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_wait_selftest(int* status, long long polls, cudaStream_t st) {
   wait_selftest_kernel<<<1, 32, 0, st>>>(status, polls);
   return cudaGetLastError();

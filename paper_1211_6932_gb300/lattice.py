@@ -163,6 +163,7 @@ class Lattice:
             raise LbmError(rc, self._L.lbm_last_error(None).decode())
         self._h = h
         self.stream_keepalive = stream
+        self._in_flight = []  # host arrays of asynchronous transfers, until the next sync
 
     # -- helpers -----------------------------------------------------------------------
     def _check(self, rc):
@@ -226,7 +227,41 @@ class Lattice:
         self._check(self._L.lbm_step(self._h, int(n)))
 
     def sync(self):
-        self._check(self._L.lbm_sync(self._h))
+        """lbm_sync: wait for the queued steps and asynchronous transfers."""
+        try:
+            self._check(self._L.lbm_sync(self._h))
+        finally:
+            self._in_flight.clear()
+
+    def _async_array(self, a, writable):
+        """A host array for an asynchronous transfer: (ny, nx), C-contiguous, of the
+        storage type (float32 for FP32, float64 for FP64), used in place (no copy, so that
+        the caller's, possibly page-locked, buffer is the one transferred)."""
+        if a is None:
+            return None
+        dt = np.float64 if self.precision == "fp64" else np.float32
+        if not isinstance(a, np.ndarray) or a.dtype != dt or a.shape != self.shape or \
+                not a.flags["C_CONTIGUOUS"] or (writable and not a.flags["WRITEABLE"]):
+            raise ValueError("asynchronous transfers take C-contiguous %s arrays of shape %s"
+                             % (np.dtype(dt).name, self.shape))
+        return a
+
+    def init_fields_async(self, rho, ux=None, uy=None):
+        """lbm_init_fields_async: returns at once; the arrays (see _async_array; page-locked,
+        e.g. torch's pin_memory().numpy(), for the copy to overlap) stay referenced, and
+        must stay unchanged, until the next sync(), which reports invalid fields."""
+        arrs = [self._async_array(a, False) for a in (rho, ux, uy)]
+        ptr = lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+        self._in_flight.extend(a for a in arrs if a is not None)
+        self._check(self._L.lbm_init_fields_async(self._h, *[ptr(a) for a in arrs]))
+
+    def moments_async(self, rho, ux=None, uy=None):
+        """lbm_moments_async into the given arrays (see _async_array) of the state after the
+        steps queued so far; they hold the fields after the next sync()."""
+        arrs = [self._async_array(a, True) for a in (rho, ux, uy)]
+        ptr = lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data)  # noqa: E731
+        self._in_flight.extend(a for a in arrs if a is not None)
+        self._check(self._L.lbm_moments_async(self._h, *[ptr(a) for a in arrs]))
 
     def pressure_tensor(self, include_sigma=False):
         """(pxx, pyy, pxy) of Eq. 18 as (ny, nx) arrays (lbm_pressure_tensor)."""

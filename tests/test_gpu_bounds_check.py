@@ -4,8 +4,8 @@ against its buffer, and a failed check is reported as LBM_ECORRUPT.  The library
 in that variant and a child process (LBM_LIBRARY=check) runs both precisions and every
 kernel family over degenerate, odd, even and ragged widths, walls, graph replays and
 single launches, the moments and diagnostics passes (including the allocation-free
-diagnostics, whose partial sums sit in the library's fixed array), and a batch under
-per-instance widths: every check must pass."""
+diagnostics, whose partial sums sit in the library's fixed array), and a batch (with a
+transposed instance) under uniform and per-instance widths: every check must pass."""
 import os
 import subprocess
 import sys
@@ -50,17 +50,23 @@ SCRIPT = textwrap.dedent('''
                     L.sync()
                     L.check_guards()
                     n += 1
+    # the batch adds a 40 x 300 instance, stored transposed (two strips of its 300-column
+    # rows), and reads every instance back through each host path
+    bsizes = sizes + [(40, 300, False)]
     insts = [Instance(nx=nx, ny=ny, eos=eos, sigma=0.114, s=s,
                       bc="walls" if w else "periodic", rho_l=rl, rho_v=rv)
-             for nx, ny, w in sizes]
+             for nx, ny, w in bsizes]
     for t in (0, TILE_PER_INSTANCE):
         b = Batch(insts, precision="fp32", tile_threads=t)
-        for i, (nx, ny, w) in enumerate(sizes):
+        assert b.is_transposed(len(sizes)) and not any(map(b.is_transposed, range(len(sizes))))
+        for i, (nx, ny, w) in enumerate(bsizes):
             b.init_fields(i, wl.droplet(nx, ny, rl, rv, 0.3 * min(nx, ny), 4.0))
         b.step(67)
         b.diagnostics()
-        for i in range(len(sizes)):
+        for i in range(len(bsizes)):
             b.moments(i)
+            b.moments(i, dtype=np.float32)
+            b.get_populations(i)
         b.check_guards()
         b.close()
         n += 1

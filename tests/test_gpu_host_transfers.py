@@ -1,6 +1,7 @@
 """Float host transfers (lbm_init_fields_f32, lbm_moments_f32 and their batch forms) give
 exactly the double-transfer results: a float field is the same start as its widened
-copy, and float moments are the double moments rounded to nearest."""
+copy, and float moments are the double moments rounded to nearest.  Asynchronous
+transfers (lbm_init_fields_async, lbm_moments_async) give the synchronous results."""
 import numpy as np
 import pytest
 
@@ -59,3 +60,70 @@ def test_batch_float_transfers():
     finally:
         b32.close()
         b64.close()
+
+
+def _pinned(a):
+    torch = pytest.importorskip("torch")
+    return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_async_transfers_equal_synchronous_ones(prec):
+    """Three cycles of upload / 70 steps / read-back queued without waiting (page-locked
+    buffers; each upload reuses the staging buffer the previous initialisation read) give
+    the synchronous calls' fields bit for bit."""
+    from paper_1211_6932_gb300 import workloads as wl
+    dt = np.float32 if prec == "fp32" else np.float64
+    c = pairs.case(75, 52, tr=0.7, sigma=0.114)
+    rl, rv = pairs.maxwell(c)
+    rng = np.random.default_rng(5)
+    starts = [(_pinned(wl.droplet(75, 52, rl, rv, r, 4.0).astype(dt)),
+               _pinned((0.01 * rng.uniform(-1, 1, (52, 75))).astype(dt))) for r in (12, 15, 18)]
+    outs = [[_pinned(np.zeros((52, 75), dt)) for _ in range(3)] for _ in starts]
+    with pairs.gpu_lattice(c, prec) as A:
+        for (rho, ux), o in zip(starts, outs):
+            A.init_fields_async(rho, ux)
+            A.step(70)
+            A.moments_async(*o)
+        A.sync()
+        A.check_guards()
+    with pairs.gpu_lattice(c, prec) as B:
+        for (rho, ux), o in zip(starts, outs):
+            B.init_fields(rho, ux)
+            B.step(70)
+            m = B.moments(dtype=dt)
+            for k, a in zip(("rho", "ux", "uy"), o):
+                assert np.array_equal(a, m[k]), k
+
+
+def test_async_read_back_and_invalid_upload():
+    """A synchronous read-back queued after an asynchronous one waits for it (each gets the
+    state of its own place in the queue); an invalid asynchronous upload is reported by
+    the next sync unless a later upload replaced it."""
+    from paper_1211_6932_gb300 import LbmError
+    from paper_1211_6932_gb300 import workloads as wl
+    c = pairs.case(75, 52, tr=0.7, sigma=0.114)
+    rl, rv = pairs.maxwell(c)
+    good = _pinned(wl.droplet(75, 52, rl, rv, 15.0, 4.0).astype(np.float32))
+    bad = _pinned(np.full((52, 75), -1.0, np.float32))
+    out = _pinned(np.zeros((52, 75), np.float32))
+    with pairs.gpu_lattice(c, "fp32") as L:
+        L.init_fields(good)
+        L.step(10)
+        before = L.moments(dtype=np.float32)["rho"]
+        L.moments_async(out)
+        L.step(3)
+        after = L.moments(dtype=np.float32)["rho"]
+        L.sync()
+        assert np.array_equal(out, before) and not np.array_equal(after, before)
+        L.init_fields_async(bad)
+        with pytest.raises(LbmError) as e:
+            L.sync()
+        assert e.value.code == -1
+        L.init_fields_async(bad)
+        L.init_fields_async(good)
+        L.sync()
+        L.step(5)
+        L.sync()
+        with pytest.raises(ValueError):
+            L.init_fields_async(good.astype(np.float64))
