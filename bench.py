@@ -155,6 +155,17 @@ def kernel_source_hash(precision="fp32"):
     return h.hexdigest()[:16]
 
 
+GRAPH_STEPS = 64  # steps per CUDA-graph replay of the library (one persistent launch each)
+
+
+def step_launches(n, groups, persistent):
+    """Step-kernel launches of one lbm_step(n) / lbm_batch_step(n): one per step and launch
+    group, or, stepping persistently, one per run of up to GRAPH_STEPS steps."""
+    if persistent:
+        return groups * (n // GRAPH_STEPS + (1 if n % GRAPH_STEPS else 0))
+    return groups * n
+
+
 def load_traffic(n_nodes, block_size, profile="sweep2_kernel_fp32.md", tile=None):
     """DRAM bytes per step from a committed ncu summary of the step kernel, scaled to
     n_nodes, or None when the kernel source, its block size or (for a batch) its tiling
@@ -373,7 +384,7 @@ def run_batch(args):
         e1.record(stream)
         e1.synchronize()
         step_ms += e0.elapsed_time(e1)
-        launches += n * per_step
+        launches += step_launches(n, per_step, b.persistent)
         if n == DIAG_EVERY:
             b.diagnostics()
             launches += diag_launches
@@ -467,11 +478,12 @@ def run_gpu(args):
     launches = 0
     diag_last = None
     t_all0.record(stream)
+    persistent = L.persistent
     for i, n in enumerate(chunks):
         ev_step[i][0].record(stream)
         L.step(n)
         ev_step[i][1].record(stream)
-        launches += n
+        launches += step_launches(n, 1, persistent)
         if n == DIAG_EVERY:
             ev_diag[i][0].record(stream)
             diag_last = L.diagnostics()
@@ -530,11 +542,16 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_kind,
-                         "kernel": ("sweep2_kernel<%d,STEP>" % nt if vec == 2
+                         "kernel": (("sweep2_persist_kernel<%d>" if persistent
+                                     else "sweep2_kernel<%d,STEP>") % nt if vec == 2
                                     else "sweep_kernel<%s,%d,STEP>"
                                     % ("float" if PREC == "fp32" else "double", nt)),
-                         "algorithmic_bytes_per_launch": bytes_lu * n_nodes,
-                         "avg_launch_ms": avg_launch_ms},
+                         "persistent": persistent,
+                         # per time step: stepping persistently, one launch runs up to
+                         # GRAPH_STEPS steps (bytes and duration scale together)
+                         "algorithmic_bytes_per_step": bytes_lu * n_nodes,
+                         "avg_step_ms": avg_launch_ms,
+                         "steps_per_launch": GRAPH_STEPS if persistent else 1},
             "e2e": {"value": e2e_value, "unit": "MLUPS",
                     "h2d_bytes_per_step": n_nodes * rho_h.element_size(),
                     "d2h_bytes_per_step": n_nodes * out_h.element_size(),

@@ -181,6 +181,26 @@ int lbm_get_populations(lbm_handle* h, double* f);
  */
 int lbm_step(lbm_handle* h, int n);
 
+/*
+ * Persistent stepping (no counterpart in the paper).  With the FP32 pair kernel (tile_vec
+ * 2), a run of up to 64 steps is one launch per launch group: resident CTAs take the
+ * (step, chunk row, strip) work items in order from a queue, and an item waits (bounded;
+ * LBM_ETIMEOUT if it runs out) only until the chunk rows whose previous step it reads, or
+ * whose previous-step reads its stores would overwrite, are complete, so the CTAs of step
+ * t + 1 start while step t finishes instead of the GPU draining between launches.  Results
+ * equal the per-step launches bit for bit.  It is used with one launch group (one kernel
+ * width and kind of strip), at least two waves of work items per step (with fewer, the
+ * first items of a step would wait on the last ones of the step before), when every work
+ * item depends on at most four chunk rows (chunks of two rows or more), and unless the
+ * environment sets LBM_PERSISTENT=0 when the work lists are built (creation, tiling
+ * change, retirement); LBM_PERSISTENT=2 drops the two-wave condition (for tests).  With it
+ * the default chunk height aims at about three waves of CTAs instead of six (taller
+ * chunks, fewer halo rows: 32 rows at 4096^2).
+ * lbm_persistent / lbm_batch_persistent: 1 if steps currently run that way, 0 if not,
+ * LBM_EINVAL for a NULL handle.
+ */
+int lbm_persistent(const lbm_handle* h);
+
 /* Wait for queued work, including asynchronous host transfers; LBM_EUNSTABLE if any
  * step met a non-finite or non-positive density since the last init, LBM_EINVAL if the
  * last (asynchronous) initialisation had invalid fields. */
@@ -451,6 +471,8 @@ int lbm_batch_get_tiling(const lbm_batch* b, int* threads, int* vec, int* rows);
  * (full-width strips for instances of at most 2 * threads columns, strips for wider
  * ones; pair kernel only). */
 int lbm_batch_launches_per_step(const lbm_batch* b);
+/* Persistent stepping of a batch (see lbm_persistent). */
+int lbm_batch_persistent(const lbm_batch* b);
 
 /*
  * Integrity checks and fault injection (for tests of the library and of its callers).

@@ -113,6 +113,8 @@ SIGNATURES = {
     "lbm_batch_instance_active": (c_int, [c_void_p, c_int]),
     "lbm_batch_instance_transposed": (c_int, [c_void_p, c_int]),
     "lbm_init_fields_async": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lbm_persistent": (c_int, [c_void_p]),
+    "lbm_batch_persistent": (c_int, [c_void_p]),
     "lbm_moments_async": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_batch_retire": (c_int, [c_void_p, c_int]),
     "lbm_batch_retire_nonfinite": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_int)]),

@@ -29,6 +29,7 @@
 
 using lbm::InstParams;
 using lbm::MomArgs;
+using lbm::ItemLink;
 using lbm::WorkItem;
 
 namespace {
@@ -49,6 +50,15 @@ struct Batch {
   std::vector<WorkItem> items;  // active instances only
   WorkItem* d_items = nullptr;
   int n_items = 0, cap_items = 0;
+  // Persistent stepping (FP32 pair kernel, sweep2_persist_kernel): per launch group g the
+  // even and odd steps' work lists and their dependency links (2 n_g entries each from
+  // 2 grp_begin[g]), the queue counter at d_sync[grp_sync[g]] followed by the group's chunk
+  // counters, and the group's grid.
+  bool persist = false;
+  WorkItem* d_items2 = nullptr;
+  ItemLink* d_links2 = nullptr;
+  int* d_sync = nullptr;
+  int cap_items2 = 0, cap_sync = 0;
   std::vector<WorkItem> all_items;  // every instance, for diagnostics
   WorkItem* d_all_items = nullptr;
   int n_all = 0, cap_all = 0;
@@ -93,6 +103,8 @@ struct Batch {
   int grp_nt[kMaxGroups] = {};
   int grp_full[kMaxGroups] = {};
   int grp_begin[kMaxGroups + 1] = {};
+  int grp_sync[kMaxGroups + 1] = {};  // persistent stepping: group g's counters
+  int grp_grid[kMaxGroups] = {};      // persistent stepping: group g's CTAs
   cudaStream_t grp_stream[kMaxGroups - 1] = {};  // graph branches
   cudaEvent_t grp_fork = nullptr, grp_join[kMaxGroups - 1] = {};
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -281,6 +293,9 @@ void destroy_batch(Batch* b) {
   drop_graphs(b);
   free_dev(b->d_inst);
   free_dev(b->d_items);
+  free_dev(b->d_items2);
+  free_dev(b->d_links2);
+  free_dev(b->d_sync);
   free_dev(b->d_all_items);
   free_dev(b->d_item_begin);
   b->slab[0] = b->slab[1] = nullptr;  // guarded buffers
@@ -369,6 +384,55 @@ bool transposed_layout(const lbm_instance& in, int nt, int vec) {
 // Step-kernel threads per CTA of instance i under the current tiling.
 int step_nt(const Batch* b, int i) { return per_instance(b) ? b->inst_nt[i] : b->nt; }
 
+// LBM_PERSISTENT in the environment: 0 never steps persistently, 2 whenever the
+// dependency rule allows (even with few items per step; for tests), anything else (the
+// default) when there are enough items per step.
+int persist_env() {
+  const char* env = std::getenv("LBM_PERSISTENT");
+  return env ? std::atoi(env) : 1;
+}
+
+// Whether persistent stepping may be used at all: FP32 pair tilings, unless switched off.
+bool persist_allowed(const Batch* b) { return !b->fp64 && b->vec == 2 && persist_env() != 0; }
+
+// Number of (kernel width, kind of strip) launch groups the active instances fall into.
+int launch_kinds(const Batch* b) {
+  bool seen[Batch::kMaxWidths + 1][2] = {};
+  int kinds = 0;
+  for (int i = 0; i < b->n_inst; ++i)
+    if (b->active[i]) {
+      const int nt = step_nt(b, i);
+      int w = Batch::kMaxWidths;
+      for (int g = 0; g < Batch::kMaxWidths; ++g)
+        if (kPairThreads[g] == nt) w = g;
+      const int full = lbm::full_width(b->inst[i].nx, nt, b->vec) ? 1 : 0;
+      if (!seen[w][full]) {
+        seen[w][full] = true;
+        ++kinds;
+      }
+    }
+  return kinds;
+}
+
+// Whether chunks of `rows` rows give the active instances at least two waves of step items
+// (resident persistent CTAs of their width): with fewer, a step's first items would wait
+// on the previous step's last ones, since the odd steps' lists start only half a step
+// further on (the 1024^2 ellipse, 640 items per step against 760 resident CTAs, stepped
+// at 48 against 53 GLUPS persistently).
+bool persist_items_ok(const Batch* b, int rows) {
+  long long items = 0;
+  int nt = 0, full = 0;
+  for (int i = 0; i < b->n_inst; ++i)
+    if (b->active[i]) {
+      nt = step_nt(b, i);
+      full = lbm::full_width(b->inst[i].nx, nt, b->vec) ? 1 : 0;
+      items += (long long)lbm::strips_for(b->inst[i].nx, nt, b->vec) *
+               ((b->inst[i].ny + rows - 1) / rows);
+    }
+  if (nt == 0) return false;
+  return items >= 2LL * lbm::persist_occupancy(nt, full) * std::max(b->sms, 1);
+}
+
 // Rows per CTA sweep: about six waves of resident CTAs (measured best on 4096^2: fewer
 // rows cost halo re-reads and row-loop start-up, more rows leave SMs idle in the tail),
 // clamped to [8, 64] for FP32 and [1, 64] for FP64, whose rows are FP64-pipe bound: on a
@@ -377,6 +441,7 @@ int step_nt(const Batch* b, int i) { return per_instance(b) ? b->inst_nt[i] : b-
 // widths each strip row counts as 1 / (resident CTAs of its width) of an SM.
 int default_rows(const Batch* b) {
   double sm_rows = 0.0;
+  const int kinds = launch_kinds(b);
   for (int i = 0; i < b->n_inst; ++i)
     if (b->active[i]) {
       const int nt = step_nt(b, i);
@@ -385,9 +450,19 @@ int default_rows(const Batch* b) {
       sm_rows += (double)lbm::strips_for(b->inst[i].nx, nt, b->vec) * b->inst[i].ny /
                  std::max(occ, 1);
     }
-  const double target = (double)std::max(b->sms, 1) * 6.0;
-  const long long r = (long long)std::ceil(sm_rows / target);
-  return (int)std::min<long long>(64, std::max<long long>(b->fp64 ? 1 : 8, r));
+  const long long lo = b->fp64 ? 1 : 8;
+  auto clamp = [&](long long r) { return (int)std::min<long long>(64, std::max(lo, r)); };
+  const int r6 = clamp((long long)std::ceil(sm_rows / ((double)std::max(b->sms, 1) * 6.0)));
+  // Persistent stepping has no drain between steps, so fewer, taller chunks (fewer halo
+  // rows) win: about three waves, rounded up to a multiple of four rows (32 rows at 4096^2,
+  // 87.5 against 84.0 GLUPS at 16 rows per step), if that still gives the two waves of
+  // items per step that persistent stepping needs (persist_items_ok).
+  if (persist_allowed(b) && kinds == 1) {
+    const long long r3 = (long long)std::ceil(sm_rows / ((double)std::max(b->sms, 1) * 3.0));
+    const int rp = clamp((r3 + 3) / 4 * 4);
+    if (persist_items_ok(b, rp)) return rp;
+  }
+  return r6;
 }
 
 // Work items of instance i: strips of W owned columns by chunks of `rows` rows.
@@ -442,6 +517,101 @@ void make_all_items(const Batch* b, std::vector<WorkItem>& out, std::vector<int>
   }
 }
 
+// Work lists of the persistent step kernel (sweep2_persist_kernel) for the current step
+// items: per launch group the even steps' list (the step items in their order), the odd
+// steps' (each instance's chunk rows from the middle one on, wrapping), the dependency
+// links, the counters and the grid (the group's share, by work, of the resident CTAs of its
+// width).  Used for FP32 pair tilings with one launch group (several groups, which run as
+// parallel graph branches of per-step launches, measured faster that way: 67.3 against
+// 58.9 GLUPS on the 256-instance batch) and at least two waves of items per step
+// (persist_items_ok), unless switched off (persist_env), and only when every item depends
+// on at most four chunks (chunks of two rows or more, but for a short last one); otherwise
+// steps are one launch per group each.
+int build_persist(Batch* b) {
+  b->persist = false;
+  if (!persist_allowed(b) || b->n_items == 0 || b->n_groups != 1 ||
+      (persist_env() != 2 && !persist_items_ok(b, b->rows)))
+    return LBM_OK;
+  const int n = b->n_items;
+  std::vector<WorkItem> items2(2 * (size_t)n);
+  std::vector<ItemLink> links2(2 * (size_t)n);
+  std::vector<double> work(b->n_groups, 0.0);
+  int sync = 0;
+  for (int g = 0; g < b->n_groups; ++g) {
+    const int lo = b->grp_begin[g], hi = b->grp_begin[g + 1], ng = hi - lo;
+    b->grp_sync[g] = sync++;  // the queue counter, then the group's chunk counters
+    int chunk0 = 0;           // local id of the first chunk of the current instance
+    for (int k = lo; k < hi;) {
+      // an instance's items are consecutive: chunk rows in order, each `strips` items
+      const int i = b->items[k].inst;
+      const InstParams& P = b->inst[i];
+      int e = k, strips = 0;
+      while (e < hi && b->items[e].inst == i) ++e;
+      while (k + strips < e && b->items[k + strips].y0 == b->items[k].y0) ++strips;
+      const int nch = (e - k) / strips;
+      if (nch * strips != e - k) return LBM_OK;
+      for (int c = 0; c < nch; ++c) {
+        const int co = (c + nch / 2) % nch;  // the odd steps' c-th chunk row
+        for (int sx = 0; sx < strips; ++sx) {
+          const int pos = k + c * strips + sx - lo;
+          for (int par = 0; par < 2; ++par) {
+            const int cc = par ? co : c;
+            const WorkItem& w = b->items[k + cc * strips + sx];
+            ItemLink ln{};
+            ln.chunk = chunk0 + cc;
+            ln.strips = strips;
+            int nd = 0;
+            for (int r = w.y0 - 2; r <= w.y1 + 1; ++r) {
+              const int rr = P.walls ? std::min(std::max(r, 0), P.ny - 1)
+                                     : ((r % P.ny) + P.ny) % P.ny;
+              const int d = chunk0 + std::min(rr / b->rows, nch - 1);
+              bool seen = false;
+              for (int j = 0; j < nd; ++j) seen |= ln.dep[j] == d;
+              if (seen) continue;
+              if (nd == 4) return LBM_OK;  // too many dependencies: no persistent stepping
+              ln.dep[nd++] = d;
+            }
+            for (int j = nd; j < 4; ++j) ln.dep[j] = ln.dep[0];
+            items2[2 * (size_t)lo + (size_t)par * ng + pos] = w;
+            links2[2 * (size_t)lo + (size_t)par * ng + pos] = ln;
+          }
+          work[g] += (double)(b->items[k + c * strips + sx].y1 - b->items[k + c * strips + sx].y0 +
+                              4) * (2 * b->grp_nt[g] + kRowFixedCols);
+        }
+      }
+      chunk0 += nch;
+      sync += nch;
+      k = e;
+    }
+  }
+  b->grp_sync[b->n_groups] = sync;
+  double total = 0.0;
+  for (double w : work) total += w;
+  for (int g = 0; g < b->n_groups; ++g) {
+    const int cap = lbm::persist_occupancy(b->grp_nt[g], b->grp_full[g]) * std::max(b->sms, 1);
+    const int share = (int)std::floor(cap * (total > 0 ? work[g] / total : 1.0));
+    b->grp_grid[g] = std::max(1, std::min(share, b->grp_begin[g + 1] - b->grp_begin[g]) );
+  }
+  if (2 * n > b->cap_items2 || !b->d_items2) {
+    free_dev(b->d_items2);
+    free_dev(b->d_links2);
+    b->cap_items2 = 0;
+    CK(b, dev_malloc(&b->d_items2, sizeof(WorkItem) * 2 * n));
+    CK(b, dev_malloc(&b->d_links2, sizeof(ItemLink) * 2 * n));
+    b->cap_items2 = 2 * n;
+  }
+  if (sync > b->cap_sync || !b->d_sync) {
+    free_dev(b->d_sync);
+    b->cap_sync = 0;
+    CK(b, dev_malloc(&b->d_sync, sizeof(int) * sync));
+    b->cap_sync = sync;
+  }
+  CK(b, cudaMemcpy(b->d_items2, items2.data(), sizeof(WorkItem) * 2 * n, cudaMemcpyHostToDevice));
+  CK(b, cudaMemcpy(b->d_links2, links2.data(), sizeof(ItemLink) * 2 * n, cudaMemcpyHostToDevice));
+  b->persist = true;
+  return LBM_OK;
+}
+
 // Rebuild and upload the work lists (after a tiling change or a retirement).
 int rebuild_items(Batch* b) {
   drop_graphs(b);
@@ -483,6 +653,10 @@ int rebuild_items(Batch* b) {
   if (!b->d_item_begin) CK(b, dev_malloc(&b->d_item_begin, sizeof(int) * (b->n_inst + 1)));
   CK(b, cudaMemcpy(b->d_item_begin, b->item_begin.data(), sizeof(int) * (b->n_inst + 1),
                    cudaMemcpyHostToDevice));
+  {
+    int rc = build_persist(b);
+    if (rc) return rc;
+  }
   // Full-width strips of the pair kernel neither read nor write the ghost columns, so
   // after steps under one set of work lists they may be stale; a pass under the new lists
   // may use strips that read them.
@@ -653,6 +827,24 @@ int launch_group(Batch* b, int g, int c, cudaStream_t st) {
   return LBM_OK;
 }
 
+// n steps (at most kGraphSteps) of launch group g from slab c as one persistent launch on
+// st, after zeroing the group's queue and chunk counters.
+int launch_group_persist(Batch* b, int g, int c, int n, cudaStream_t st) {
+  int* sync = b->d_sync + b->grp_sync[g];
+  const int ints = b->grp_sync[g + 1] - b->grp_sync[g];
+  cudaError_t e = cudaMemsetAsync(sync, 0, sizeof(int) * ints, st);
+  if (e == cudaSuccess) {
+    const int lo = b->grp_begin[g], ng = b->grp_begin[g + 1] - lo;
+    e = lbm::launch_persist(b->grp_nt[g], b->grp_full[g], (float*)b->slab[c],
+                            (float*)b->slab[c ^ 1], b->d_inst, b->d_items2 + 2 * (size_t)lo,
+                            b->d_links2 + 2 * (size_t)lo, ng, n, sync, sync + 1, b->d_status,
+                            b->grp_grid[g], st);
+  }
+  if (e != cudaSuccess)
+    return set_err(b->err, LBM_ECUDA, "persistent step launch failed: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
 // One step of every active instance: the launch groups one after another on st.
 int launch_step(Batch* b, cudaStream_t st) {
   for (int g = 0; g < b->n_groups; ++g) {
@@ -680,6 +872,8 @@ int ensure_branches(Batch* b) {
 // so the groups overlap on the GPU and fill each other's tails.  b->cur is unchanged.
 int queue_steps(Batch* b, int n, cudaStream_t st) {
   const int start = b->cur;
+  if (b->persist && b->n_groups <= 1)
+    return n > 0 ? launch_group_persist(b, 0, start, n, st) : LBM_OK;
   if (b->n_groups <= 1) {
     int rc = LBM_OK;
     for (int k = 0; k < n && rc == LBM_OK; ++k) rc = launch_step(b, st);
@@ -695,6 +889,10 @@ int queue_steps(Batch* b, int n, cudaStream_t st) {
     return set_err(b->err, LBM_ECUDA, "stream fork failed: %s", cudaGetErrorString(e));
   for (int gi = 0; gi < b->n_groups && rc == LBM_OK; ++gi) {
     cudaStream_t sg = gi == 0 ? st : b->grp_stream[gi - 1];
+    if (b->persist) {
+      rc = n > 0 ? launch_group_persist(b, gi, start, n, sg) : LBM_OK;
+      continue;
+    }
     for (int k = 0; k < n && rc == LBM_OK; ++k) rc = launch_group(b, gi, start ^ (k & 1), sg);
   }
   // Join every branch that was forked, even after a failed launch.
@@ -2141,6 +2339,10 @@ int lbm_batch_active(const lbm_batch* b) {
   for (int a : b->b.active) n += a;
   return n;
 }
+
+int lbm_persistent(const lbm_handle* h) { return h ? (h->b.persist ? 1 : 0) : LBM_EINVAL; }
+
+int lbm_batch_persistent(const lbm_batch* b) { return b ? (b->b.persist ? 1 : 0) : LBM_EINVAL; }
 
 int lbm_batch_instance_transposed(const lbm_batch* b, int i) {
   if (!b || i < 0 || i >= b->b.n_inst) return LBM_EINVAL;

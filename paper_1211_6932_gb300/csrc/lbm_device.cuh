@@ -846,14 +846,25 @@ constexpr int sweep2_min_blocks(int nt) {
   return nt == 32 ? 20 : nt == 64 ? 10 : nt == 96 ? 6 : nt == 128 ? 5 : 65536 / (nt * 128);
 }
 
-// FULL selects the full-width strip at compile time (its own instantiation, so that the
-// strip-mode code keeps constant load offsets); a CTA whose instance does not match the
-// instantiation returns at once (the moments pass launches both over one item list).
-template <int NT, int MODE, bool FULL>
-__global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
-    const float* __restrict__ fin, float* __restrict__ fout, const InstParams* __restrict__ insts,
-    const WorkItem* __restrict__ items, int n_items, MomArgs<float> mo,
-    int* __restrict__ status) {
+// Work a pair-kernel item does besides its own: none for one item per CTA (sweep2_kernel);
+// the persistent kernel's queue and dependency bookkeeping otherwise (PersistHook).  Lane 0
+// of the CTA's last warp runs start() once the item's first row copies are issued (while
+// every warp waits for those rows) and row(s) after the copy issue of sweep step s.
+struct NoHook {
+  __device__ __forceinline__ void start() {}
+  __device__ __forceinline__ void row(int) {}
+};
+
+// One work item of the pair kernel (a strip of rows [y0, y1) of one instance), the body of
+// sweep2_kernel and sweep2_persist_kernel.  FULL selects the full-width strip at compile
+// time (its own instantiation, so that the strip-mode code keeps constant load offsets).
+// Returns true if a bounded wait ran out: the CTA has then waited for its copies in flight
+// and set STATUS_TIMEOUT.  `part` indexes the diagnostics partials (MODE_MOMENTS).
+template <int NT, int MODE, bool FULL, typename Hook>
+__device__ __forceinline__ bool sweep2_item(const float* __restrict__ fin,
+                                            float* __restrict__ fout, const InstParams& P,
+                                            const WorkItem& it, const MomArgs<float>& mo,
+                                            int* __restrict__ status, int part, Hook& hook) {
   typedef Sweep2Cfg<NT> C;
   typedef Num<float2> N;
   constexpr int WO = C::WO, SEG = C::SEG, NB = C::NBAR;
@@ -871,11 +882,6 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
   __shared__ float red_f[NT / 32][2];
   __shared__ int red_i[NT / 32];
 
-  if ((int)blockIdx.x >= n_items) return;
-  const WorkItem it = items[blockIdx.x];
-  const InstParams& P = insts[it.inst];
-  // the step launches hold items of one kind only (the host groups them, strips_for)
-  if (MODE == MODE_MOMENTS && (P.nx <= 2 * NT) != FULL) return;
   const Phys<float> ph = load_phys<float>(P);
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -960,9 +966,11 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
   __syncthreads();
   if (issuer) {
     const int n0 = min(nload, C::LEAD + 1);
+    fence_proxy_async_smem();  // reads of the slots by an earlier item precede the copies
     for (int j = 0; j < n0; ++j) issue_row(j);
     issued = n0;
   }
+  if (tid == NT - 32) hook.start();
 
   float2 cur[Q], nxt[Q];
   float2 cur_rho = N::k(1.f), cur_dr = N::k(0.f);
@@ -1060,6 +1068,7 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
       issue_row(s + C::LEAD);
       issued = s + C::LEAD + 1;
     }
+    if (tid == NT - 32) hook.row(s);  // bookkeeping of the persistent kernel
 
     if (s >= 3 && owner && psi_nb_ok) {
       const int yc = rstart + (s - 1) * dir;
@@ -1191,7 +1200,7 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
       }
       atomicOr(status, STATUS_TIMEOUT);
     }
-    return;
+    return true;
   }
   if (MODE == MODE_STEP) {
     if (flag_bad) atomicOr(status, STATUS_NONFINITE);
@@ -1228,13 +1237,190 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
         f1 = fmaxf(f1, red_f[w][1]);
         b += red_i[w];
       }
-      mo.part_sum[3 * blockIdx.x + 0] = s0;
-      mo.part_sum[3 * blockIdx.x + 1] = s1;
-      mo.part_sum[3 * blockIdx.x + 2] = s2;
-      mo.part_max[2 * blockIdx.x + 0] = f0;
-      mo.part_max[2 * blockIdx.x + 1] = f1;
-      mo.part_bad[blockIdx.x] = b;
+      mo.part_sum[3 * part + 0] = s0;
+      mo.part_sum[3 * part + 1] = s1;
+      mo.part_sum[3 * part + 2] = s2;
+      mo.part_max[2 * part + 0] = f0;
+      mo.part_max[2 * part + 1] = f1;
+      mo.part_bad[part] = b;
     }
+  }
+  return false;
+}
+
+// Pair kernel, one CTA per work item.  A CTA whose instance does not match the FULL
+// instantiation returns at once (the moments pass launches both over one item list).
+template <int NT, int MODE, bool FULL>
+__global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_kernel(
+    const float* __restrict__ fin, float* __restrict__ fout, const InstParams* __restrict__ insts,
+    const WorkItem* __restrict__ items, int n_items, MomArgs<float> mo,
+    int* __restrict__ status) {
+  if ((int)blockIdx.x >= n_items) return;
+  const WorkItem it = items[blockIdx.x];
+  const InstParams& P = insts[it.inst];
+  // the step launches hold items of one kind only (the host groups them, strips_for)
+  if (MODE == MODE_MOMENTS && (P.nx <= 2 * NT) != FULL) return;
+  NoHook hook;
+  sweep2_item<NT, MODE, FULL>(fin, fout, P, it, mo, status, (int)blockIdx.x, hook);
+}
+
+// Dependencies of a work item of the persistent kernel: its chunk (a chunk row of one
+// instance: every strip of rows [y0, y1)), the strips of a chunk row of its instance, and
+// up to four chunks, its own among them, whose previous step it waits for: the chunks
+// whose rows it reads (its rows and the two beyond each end, wrapped, or clamped at walls)
+// and the chunks that read its rows (whose previous-step reads its stores would overwrite).
+// Unused dependency entries repeat a used one.
+struct ItemLink {
+  int chunk, strips, dep[4], pad0, pad1;
+};
+
+constexpr int DEP_WAIT_LIMIT = 1 << 24;  // polls (with a short sleep) before giving up
+
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+__device__ __forceinline__ void red_add_relaxed_gpu(int* p, int v) {
+  asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Whether every dependency chunk of ln has `need` completed strips (acquire loads, issued
+// together).
+__device__ __forceinline__ bool deps_met(const int* done, const ItemLink& ln, int need) {
+  const int a = ld_acquire_gpu(done + ln.dep[0]), b = ld_acquire_gpu(done + ln.dep[1]);
+  const int c = ld_acquire_gpu(done + ln.dep[2]), d = ld_acquire_gpu(done + ln.dep[3]);
+  return min(min(a, b), min(c, d)) >= need;
+}
+
+// Wait until deps_met; false after DEP_WAIT_LIMIT rounds.
+__device__ __forceinline__ bool wait_deps(const int* done, const ItemLink& ln, int need) {
+  for (int polls = 0; !deps_met(done, ln, need); ++polls) {
+    if (polls + 1 >= DEP_WAIT_LIMIT) return false;
+    __nanosleep(64);
+  }
+  return true;
+}
+
+// Queue and dependency bookkeeping of the persistent kernel, done by lane 0 of the CTA's
+// last warp inside an item so that its latencies overlap the item's rows: once the
+// item's first row copies are issued, while every warp waits for those rows, it releases
+// the previous item (its chunk counter is incremented; the CTA barrier at that item's end
+// ordered every thread's stores before this thread's release fence) and takes the next
+// item from the queue; after the copy issue of sweep step 2 it reads the next item's
+// dependency link, after step 4 its dependency counters.  If those already show the next
+// item's dependencies met, the next item starts without waiting.  (Doing this on the
+// issuing thread delayed warp 0, and with it every row barrier, by the fence and the queue
+// atomic: 82.1 against 84.0 GLUPS on the 4096^2 field; taking two items ahead and
+// reading everything at the start measured 86.4 against 87.6 at 32-row chunks.)  The
+// state lives in shared memory, not in every thread's registers.
+struct PersistState {
+  ItemLink ln;   // the next item's dependency link once have_link
+  int release;   // chunk of the finished item not yet released, or -1
+  int next;      // the item taken for after the current one
+  int have_link, dep_ok;
+};
+
+struct PersistHook {
+  PersistState* st;
+  int* queue;
+  const ItemLink* links2;
+  int* done;
+  int n_items, total;
+  __device__ __forceinline__ void release_done() {
+    if (st->release >= 0) {
+      fence_acq_rel_gpu();
+      red_add_relaxed_gpu(done + st->release, 1);
+      st->release = -1;
+    }
+  }
+  __device__ __forceinline__ void start() {
+    release_done();
+    st->next = atomicAdd(queue, 1);
+    st->have_link = st->dep_ok = 0;
+  }
+  __device__ __forceinline__ void row(int s) {
+    if (s != 2 && s != 4) return;
+    const int next = st->next;
+    if (next >= total || next < n_items) return;
+    const int t = next / n_items;
+    if (s == 2) {
+      st->ln = links2[(t & 1) * n_items + (next - t * n_items)];
+      st->have_link = 1;
+    } else if (st->have_link) {
+      st->dep_ok = deps_met(done, st->ln, st->ln.strips * t);
+    }
+  }
+};
+
+// Persistent pair kernel for `steps` time steps of one launch group (STEP mode): the CTAs
+// take work items in order from *queue, item q being step t = q / n_items, entry
+// k = q - t n_items of that step's list (items2 and links2 hold the even steps' list, then
+// the odd steps', which visits each instance's chunks starting from the middle, so that
+// the first items of a step do not wait on the last ones of the step before).  Step t
+// reads slab t & 1 and writes the other.  An item's copies start only once each
+// dependency chunk has completed all strips of steps 0 .. t-1 (done[] counts completed
+// strips per chunk; acquire loads, then a proxy fence before the bulk reads); a finished
+// item is released (a CTA barrier, then a release fence and an increment by thread 0) at
+// the latest before its CTA waits for anything.  A CTA takes its next item from the queue
+// while it works on the current one (PersistHook).  An item waits only on items earlier
+// in the queue: the earliest unfinished item is some CTA's current one (a CTA's next item
+// comes after its current one), its dependencies are finished and released, so every
+// wait ends unless a CTA gives up; a CTA that gives up sets STATUS_TIMEOUT and returns,
+// and the CTAs waiting on it give up in turn.
+template <int NT, bool FULL>
+__global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_persist_kernel(
+    float* slab0, float* slab1, const InstParams* __restrict__ insts,
+    const WorkItem* __restrict__ items2, const ItemLink* __restrict__ links2, int n_items,
+    int steps, int* queue, int* done, int* __restrict__ status) {
+  __shared__ int s_q, s_stop;
+  __shared__ PersistState ps;
+  const MomArgs<float> mo{};
+  const int total = steps * n_items;
+  PersistHook h{&ps, queue, links2, done, n_items, total};
+  if (threadIdx.x == 0) {
+    ps.release = -1;
+    ps.have_link = ps.dep_ok = 0;
+    ps.next = atomicAdd(queue, 1);
+  }
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int q = ps.next;
+      int stop = 0;
+      if (q < total) {
+        const int t = q / n_items;
+        if (t > 0 && !ps.dep_ok) {
+          h.release_done();  // never wait while holding a finished item
+          if (!ps.have_link) ps.ln = links2[(t & 1) * n_items + (q - t * n_items)];
+          if (!wait_deps(done, ps.ln, ps.ln.strips * t)) {
+            atomicOr(status, STATUS_TIMEOUT);
+            stop = 1;
+          }
+        }
+        fence_proxy_async_global();  // the acquired stores precede this CTA's bulk reads
+      } else {
+        h.release_done();
+      }
+      s_q = q;
+      s_stop = stop;
+    }
+    __syncthreads();
+    const int q = s_q;
+    if (q >= total || s_stop) return;
+    const int t = q / n_items, k = q - t * n_items, par = t & 1;
+    const WorkItem it = items2[par * n_items + k];
+    if (sweep2_item<NT, MODE_STEP, FULL>(par ? slab1 : slab0, par ? slab0 : slab1,
+                                         insts[it.inst], it, mo, status, 0, h))
+      return;
+    __syncthreads();  // every thread's stores of the item precede its release
+    if (threadIdx.x == 0) ps.release = links2[par * n_items + k].chunk;
   }
 }
 

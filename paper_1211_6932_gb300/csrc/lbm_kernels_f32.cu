@@ -17,6 +17,33 @@ cudaError_t launch_sweep<float>(int nt, int vec, int mode, int full, const float
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_persist(int nt, int full, float* slab0, float* slab1,
+                           const InstParams* d_inst, const WorkItem* items2,
+                           const ItemLink* links2, int n_items, int steps, int* queue,
+                           int* done, int* d_status, int grid, cudaStream_t st) {
+#define LBM_PERSIST(T)                                                                       \
+  if (nt == T)                                                                               \
+    return full ? launch_persist2_cfg<T, true>(slab0, slab1, d_inst, items2, links2, n_items, \
+                                               steps, queue, done, d_status, grid, st)       \
+                : launch_persist2_cfg<T, false>(slab0, slab1, d_inst, items2, links2,        \
+                                                n_items, steps, queue, done, d_status, grid, \
+                                                st);
+  LBM_PERSIST(32)
+  LBM_PERSIST(64)
+  LBM_PERSIST(96)
+  LBM_PERSIST(128)
+#undef LBM_PERSIST
+  return cudaErrorInvalidValue;
+}
+
+int persist_occupancy(int nt, int full) {
+  if (nt == 32) return full ? persist_occupancy_cfg<32, true>() : persist_occupancy_cfg<32, false>();
+  if (nt == 64) return full ? persist_occupancy_cfg<64, true>() : persist_occupancy_cfg<64, false>();
+  if (nt == 96) return full ? persist_occupancy_cfg<96, true>() : persist_occupancy_cfg<96, false>();
+  if (nt == 128) return full ? persist_occupancy_cfg<128, true>() : persist_occupancy_cfg<128, false>();
+  return 1;
+}
+
 template <>
 int sweep_occupancy<float>(int nt, int vec) {
   if (nt == 64 && vec == 1) return occupancy_cfg<float, 64>();

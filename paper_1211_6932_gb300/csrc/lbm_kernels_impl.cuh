@@ -79,6 +79,34 @@ static cudaError_t launch_sweep2_mode(int mode, int full, const float* fin, floa
                                                            mo, d_status, st);
 }
 
+// Persistent pair kernel (sweep2_persist_kernel) with `grid` CTAs.
+template <int NT, bool FULL>
+static cudaError_t launch_persist2_cfg(float* slab0, float* slab1, const InstParams* d_inst,
+                                       const WorkItem* items2, const ItemLink* links2,
+                                       int n_items, int steps, int* queue, int* done,
+                                       int* d_status, int grid, cudaStream_t st) {
+  constexpr size_t smem = Sweep2Cfg<NT>::BYTES;
+  static std::atomic<unsigned long long> flag{0};
+  cudaError_t e = ensure_smem_attr(sweep2_persist_kernel<NT, FULL>, smem, flag);
+  if (e != cudaSuccess) return e;
+  if (n_items <= 0 || steps <= 0 || grid <= 0) return cudaSuccess;
+  sweep2_persist_kernel<NT, FULL><<<grid, NT, smem, st>>>(slab0, slab1, d_inst, items2, links2,
+                                                          n_items, steps, queue, done,
+                                                          d_status);
+  return cudaGetLastError();
+}
+
+template <int NT, bool FULL>
+static int persist_occupancy_cfg() {
+  constexpr size_t smem = Sweep2Cfg<NT>::BYTES;
+  cudaFuncSetAttribute(sweep2_persist_kernel<NT, FULL>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &occ, sweep2_persist_kernel<NT, FULL>, NT, smem);
+  return (e == cudaSuccess && occ > 0) ? occ : 1;
+}
+
 template <int NT>
 static int occupancy2_cfg() {
   constexpr size_t smem = Sweep2Cfg<NT>::BYTES;

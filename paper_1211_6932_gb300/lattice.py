@@ -226,6 +226,14 @@ class Lattice:
     def step(self, n=1):
         self._check(self._L.lbm_step(self._h, int(n)))
 
+    @property
+    def persistent(self):
+        """Whether steps run as persistent launches (lbm_persistent)."""
+        rc = self._L.lbm_persistent(self._h)
+        if rc < 0:
+            self._check(rc)
+        return bool(rc)
+
     def sync(self):
         """lbm_sync: wait for the queued steps and asynchronous transfers."""
         try:
@@ -542,6 +550,11 @@ class Batch:
     @property
     def active(self):
         return self._check(self._L.lbm_batch_active(self._h))
+
+    @property
+    def persistent(self):
+        """Whether steps run as persistent launches (lbm_batch_persistent)."""
+        return bool(self._check(self._L.lbm_batch_persistent(self._h)))
 
     def is_transposed(self, i):
         """Whether instance i is stored with its axes exchanged

@@ -1,0 +1,102 @@
+"""Persistent stepping (sweep2_persist_kernel: one launch per run of up to 64 steps and
+launch group, CTAs taking (step, chunk row, strip) items from a queue and waiting only on
+the chunk rows of the previous step they depend on) gives the populations of one launch
+per step and group bit for bit: periodic and wall boundaries, strips and full-width
+strips, odd widths, ragged last chunks (down to one row), two-row chunks, graph replays
+and shorter runs, and a batch of one launch group (batches of several groups keep one
+launch per step and group)."""
+import os
+
+import numpy as np
+import pytest
+
+from tests import pairs
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(make, persistent, steps=(70, 5)):
+    old = os.environ.get("LBM_PERSISTENT")
+    # 2: persistent whenever the dependency rule allows, also with fewer items per step
+    # than the default rule asks for (these small lattices are the hard cases)
+    os.environ["LBM_PERSISTENT"] = "2" if persistent else "0"
+    try:
+        obj = make()
+    finally:
+        if old is None:
+            del os.environ["LBM_PERSISTENT"]
+        else:
+            os.environ["LBM_PERSISTENT"] = old
+    try:
+        mode = obj.persistent
+        out = []
+        for n in steps:
+            obj.step(n)
+            out.append(obj.get_populations() if hasattr(obj, "nx") else
+                       [obj.get_populations(i) for i in range(len(obj))])
+        return mode, out
+    finally:
+        obj.close()
+
+
+LATTICES = [
+    (pairs.case(600, 250, tr=0.7, sigma=0.114), {}),                      # strips, periodic
+    (pairs.case(300, 97, tr=0.6, sigma=0.114, walls=True, visc="step", nu_l=0.05, nu_v=0.3),
+     {}),                                                                  # walls, ragged chunk
+    (pairs.case(257, 37, tr=0.7, sigma=0.114), {"tile_rows": 12}),        # odd nx, 1-row last chunk
+    (pairs.case(200, 64, tr=0.8, sigma=0.11), {"tile_rows": 2}),          # full width, 2-row chunks
+    (pairs.case(301, 50, tr=0.7, sigma=0.114), {"tile_threads": 64}),     # 64-thread strips
+]
+
+
+@pytest.mark.parametrize("k", range(len(LATTICES)))
+def test_persistent_lattice_equals_per_step_launches(k):
+    c, kw = LATTICES[k]
+    f0 = pairs.droplet_state(c, vel=0.01)
+
+    def make():
+        L = pairs.gpu_lattice(c, "fp32", **kw)
+        L.set_populations(f0)
+        return L
+    mp, a = _run(make, True)
+    mq, b = _run(make, False)
+    assert mp and not mq
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_default_rule_steps_large_lattices_persistently():
+    """Without LBM_PERSISTENT the 4096^2 field steps persistently (its default 32-row chunks
+    give 2176 items per step, about three waves) and a 1024^2 lattice does not (fewer
+    items than two waves of resident CTAs)."""
+    c = pairs.case(4096, 4096, tr=0.7, sigma=0.114)
+    with pairs.gpu_lattice(c, "fp32") as L:
+        assert L.persistent and L.tiling[2] == 32
+    with pairs.gpu_lattice(dict(c, nx=1024, ny=1024), "fp32") as L:
+        assert not L.persistent
+
+
+def test_persistent_batch_equals_per_step_launches():
+    """A batch whose instances form one launch group (every instance swept in one
+    full-width 128-thread strip per row) steps persistently; a batch of several groups
+    (strips and full-width strips) keeps one launch per step and group.  Both give the
+    per-step populations bit for bit."""
+    from paper_1211_6932_gb300 import Batch
+    from tests.test_gpu_batch import CASES, instance, start_fields
+    for cs, single in ((CASES[:1] + CASES[2:3] + [pairs.case(200, 90, tr=0.75, sigma=0.114),
+                                                 pairs.case(130, 67, tr=0.8, sigma=0.11,
+                                                            walls=True)], True),
+                       (CASES + [pairs.case(400, 40, tr=0.75, sigma=0.114)], False)):
+        fields = [start_fields(c, 60 + i) for i, c in enumerate(cs)]
+
+        def make():
+            b = Batch([instance(c) for c in cs], precision="fp32")
+            for i, fl in enumerate(fields):
+                b.init_fields(i, *fl)
+            return b
+        mp, a = _run(make, True)
+        mq, b = _run(make, False)
+        assert mp == single and not mq
+        for x, y in zip(a, b):
+            for i in range(len(cs)):
+                assert np.array_equal(x[i], y[i]), i
