@@ -219,6 +219,18 @@ int lbm_sync(lbm_handle* h);
 int lbm_selftest_timeout(lbm_handle* h, long long polls);
 
 /*
+ * The same check for the persistent step kernel's dependency wait (see lbm_persistent):
+ * one work item of the lattice is run as a two-step persistent launch whose second step
+ * waits on a chunk counter that no item increments; the wait gives up after `polls`
+ * rounds (1 to 2^20, each a few hundred nanoseconds), sets the timeout bit and the
+ * kernel returns.  Returns LBM_ETIMEOUT, as every later lbm_sync does until the state is
+ * replaced; the current state is not changed (the first step writes only the other
+ * population buffer).  LBM_EINVAL unless the lattice is FP32_DEV with tile_vec 2.
+ * Synchronous.
+ */
+int lbm_selftest_dep_timeout(lbm_handle* h, int polls);
+
+/*
  * Discrete pressure tensor of Eq. 18 at every node of the current state (a diagnostic):
  *   P = rho c_s^2 I + (G/2) psi(x) sum_q w(|e_q|^2) psi(x + e_q) e_q e_q,
  * w = 1/3 on the axes and 1/12 on the diagonals (Eq. 7), psi of Eq. 24, rho as in

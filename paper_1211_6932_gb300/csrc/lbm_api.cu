@@ -838,7 +838,7 @@ int launch_group_persist(Batch* b, int g, int c, int n, cudaStream_t st) {
     e = lbm::launch_persist(b->grp_nt[g], b->grp_full[g], (float*)b->slab[c],
                             (float*)b->slab[c ^ 1], b->d_inst, b->d_items2 + 2 * (size_t)lo,
                             b->d_links2 + 2 * (size_t)lo, ng, n, sync, sync + 1, b->d_status,
-                            b->grp_grid[g], st);
+                            b->grp_grid[g], lbm::DEP_WAIT_LIMIT, st);
   }
   if (e != cudaSuccess)
     return set_err(b->err, LBM_ECUDA, "persistent step launch failed: %s", cudaGetErrorString(e));
@@ -1983,6 +1983,47 @@ int lbm_selftest_timeout(lbm_handle* h, long long polls) {
   if (e != cudaSuccess)
     return set_err(h->b.err, LBM_ECUDA, "self-test launch failed: %s", cudaGetErrorString(e));
   return sync_status(&h->b);
+}
+
+int lbm_selftest_dep_timeout(lbm_handle* h, int polls) {
+  DeviceGuard g_(h ? &h->b : nullptr);
+  if (!h) return LBM_EINVAL;
+  Batch* b = &h->b;
+  if (polls < 1 || polls > (1 << 20))
+    return set_err(b->err, LBM_EINVAL, "polls must be in [1, 2^20]");
+  if (b->fp64 || b->vec != 2 || b->n_items < 1 || b->n_groups < 1)
+    return set_err(b->err, LBM_EINVAL, "the self-test needs an FP32 lattice with tile_vec 2");
+  // One item, two steps: step 0 runs and releases chunk 0; step 1 waits for chunk 1, which
+  // no item has, so its wait runs out.
+  WorkItem items2[2] = {b->items[0], b->items[0]};
+  ItemLink links2[2];
+  for (ItemLink& l : links2) {
+    l = ItemLink{};
+    l.chunk = 0;
+    l.strips = 1;
+    for (int& d : l.dep) d = 1;
+  }
+  void* buf = nullptr;
+  int rc = dev_alloc(b, &buf, sizeof(items2) + sizeof(links2) + 4 * sizeof(int));
+  if (rc) return rc;
+  char* p = (char*)buf;
+  WorkItem* d_items2 = (WorkItem*)p;
+  ItemLink* d_links2 = (ItemLink*)(p + sizeof(items2));
+  int* sync = (int*)(p + sizeof(items2) + sizeof(links2));
+  cudaError_t e = cudaMemcpyAsync(d_items2, items2, sizeof(items2), cudaMemcpyHostToDevice,
+                                  b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_links2, links2, sizeof(links2), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sync, 0, 4 * sizeof(int), b->stream);
+  if (e == cudaSuccess)
+    e = lbm::launch_persist(b->grp_nt[0], b->grp_full[0], (float*)b->slab[b->cur],
+                            (float*)b->slab[b->cur ^ 1], b->d_inst, d_items2, d_links2, 1, 2,
+                            sync, sync + 1, b->d_status, 1, polls, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  dev_free(buf);
+  if (e != cudaSuccess)
+    return set_err(b->err, LBM_ECUDA, "self-test launch failed: %s", cudaGetErrorString(e));
+  return sync_status(b);
 }
 
 int lbm_init_droplets(lbm_handle* h, const lbm_droplet* drops, int n, const lbm_warm_params* p,

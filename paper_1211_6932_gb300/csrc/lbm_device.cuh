@@ -1300,10 +1300,11 @@ __device__ __forceinline__ bool deps_met(const int* done, const ItemLink& ln, in
   return min(min(a, b), min(c, d)) >= need;
 }
 
-// Wait until deps_met; false after DEP_WAIT_LIMIT rounds.
-__device__ __forceinline__ bool wait_deps(const int* done, const ItemLink& ln, int need) {
+// Wait until deps_met; false after `limit` rounds.
+__device__ __forceinline__ bool wait_deps(const int* done, const ItemLink& ln, int need,
+                                          int limit) {
   for (int polls = 0; !deps_met(done, ln, need); ++polls) {
-    if (polls + 1 >= DEP_WAIT_LIMIT) return false;
+    if (polls + 1 >= limit) return false;
     __nanosleep(64);
   }
   return true;
@@ -1374,12 +1375,13 @@ struct PersistHook {
 // in the queue: the earliest unfinished item is some CTA's current one (a CTA's next item
 // comes after its current one), its dependencies are finished and released, so every
 // wait ends unless a CTA gives up; a CTA that gives up sets STATUS_TIMEOUT and returns,
-// and the CTAs waiting on it give up in turn.
+// and the CTAs waiting on it give up in turn.  dep_limit bounds each dependency wait
+// (DEP_WAIT_LIMIT; a failure-detection self-test passes a short one).
 template <int NT, bool FULL>
 __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_persist_kernel(
     float* slab0, float* slab1, const InstParams* __restrict__ insts,
     const WorkItem* __restrict__ items2, const ItemLink* __restrict__ links2, int n_items,
-    int steps, int* queue, int* done, int* __restrict__ status) {
+    int steps, int* queue, int* done, int* __restrict__ status, int dep_limit) {
   __shared__ int s_q, s_stop;
   __shared__ PersistState ps;
   const MomArgs<float> mo{};
@@ -1399,7 +1401,7 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_persist_kern
         if (t > 0 && !ps.dep_ok) {
           h.release_done();  // never wait while holding a finished item
           if (!ps.have_link) ps.ln = links2[(t & 1) * n_items + (q - t * n_items)];
-          if (!wait_deps(done, ps.ln, ps.ln.strips * t)) {
+          if (!wait_deps(done, ps.ln, ps.ln.strips * t, dep_limit)) {
             atomicOr(status, STATUS_TIMEOUT);
             stop = 1;
           }

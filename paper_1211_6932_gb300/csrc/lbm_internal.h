@@ -63,11 +63,12 @@ cudaError_t launch_pressure(const S* rho, const InstParams& P, double sigma, dou
 // FP32 pair kernel in its persistent form (sweep2_persist_kernel): `steps` time steps of
 // one launch group, from slab0 (step 0 reads it) and slab1, with `grid` CTAs.  items2 and
 // links2 hold 2 n_items entries (the even steps' list, then the odd steps'); queue (one int)
-// and done (one int per chunk) must be zero at launch.
+// and done (one int per chunk) must be zero at launch; dep_limit bounds each dependency
+// wait (DEP_WAIT_LIMIT).
 cudaError_t launch_persist(int nt, int full, float* slab0, float* slab1,
                            const InstParams* d_inst, const WorkItem* items2,
                            const ItemLink* links2, int n_items, int steps, int* queue,
-                           int* done, int* d_status, int grid, cudaStream_t st);
+                           int* done, int* d_status, int grid, int dep_limit, cudaStream_t st);
 // Resident CTAs per SM of the persistent pair kernel of width nt (at least 1).
 int persist_occupancy(int nt, int full);
 

@@ -20,14 +20,16 @@ cudaError_t launch_sweep<float>(int nt, int vec, int mode, int full, const float
 cudaError_t launch_persist(int nt, int full, float* slab0, float* slab1,
                            const InstParams* d_inst, const WorkItem* items2,
                            const ItemLink* links2, int n_items, int steps, int* queue,
-                           int* done, int* d_status, int grid, cudaStream_t st) {
+                           int* done, int* d_status, int grid, int dep_limit,
+                           cudaStream_t st) {
 #define LBM_PERSIST(T)                                                                       \
   if (nt == T)                                                                               \
     return full ? launch_persist2_cfg<T, true>(slab0, slab1, d_inst, items2, links2, n_items, \
-                                               steps, queue, done, d_status, grid, st)       \
+                                               steps, queue, done, d_status, grid, dep_limit, \
+                                               st)                                           \
                 : launch_persist2_cfg<T, false>(slab0, slab1, d_inst, items2, links2,        \
                                                 n_items, steps, queue, done, d_status, grid, \
-                                                st);
+                                                dep_limit, st);
   LBM_PERSIST(32)
   LBM_PERSIST(64)
   LBM_PERSIST(96)

@@ -84,7 +84,8 @@ template <int NT, bool FULL>
 static cudaError_t launch_persist2_cfg(float* slab0, float* slab1, const InstParams* d_inst,
                                        const WorkItem* items2, const ItemLink* links2,
                                        int n_items, int steps, int* queue, int* done,
-                                       int* d_status, int grid, cudaStream_t st) {
+                                       int* d_status, int grid, int dep_limit,
+                                       cudaStream_t st) {
   constexpr size_t smem = Sweep2Cfg<NT>::BYTES;
   static std::atomic<unsigned long long> flag{0};
   cudaError_t e = ensure_smem_attr(sweep2_persist_kernel<NT, FULL>, smem, flag);
@@ -92,7 +93,7 @@ static cudaError_t launch_persist2_cfg(float* slab0, float* slab1, const InstPar
   if (n_items <= 0 || steps <= 0 || grid <= 0) return cudaSuccess;
   sweep2_persist_kernel<NT, FULL><<<grid, NT, smem, st>>>(slab0, slab1, d_inst, items2, links2,
                                                           n_items, steps, queue, done,
-                                                          d_status);
+                                                          d_status, dep_limit);
   return cudaGetLastError();
 }
 

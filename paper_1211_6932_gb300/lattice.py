@@ -322,6 +322,11 @@ class Lattice:
         code LBM_ETIMEOUT when the timeout is detected and reported."""
         self._check(self._L.lbm_selftest_timeout(self._h, int(polls)))
 
+    def selftest_dep_timeout(self, polls=1000):
+        """The same check for the persistent kernel's dependency wait
+        (lbm_selftest_dep_timeout); raises LbmError with code LBM_ETIMEOUT."""
+        self._check(self._L.lbm_selftest_dep_timeout(self._h, int(polls)))
+
     def moments(self, out=None, dtype=np.float64):
         """rho, ux, uy of Eq. 6 as host arrays of dtype (float64, or float32 for the float
         transfer, lbm_moments_f32).  With out= (a C-contiguous float64 or float32 (ny, nx)

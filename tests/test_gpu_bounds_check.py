@@ -74,10 +74,13 @@ SCRIPT = textwrap.dedent('''
 ''')
 
 
-def test_bounds_check_build_runs_clean():
+@pytest.mark.parametrize("persistent", ["0", "2"])
+def test_bounds_check_build_runs_clean(persistent):
+    """Once with one launch per step, once with persistent stepping wherever the
+    dependency rule allows (LBM_PERSISTENT=2: every single-group FP32 pair tiling)."""
     from paper_1211_6932_gb300 import build
     build.build(check=True)
-    env = dict(os.environ, LBM_LIBRARY="check")
+    env = dict(os.environ, LBM_LIBRARY="check", LBM_PERSISTENT=persistent)
     r = subprocess.run([sys.executable, "-c", SCRIPT], cwd=ROOT, env=env,
                        capture_output=True, text=True, timeout=1200)
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]

@@ -31,6 +31,40 @@ def test_bounded_wait_timeout_is_reported_and_context_survives():
         assert np.array_equal(L.get_populations(), ref.get_populations())
 
 
+@pytest.mark.parametrize("walls", [False, True])
+def test_persistent_dependency_wait_runs_out_cleanly(walls):
+    """The persistent kernel's dependency wait on a counter that nothing increments gives
+    up after its bound: LBM_ETIMEOUT, reported until the state is replaced, the current
+    state untouched, and the lattice then steps (persistently) as a fresh one does."""
+    from paper_1211_6932_gb300 import LbmError
+    c = pairs.case(300, 70, tr=0.7, sigma=0.114, walls=walls)
+    f = pairs.droplet_state(c, vel=0.01)
+    with pairs.gpu_lattice(c, "fp32") as L, pairs.gpu_lattice(c, "fp32") as ref:
+        L.set_populations(f)
+        with pytest.raises(LbmError) as ei:
+            L.selftest_dep_timeout(2000)
+        assert ei.value.code == -5
+        with pytest.raises(LbmError) as ei:
+            L.sync()
+        assert ei.value.code == -5
+        # the populations are copied before the status is reported
+        from paper_1211_6932_gb300.lattice import _d
+        g = np.empty((9,) + L.shape)
+        assert L._L.lbm_get_populations(L.handle, _d(g)) == -5
+        ref.set_populations(f)
+        assert np.array_equal(g, ref.get_populations())
+        L.set_populations(f)
+        ref.set_populations(f)
+        L.step(70)
+        ref.step(70)
+        L.sync()
+        assert np.array_equal(L.get_populations(), ref.get_populations())
+        for polls in (0, 1 << 21):
+            with pytest.raises(LbmError) as ei:
+                L.selftest_dep_timeout(polls)
+            assert ei.value.code == -1
+
+
 def test_selftest_rejects_bad_poll_counts():
     from paper_1211_6932_gb300 import LbmError
     c = pairs.case(32, 32, tr=0.7, sigma=0.114)
