@@ -175,7 +175,9 @@ int lbm_get_populations(lbm_handle* h, double* f);
 
 /*
  * Advance n >= 0 time steps (Eqs. 1-7 with the forcing of Eq. 25, Sec. II-III).  Each
- * step is one launch of the fused kernel; runs of steps are replayed from a CUDA graph.
+ * step is one pass of the fused kernel: one launch per step, or, stepping persistently
+ * (see lbm_persistent), one launch per run of up to 64 steps; runs of 64 steps are
+ * replayed from a CUDA graph.
  * Asynchronous: returns once the work is queued.  Status is reported by lbm_sync and by
  * every synchronous call.
  */
@@ -423,7 +425,8 @@ const char* lbm_batch_last_error(const lbm_batch* b);
 int lbm_batch_init_fields(lbm_batch* b, int i, const double* rho, const double* ux,
                           const double* uy);
 /* Advance every active instance n steps (one launch per step, kernel width and kind of
- * strip, CUDA-graph replay; see lbm_batch_launches_per_step). */
+ * strip, or one per run of up to 64 steps stepping persistently; CUDA-graph replay; see
+ * lbm_batch_launches_per_step and lbm_batch_persistent). */
 int lbm_batch_step(lbm_batch* b, int n);
 /* Float host variant of lbm_batch_init_fields, as lbm_init_fields_f32. */
 int lbm_batch_init_fields_f32(lbm_batch* b, int i, const float* rho, const float* ux,
@@ -478,10 +481,11 @@ int lbm_batch_autotune(lbm_batch* b, int steps, const char* cache_path, int* thr
                        int* vec, int* rows, double* ms_per_step);
 /* Tiling in use by a batch (threads is LBM_TILE_PER_INSTANCE for per-instance widths). */
 int lbm_batch_get_tiling(const lbm_batch* b, int* threads, int* vec, int* rows);
-/* Step-kernel launches per step of lbm_batch_step (0 when nothing is active): one per
- * kernel width in use (several only with LBM_TILE_PER_INSTANCE) and kind of strip
- * (full-width strips for instances of at most 2 * threads columns, strips for wider
- * ones; pair kernel only). */
+/* Launch groups of lbm_batch_step (0 when nothing is active): one per kernel width in use
+ * (several only with LBM_TILE_PER_INSTANCE) and kind of strip (full-width strips for
+ * instances of at most 2 * threads columns, strips for wider ones; pair kernel only).
+ * Each group is one step-kernel launch per step, or per run of up to 64 steps when the
+ * batch steps persistently (lbm_batch_persistent). */
 int lbm_batch_launches_per_step(const lbm_batch* b);
 /* Persistent stepping of a batch (see lbm_persistent). */
 int lbm_batch_persistent(const lbm_batch* b);
