@@ -1315,12 +1315,15 @@ __device__ __forceinline__ bool wait_deps(const int* done, const ItemLink& ln, i
 // item's first row copies are issued, while every warp waits for those rows, it releases
 // the previous item (its chunk counter is incremented; the CTA barrier at that item's end
 // ordered every thread's stores before this thread's release fence) and takes the next
-// item from the queue; after the copy issue of sweep step 2 it reads the next item's
-// dependency link, after step 4 its dependency counters.  If those already show the next
+// item from the queue and reads its dependency link; after the copy issue of sweep step
+// 4 it reads the next item's dependency counters.  If those already show the next
 // item's dependencies met, the next item starts without waiting.  (Doing this on the
 // issuing thread delayed warp 0, and with it every row barrier, by the fence and the queue
 // atomic: 82.1 against 84.0 GLUPS on the 4096^2 field; taking two items ahead and
-// reading everything at the start measured 86.4 against 87.6 at 32-row chunks.)  The
+// reading everything at the start measured 86.4 against 87.6 at 32-row chunks, reading
+// the link at step 2 instead of at the start 87.6 against 87.8; a second set of row
+// barriers, so that the next item could be published before the end-of-item barrier and
+// two of the three barriers per item dropped, 87.2 against 87.6.)  The
 // state lives in shared memory, not in every thread's registers.
 struct PersistState {
   ItemLink ln;   // the next item's dependency link once have_link
@@ -1343,21 +1346,19 @@ struct PersistHook {
     }
   }
   __device__ __forceinline__ void start() {
-    release_done();
-    st->next = atomicAdd(queue, 1);
+    const int next = atomicAdd(queue, 1);
+    release_done();  // its fence drains while the atomic is in flight
+    st->next = next;
     st->have_link = st->dep_ok = 0;
-  }
-  __device__ __forceinline__ void row(int s) {
-    if (s != 2 && s != 4) return;
-    const int next = st->next;
-    if (next >= total || next < n_items) return;
-    const int t = next / n_items;
-    if (s == 2) {
+    if (next < total && next >= n_items) {
+      const int t = next / n_items;
       st->ln = links2[(t & 1) * n_items + (next - t * n_items)];
       st->have_link = 1;
-    } else if (st->have_link) {
-      st->dep_ok = deps_met(done, st->ln, st->ln.strips * t);
     }
+  }
+  __device__ __forceinline__ void row(int s) {
+    if (s != 4 || !st->have_link) return;
+    st->dep_ok = deps_met(done, st->ln, st->ln.strips * (st->next / n_items));
   }
 };
 
