@@ -7,10 +7,16 @@
 //                     staged in shared memory as floats (rows padded to avoid bank
 //                     conflicts); forward, and in training mode the backward pass down to
 //                     the per-row deltas, which are written to row-major scratch.
-//   mlp_param_kernel  one thread per parameter: the gradient as a sum over rows in row
-//                     order (deterministic), then the Adam update of the FP32 master
-//                     weight, its moments and its BF16 copy.  Block 0 also reduces the
-//                     loss in a fixed order.
+//   mlp_param_kernel  32 parameters per block, one per lane, and the rows split over the
+//                     block's 8 warps (warp w sums rows w, w + 8, ... in order); the 8
+//                     partial sums are added in warp order (deterministic), then the
+//                     Adam update of the FP32 master weight, its moments and its BF16
+//                     copy.  Block 0 also reduces the loss in a fixed order.  (One thread
+//                     per parameter summing all rows left one warp per SM waiting on its
+//                     loads: 34 us of a 49 us update under ncu, against 18.6 us.  With 32
+//                     row slices the Adam trajectory of 60 updates left 1.4 % of the
+//                     parameters more than 1e-5 from the oracle's, against 1 % allowed:
+//                     the summation order moves parameters whose second moment is tiny.)
 // Runs of training updates are replayed from a captured CUDA graph.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -34,6 +40,8 @@ constexpr int W1S = NI + 1;  // padded row strides in shared memory
 constexpr int W2S = NH + 1;
 constexpr int ROWS_PER_BLOCK = 8;  // warps per block in the rows kernel
 constexpr int PARAM_THREADS = 256;
+constexpr int PARAM_SLICES = PARAM_THREADS / 32;  // row slices (warps) per parameter
+constexpr int PARAM_BLOCKS = (NP + 31) / 32;      // 32 parameters per block
 constexpr int kGraphUpdates = 50;
 constexpr int kLossHistory = 1 << 16;
 
@@ -228,10 +236,12 @@ __global__ void __launch_bounds__(PARAM_THREADS) mlp_param_kernel(
         loss_hist[(*update_counter - 1) & (kLossHistory - 1)] = L;
     }
   }
-  const int p = blockIdx.x * PARAM_THREADS + tid;
-  if (p >= NP) return;
-  // dL/dp = sum over rows, in row order, of (delta of the output unit) x (input value)
-  const float* da;
+  const int lane = tid & 31, slice = tid >> 5;
+  const int p = blockIdx.x * 32 + lane;
+  __shared__ float part[PARAM_SLICES][32];
+  // dL/dp = sum over rows of (delta of the output unit) x (input value): warp `slice` sums
+  // rows slice, slice + PARAM_SLICES, ... in order, lane l for parameter p
+  const float* da = nullptr;
   const float* xb = nullptr;
   int sa, ia, sb = 0, ib = 0;
   if (p < OFF_B1) {
@@ -248,11 +258,22 @@ __global__ void __launch_bounds__(PARAM_THREADS) mlp_param_kernel(
     da = rb.dy; sa = NO; ia = p - OFF_B3;
   }
   float g = 0.f;
-  if (xb) {
-    for (int r = 0; r < n; ++r) g = fmaf(da[(size_t)r * sa + ia], xb[(size_t)r * sb + ib], g);
-  } else {
-    for (int r = 0; r < n; ++r) g += da[(size_t)r * sa + ia];
+  if (p < NP) {
+    if (xb) {
+#pragma unroll 4
+      for (int r = slice; r < n; r += PARAM_SLICES)
+        g = fmaf(da[(size_t)r * sa + ia], xb[(size_t)r * sb + ib], g);
+    } else {
+#pragma unroll 4
+      for (int r = slice; r < n; r += PARAM_SLICES) g += da[(size_t)r * sa + ia];
+    }
   }
+  part[slice][lane] = g;
+  __syncthreads();
+  if (slice != 0 || p >= NP) return;
+  g = part[0][lane];
+#pragma unroll
+  for (int k = 1; k < PARAM_SLICES; ++k) g += part[k][lane];
   if (grad_out) grad_out[p] = g;
   if (mode != PARAM_ADAM) return;
   // Adam (Kingma & Ba 2015, Algorithm 1) on the FP32 master weight
@@ -361,7 +382,7 @@ int launch_rows(lbm_mlp* h, int mode, int n, double* y_out, long long* counter,
 int launch_update(lbm_mlp* h, const AdamArgs& a, cudaStream_t st) {
   int rc = launch_rows(h, ROWS_TRAIN, h->n, nullptr, h->counter, st);
   if (rc) return rc;
-  mlp_param_kernel<<<(NP + PARAM_THREADS - 1) / PARAM_THREADS, PARAM_THREADS, 0, st>>>(
+  mlp_param_kernel<<<PARAM_BLOCKS, PARAM_THREADS, 0, st>>>(
       h->rb, h->n, h->master, h->w, h->m1, h->m2, nullptr, a, PARAM_ADAM, h->counter,
       h->loss_hist, nullptr);
   MCK(h, cudaGetLastError());
@@ -595,7 +616,7 @@ int lbm_mlp_gradient(lbm_mlp* h, float* grad, float* loss) {
   MlpDeviceGuard guard(h);
   int rc = launch_rows(h, ROWS_TRAIN, h->n, nullptr, nullptr, h->stream);
   if (rc) return rc;
-  mlp_param_kernel<<<(NP + PARAM_THREADS - 1) / PARAM_THREADS, PARAM_THREADS, 0, h->stream>>>(
+  mlp_param_kernel<<<PARAM_BLOCKS, PARAM_THREADS, 0, h->stream>>>(
       h->rb, h->n, h->master, h->w, h->m1, h->m2, h->grad, AdamArgs{}, PARAM_GRAD, nullptr,
       nullptr, h->loss_one);
   MCK(h, cudaGetLastError());
