@@ -114,6 +114,8 @@ SIGNATURES = {
     "lbm_batch_instance_transposed": (c_int, [c_void_p, c_int]),
     "lbm_init_fields_async": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_persistent": (c_int, [c_void_p]),
+    "lbm_debug_persist_plan": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_int, c_int,
+                                       c_void_p, c_void_p, c_void_p]),
     "lbm_selftest_dep_timeout": (c_int, [c_void_p, c_int]),
     "lbm_batch_persistent": (c_int, [c_void_p]),
     "lbm_moments_async": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),

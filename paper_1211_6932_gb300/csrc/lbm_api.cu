@@ -527,6 +527,65 @@ void make_all_items(const Batch* b, std::vector<WorkItem>& out, std::vector<int>
 // (persist_items_ok), unless switched off (persist_env), and only when every item depends
 // on at most four chunks (chunks of two rows or more, but for a short last one); otherwise
 // steps are one launch per group each.
+// Persistent work lists of one launch group: `items` [lo, hi) (an instance's items
+// consecutive, chunk rows in order of `rows` rows each, `strips` items per chunk row) into
+// items2 / links2 (2 (hi - lo) entries: the even steps' list, then the odd steps', which
+// visits each instance's chunk rows from the middle one on).  Chunk ids count from 0 over
+// the group's instances; *n_chunks receives their number, rowwork (may be NULL) the rows
+// the group's items load.  False if an item would depend on more than four chunks (chunks
+// of one row): the group then cannot step persistently.  Host code only.
+bool plan_persist_group(const std::vector<WorkItem>& items, int lo, int hi,
+                        const std::vector<InstParams>& inst, int rows, WorkItem* items2,
+                        ItemLink* links2, int* n_chunks, double* rowwork) {
+  const int ng = hi - lo;
+  int chunk0 = 0;  // id of the first chunk of the current instance
+  double work = 0.0;
+  for (int k = lo; k < hi;) {
+    const int i = items[k].inst;
+    const InstParams& P = inst[i];
+    int e = k, strips = 0;
+    while (e < hi && items[e].inst == i) ++e;
+    while (k + strips < e && items[k + strips].y0 == items[k].y0) ++strips;
+    const int nch = (e - k) / strips;
+    if (nch * strips != e - k) return false;
+    for (int c = 0; c < nch; ++c) {
+      const int co = (c + nch / 2) % nch;  // the odd steps' c-th chunk row
+      for (int sx = 0; sx < strips; ++sx) {
+        const int pos = k + c * strips + sx - lo;
+        for (int par = 0; par < 2; ++par) {
+          const int cc = par ? co : c;
+          const WorkItem& w = items[k + cc * strips + sx];
+          ItemLink ln{};
+          ln.chunk = chunk0 + cc;
+          ln.strips = strips;
+          int nd = 0;
+          // the chunks holding the rows it reads: its own and two beyond each end
+          // (wrapped, or clamped at walls); by symmetry also those that read its rows
+          for (int r = w.y0 - 2; r <= w.y1 + 1; ++r) {
+            const int rr = P.walls ? std::min(std::max(r, 0), P.ny - 1)
+                                   : ((r % P.ny) + P.ny) % P.ny;
+            const int d = chunk0 + std::min(rr / rows, nch - 1);
+            bool seen = false;
+            for (int j = 0; j < nd; ++j) seen |= ln.dep[j] == d;
+            if (seen) continue;
+            if (nd == 4) return false;
+            ln.dep[nd++] = d;
+          }
+          for (int j = nd; j < 4; ++j) ln.dep[j] = ln.dep[0];
+          items2[(size_t)par * ng + pos] = w;
+          links2[(size_t)par * ng + pos] = ln;
+        }
+        work += items[k + c * strips + sx].y1 - items[k + c * strips + sx].y0 + 4;
+      }
+    }
+    chunk0 += nch;
+    k = e;
+  }
+  *n_chunks = chunk0;
+  if (rowwork) *rowwork = work;
+  return true;
+}
+
 int build_persist(Batch* b) {
   b->persist = false;
   if (!persist_allowed(b) || b->n_items == 0 || b->n_groups != 1 ||
@@ -538,51 +597,14 @@ int build_persist(Batch* b) {
   std::vector<double> work(b->n_groups, 0.0);
   int sync = 0;
   for (int g = 0; g < b->n_groups; ++g) {
-    const int lo = b->grp_begin[g], hi = b->grp_begin[g + 1], ng = hi - lo;
+    const int lo = b->grp_begin[g], hi = b->grp_begin[g + 1];
     b->grp_sync[g] = sync++;  // the queue counter, then the group's chunk counters
-    int chunk0 = 0;           // local id of the first chunk of the current instance
-    for (int k = lo; k < hi;) {
-      // an instance's items are consecutive: chunk rows in order, each `strips` items
-      const int i = b->items[k].inst;
-      const InstParams& P = b->inst[i];
-      int e = k, strips = 0;
-      while (e < hi && b->items[e].inst == i) ++e;
-      while (k + strips < e && b->items[k + strips].y0 == b->items[k].y0) ++strips;
-      const int nch = (e - k) / strips;
-      if (nch * strips != e - k) return LBM_OK;
-      for (int c = 0; c < nch; ++c) {
-        const int co = (c + nch / 2) % nch;  // the odd steps' c-th chunk row
-        for (int sx = 0; sx < strips; ++sx) {
-          const int pos = k + c * strips + sx - lo;
-          for (int par = 0; par < 2; ++par) {
-            const int cc = par ? co : c;
-            const WorkItem& w = b->items[k + cc * strips + sx];
-            ItemLink ln{};
-            ln.chunk = chunk0 + cc;
-            ln.strips = strips;
-            int nd = 0;
-            for (int r = w.y0 - 2; r <= w.y1 + 1; ++r) {
-              const int rr = P.walls ? std::min(std::max(r, 0), P.ny - 1)
-                                     : ((r % P.ny) + P.ny) % P.ny;
-              const int d = chunk0 + std::min(rr / b->rows, nch - 1);
-              bool seen = false;
-              for (int j = 0; j < nd; ++j) seen |= ln.dep[j] == d;
-              if (seen) continue;
-              if (nd == 4) return LBM_OK;  // too many dependencies: no persistent stepping
-              ln.dep[nd++] = d;
-            }
-            for (int j = nd; j < 4; ++j) ln.dep[j] = ln.dep[0];
-            items2[2 * (size_t)lo + (size_t)par * ng + pos] = w;
-            links2[2 * (size_t)lo + (size_t)par * ng + pos] = ln;
-          }
-          work[g] += (double)(b->items[k + c * strips + sx].y1 - b->items[k + c * strips + sx].y0 +
-                              4) * (2 * b->grp_nt[g] + kRowFixedCols);
-        }
-      }
-      chunk0 += nch;
-      sync += nch;
-      k = e;
-    }
+    int nch = 0;
+    if (!plan_persist_group(b->items, lo, hi, b->inst, b->rows, items2.data() + 2 * (size_t)lo,
+                            links2.data() + 2 * (size_t)lo, &nch, &work[g]))
+      return LBM_OK;  // too many dependencies: no persistent stepping
+    work[g] *= 2 * b->grp_nt[g] + kRowFixedCols;
+    sync += nch;
   }
   b->grp_sync[b->n_groups] = sync;
   double total = 0.0;
@@ -2379,6 +2401,44 @@ int lbm_batch_active(const lbm_batch* b) {
   int n = 0;
   for (int a : b->b.active) n += a;
   return n;
+}
+
+int lbm_debug_persist_plan(int n_inst, const int* nx, const int* ny, const int* walls,
+                           int threads, int rows, int* n_items, int* items_out,
+                           int* links_out) {
+  if (n_inst < 1 || !nx || !ny || !n_items || rows < 1) return LBM_EINVAL;
+  if (threads != 32 && threads != 64 && threads != 96 && threads != 128) return LBM_EINVAL;
+  std::vector<InstParams> inst(n_inst);
+  std::vector<WorkItem> items;
+  for (int i = 0; i < n_inst; ++i) {
+    if (nx[i] < 1 || ny[i] < 1) return LBM_EINVAL;
+    std::memset(&inst[i], 0, sizeof(InstParams));
+    inst[i].nx = nx[i];
+    inst[i].ny = ny[i];
+    inst[i].walls = walls && walls[i] ? 1 : 0;
+    append_items(inst[i], i, threads, 2, rows, items);
+  }
+  const int n = (int)items.size();
+  *n_items = n;
+  std::vector<WorkItem> items2(2 * (size_t)n);
+  std::vector<ItemLink> links2(2 * (size_t)n);
+  int nch = 0;
+  if (!plan_persist_group(items, 0, n, inst, rows, items2.data(), links2.data(), &nch,
+                          nullptr))
+    return 1;
+  for (int k = 0; k < 2 * n; ++k) {
+    if (items_out) {
+      const WorkItem& w = items2[k];
+      const int v[5] = {w.inst, w.x0, w.y0, w.y1, w.dir};
+      std::memcpy(items_out + 5 * (size_t)k, v, sizeof v);
+    }
+    if (links_out) {
+      const ItemLink& l = links2[k];
+      const int v[6] = {l.chunk, l.strips, l.dep[0], l.dep[1], l.dep[2], l.dep[3]};
+      std::memcpy(links_out + 6 * (size_t)k, v, sizeof v);
+    }
+  }
+  return LBM_OK;
 }
 
 int lbm_persistent(const lbm_handle* h) { return h ? (h->b.persist ? 1 : 0) : LBM_EINVAL; }
