@@ -989,6 +989,68 @@ def warm_start_ab(stream):
     }
 
 
+def network_gemms():
+    """The warm-start network's training update against the tensor-core route: device time
+    of cuBLAS bf16 products (torch.matmul) of the update's eight shapes, each replayed 100
+    times from a CUDA graph (10 replays timed with CUDA events on the replay stream), and
+    the library's fused update (4000 updates of one network on 256 rows).  One JSON line."""
+    import numpy as np
+    import torch
+
+    from paper_1211_6932_gb300 import workloads as wl
+    from paper_1211_6932_gb300.mlp import Mlp
+    rows, ni, nh, no = 256, 4, 64, 5
+    shapes = [("forward", rows, ni, nh), ("forward", rows, nh, nh), ("forward", rows, nh, no),
+              ("weight gradient", no, rows, nh), ("input gradient", rows, no, nh),
+              ("weight gradient", nh, rows, nh), ("input gradient", rows, nh, nh),
+              ("weight gradient", nh, rows, ni)]
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.Stream(device=dev)
+    products = []
+    for kind, m, k, n in shapes:
+        a = torch.randn(m, k, device=dev, dtype=torch.bfloat16)
+        b = torch.randn(k, n, device=dev, dtype=torch.bfloat16)
+        c = torch.empty(m, n, device=dev, dtype=torch.bfloat16)
+        with torch.cuda.stream(st):
+            for _ in range(3):
+                torch.matmul(a, b, out=c)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            for _ in range(100):
+                torch.matmul(a, b, out=c)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            g.replay()
+            e0.record()
+            for _ in range(10):
+                g.replay()
+            e1.record()
+        torch.cuda.synchronize()
+        products.append({"product": "%s %dx%dx%d" % (kind, m, k, n),
+                         "us": e0.elapsed_time(e1) * 1e3 / 1000})
+    rng = np.random.default_rng(0)
+    x, y = rng.uniform(size=(rows, ni)), rng.normal(size=(rows, no))
+    net = Mlp(wl.mlp_init(0), max_rows=4096)
+    try:
+        net.fit_scaling(x, y)
+        net.set_data(x, y)
+        net.train(100, lr=1e-3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        net.train(4000, lr=1e-3)
+        torch.cuda.synchronize()
+        update_us = (time.perf_counter() - t0) / 4000 * 1e6
+    finally:
+        net.close()
+    print(json.dumps({"metric": "warm-start network update against cuBLAS bf16 products",
+                      "products": products,
+                      "products_sum_us": sum(p["us"] for p in products),
+                      "fused_update_us": update_us}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1016,6 +1078,9 @@ def main():
                     help="fp32 (default; the headline) or fp64 (the parity mode)")
     ap.add_argument("--grid", type=int, default=4096,
                     help="square grid side (default 4096; smaller grids for profiling)")
+    ap.add_argument("--network-gemms", action="store_true",
+                    help="only time the warm-start network's update against cuBLAS bf16 "
+                         "products of its shapes (one JSON line)")
     args = ap.parse_args()
     global NX, NY, PREC, BATCH_SCREEN
     NX = NY = args.grid
@@ -1023,6 +1088,8 @@ def main():
     BATCH_SCREEN = args.batch_screen
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.network_gemms:
+        return network_gemms()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch256":
