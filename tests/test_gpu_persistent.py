@@ -100,3 +100,36 @@ def test_persistent_batch_equals_per_step_launches():
         for x, y in zip(a, b):
             for i in range(len(cs)):
                 assert np.array_equal(x[i], y[i]), i
+
+
+def test_long_persistent_run_on_the_field_equals_per_step_launches():
+    """Stress test of the cross-step pipeline: the 4096^2 field of 64 droplets (the bench's
+    recipe) stepped 10^4 times persistently (its default, 2176 items per step on 760 CTAs)
+    and with one launch per step ends in the same populations bit for bit."""
+    from paper_1211_6932_gb300 import Eos, Lattice, maxwell
+    from paper_1211_6932_gb300 import workloads as wl
+    a = 0.25
+    eos = Eos(a=a, T=0.6 * wl.t_crit(a))
+    rl, rv = maxwell(eos)
+    rho, _, _ = wl.multi_droplets(4096, 4096, rl, rv, 4.0, 64, 40.0, 200.0, seed=5)
+
+    def run(persistent):
+        old = os.environ.get("LBM_PERSISTENT")
+        os.environ["LBM_PERSISTENT"] = "1" if persistent else "0"
+        try:
+            L = Lattice(4096, 4096, eos, sigma=0.114, nu_l=0.05, nu_v=0.5, visc_mode="linear",
+                        precision="fp32")
+        finally:
+            if old is None:
+                del os.environ["LBM_PERSISTENT"]
+            else:
+                os.environ["LBM_PERSISTENT"] = old
+        with L:
+            assert L.persistent == persistent
+            L.init_fields(rho)
+            L.step(10000)
+            return L.moments(dtype=np.float32)["rho"], L.get_populations()
+    rp, fp = run(True)
+    rq, fq = run(False)
+    assert np.isfinite(rp).all()
+    assert np.array_equal(rp, rq) and np.array_equal(fp, fq)
