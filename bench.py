@@ -166,16 +166,18 @@ def step_launches(n, groups, persistent):
     return groups * n
 
 
-def load_traffic(n_nodes, block_size, profile="sweep2_kernel_fp32.md", tile=None):
+def load_traffic(n_nodes, block_size, profile="sweep2_kernel_fp32.md", tile=None,
+                 stepping=None):
     """DRAM bytes per step from a committed ncu summary of the step kernel, scaled to
-    n_nodes, or None when the kernel source, its block size or (for a batch) its tiling
-    has changed since that capture."""
+    n_nodes, or None when the kernel source, its block size, (for a batch) its tiling or
+    the way it steps ("persistent" or "per-step") has changed since that capture."""
     path = os.path.join(ROOT, "profiles", profile)
     vals = {}
     try:
         with open(path) as fh:
             for line in fh:
-                for key in ("kernel_hash", "block_size", "tile", "dram_bytes_per_node"):
+                for key in ("kernel_hash", "block_size", "tile", "stepping",
+                            "dram_bytes_per_node"):
                     if line.strip().startswith(key + ":"):
                         vals[key] = line.split(":", 1)[1].strip().strip("`")
     except OSError:
@@ -185,6 +187,8 @@ def load_traffic(n_nodes, block_size, profile="sweep2_kernel_fp32.md", tile=None
     if vals.get("block_size") != str(block_size):
         return None
     if tile is not None and vals.get("tile") != tile:
+        return None
+    if stepping is not None and vals.get("stepping") != stepping:
         return None
     return float(vals["dram_bytes_per_node"]) * n_nodes
 
@@ -398,7 +402,8 @@ def run_batch(args):
     peak, peak_kind = load_peak()
     avg = step_ms / K
     achieved = BYTES_PER_LU * n_nodes / (avg * 1e-3) / 1e9
-    traffic = (load_traffic(n_nodes, nt, "sweep2_kernel_batch256.md", "%d,%d,%d" % (nt, vec, rows))
+    traffic = (load_traffic(n_nodes, nt, "sweep2_kernel_batch256.md", "%d,%d,%d" % (nt, vec, rows),
+                            "persistent" if b.persistent else "per-step")
                if nt > 0 else None)
     if rank == 0:
         line = {"metric": "MLUPS (D2Q9 MRT-pseudopotential step, 256-instance batch, FP32)",
@@ -422,7 +427,8 @@ def run_batch(args):
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
                              "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                              "traffic_scope": "per step (every launch of one step)",
-                             "peak_source": peak_kind, "avg_step_ms": avg},
+                             "peak_source": peak_kind, "avg_step_ms": avg,
+                             "persistent": b.persistent},
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     b.close()
@@ -530,7 +536,8 @@ def run_gpu(args):
     bytes_lu = BYTES_PER_LU * (2 if PREC == "fp64" else 1)
     achieved = bytes_lu * n_nodes / (avg_launch_ms * 1e-3) / 1e9
     nt, vec, rows = L.tiling
-    traffic = load_traffic(n_nodes, nt) if vec == 2 and PREC == "fp32" else None
+    traffic = (load_traffic(n_nodes, nt, stepping="persistent" if persistent else "per-step")
+               if vec == 2 and PREC == "fp32" else None)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K,

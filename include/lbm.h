@@ -185,15 +185,17 @@ int lbm_step(lbm_handle* h, int n);
 
 /*
  * Persistent stepping (no counterpart in the paper).  With the FP32 pair kernel (tile_vec
- * 2), a run of up to 64 steps is one launch per launch group: resident CTAs take the
- * (step, chunk row, strip) work items in order from a queue, and an item waits (bounded;
- * LBM_ETIMEOUT if it runs out) only until the chunk rows whose previous step it reads, or
- * whose previous-step reads its stores would overwrite, are complete, so the CTAs of step
- * t + 1 start while step t finishes instead of the GPU draining between launches.  Results
- * equal the per-step launches bit for bit.  It is used with one launch group (one kernel
- * width and kind of strip), at least two waves of work items per step (with fewer, the
- * first items of a step would wait on the last ones of the step before), when every work
- * item depends on at most four chunk rows (chunks of two rows or more), and unless the
+ * 2), a run of up to 64 steps is one launch: resident CTAs take the (step, chunk row,
+ * strip) work items in order from a queue, and an item waits (bounded; LBM_ETIMEOUT if it
+ * runs out) only until the chunk rows whose previous step it reads, or whose previous-step
+ * reads its stores would overwrite, are complete, so the CTAs of step t + 1 start while
+ * step t finishes instead of the GPU draining between launches.  Results equal the
+ * per-step launches bit for bit.  It is used with one kernel width (a batch's instances
+ * swept in strips and those swept in full-width strips then share the launch, each work
+ * item taking the sweep of its instance), at least two waves of work items per step (with
+ * fewer, the first items of a step would wait on the last ones of the step before), when
+ * every work item depends on at most four chunk rows (chunks of two rows or more), unless the
+ * autotuner measured one launch per step faster for the tiling it chose, and unless the
  * environment sets LBM_PERSISTENT=0 when the work lists are built (creation, tiling
  * change, retirement); LBM_PERSISTENT=2 drops the two-wave condition (for tests).  With it
  * the default chunk height aims at about three waves of CTAs instead of six (taller
@@ -351,9 +353,12 @@ int lbm_set_tiling(lbm_handle* h, int threads, int vec, int rows);
  * 28, 32, 40, 48 and 64 rows is timed twice (the better time counts) over `steps` steps, rounded
  * up to even, stepped as lbm_step steps them (graph replays for each 64; CUDA events on
  * the handle's stream) on a saved copy of the state, which is restored afterwards (state and
- * step count are unchanged).  The fastest is kept.  cache_path (may be NULL) names a text
- * file of earlier choices keyed by precision, lattice sizes and GPU; a hit skips the
- * timing, a miss appends the new choice.  The chosen values are returned through the
+ * step count are unchanged); a tiling that steps persistently (lbm_persistent) is timed
+ * that way and again with one launch per step.  The fastest is kept, with its stepping
+ * (a later lbm_set_tiling returns to the default rule).  cache_path (may be NULL) names a
+ * text file of earlier choices keyed by precision, lattice sizes and GPU, one line each
+ * (key, threads, vec, rows, ms per step, 1 if persistent stepping is allowed); a hit skips
+ * the timing, a miss appends the new choice.  The chosen values are returned through the
  * optional out pointers (ms_per_step: the measured time of the choice, or the cached one).
  * The environment variable LBM_TILE="threads,vec,rows", when set, overrides everything.
  */
@@ -498,11 +503,11 @@ int lbm_batch_autotune(lbm_batch* b, int steps, const char* cache_path, int* thr
                        int* vec, int* rows, double* ms_per_step);
 /* Tiling in use by a batch (threads is LBM_TILE_PER_INSTANCE for per-instance widths). */
 int lbm_batch_get_tiling(const lbm_batch* b, int* threads, int* vec, int* rows);
-/* Launch groups of lbm_batch_step (0 when nothing is active): one per kernel width in use
- * (several only with LBM_TILE_PER_INSTANCE) and kind of strip (full-width strips for
- * instances of at most 2 * threads columns, strips for wider ones; pair kernel only).
- * Each group is one step-kernel launch per step, or per run of up to 64 steps when the
- * batch steps persistently (lbm_batch_persistent). */
+/* Step-kernel launches of lbm_batch_step per step (0 when nothing is active): one per
+ * launch group, that is per kernel width in use (several only with LBM_TILE_PER_INSTANCE)
+ * and kind of strip (full-width strips for instances of at most 2 * threads columns,
+ * strips for wider ones; pair kernel only); 1 when the batch steps persistently
+ * (lbm_batch_persistent), every group then sharing one launch per run of up to 64 steps. */
 int lbm_batch_launches_per_step(const lbm_batch* b);
 /* Persistent stepping of a batch (see lbm_persistent). */
 int lbm_batch_persistent(const lbm_batch* b);

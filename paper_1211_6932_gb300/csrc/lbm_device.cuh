@@ -856,11 +856,13 @@ struct NoHook {
 };
 
 // One work item of the pair kernel (a strip of rows [y0, y1) of one instance), the body of
-// sweep2_kernel and sweep2_persist_kernel.  FULL selects the full-width strip at compile
-// time (its own instantiation, so that the strip-mode code keeps constant load offsets).
+// sweep2_kernel and sweep2_persist_kernel.  FULL selects the full-width strip (1) or the
+// strip (0) at compile time (its own instantiation, so that the strip-mode code keeps
+// constant load offsets), or (2) per item: full-width if the instance's rows fit one strip
+// (nx <= 2 NT), for a work list of both kinds in one kernel.
 // Returns true if a bounded wait ran out: the CTA has then waited for its copies in flight
 // and set STATUS_TIMEOUT.  `part` indexes the diagnostics partials (MODE_MOMENTS).
-template <int NT, int MODE, bool FULL, typename Hook>
+template <int NT, int MODE, int FULL, typename Hook>
 __device__ __forceinline__ bool sweep2_item(const float* __restrict__ fin,
                                             float* __restrict__ fout, const InstParams& P,
                                             const WorkItem& it, const MomArgs<float>& mo,
@@ -868,7 +870,7 @@ __device__ __forceinline__ bool sweep2_item(const float* __restrict__ fin,
   typedef Sweep2Cfg<NT> C;
   typedef Num<float2> N;
   constexpr int WO = C::WO, SEG = C::SEG, NB = C::NBAR;
-  constexpr int PSW = FULL ? C::PSW : C::PSW_STRIP;
+  constexpr int PSW = FULL == 0 ? C::PSW_STRIP : C::PSW;
   constexpr int DA = C::DA, DC = C::DC, DB = C::DB, RING = C::PLANE_ROWS * SEG;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
@@ -894,7 +896,7 @@ __device__ __forceinline__ bool sweep2_item(const float* __restrict__ fin,
   // edge columns are read across the row in shared memory, and the ghost columns are
   // neither read nor written.  Otherwise threads 1 .. NT-2 own WO columns from x0 and
   // threads 0 and NT-1 evaluate psi of the halo columns.
-  constexpr bool full = FULL;
+  const bool full = FULL == 2 ? nx <= 2 * NT : FULL == 1;
   const int c0 = full ? 2 * tid : 2 * tid - 2;  // first CTA column of this thread
   const int xa = x0 + c0;                 // its global column (xa, xa + 1)
   const int xend = full ? nx : min(x0 + WO, nx);
@@ -1362,7 +1364,7 @@ struct PersistHook {
   }
 };
 
-// Persistent pair kernel for `steps` time steps of one launch group (STEP mode): the CTAs
+// Persistent pair kernel for `steps` time steps of one work list (STEP mode): the CTAs
 // take work items in order from *queue, item q being step t = q / n_items, entry
 // k = q - t n_items of that step's list (items2 and links2 hold the even steps' list, then
 // the odd steps', which visits each instance's chunks starting from the middle, so that
@@ -1377,8 +1379,13 @@ struct PersistHook {
 // comes after its current one), its dependencies are finished and released, so every
 // wait ends unless a CTA gives up; a CTA that gives up sets STATUS_TIMEOUT and returns,
 // and the CTAs waiting on it give up in turn.  dep_limit bounds each dependency wait
-// (DEP_WAIT_LIMIT; a failure-detection self-test passes a short one).
-template <int NT, bool FULL>
+// (DEP_WAIT_LIMIT; a failure-detection self-test passes a short one).  KIND selects the
+// item body: PERSIST_STRIP or PERSIST_FULL for a group of one kind of strip, PERSIST_MIXED
+// for a list holding both kinds (a batch of narrow and wide instances, one queue), where
+// each item takes the full-width body if its instance's rows fit one strip (nx <= 2 NT).
+constexpr int PERSIST_STRIP = 0, PERSIST_FULL = 1, PERSIST_MIXED = 2;
+
+template <int NT, int KIND>
 __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_persist_kernel(
     float* slab0, float* slab1, const InstParams* __restrict__ insts,
     const WorkItem* __restrict__ items2, const ItemLink* __restrict__ links2, int n_items,
@@ -1419,9 +1426,11 @@ __global__ void __launch_bounds__(NT, sweep2_min_blocks(NT)) sweep2_persist_kern
     if (q >= total || s_stop) return;
     const int t = q / n_items, k = q - t * n_items, par = t & 1;
     const WorkItem it = items2[par * n_items + k];
-    if (sweep2_item<NT, MODE_STEP, FULL>(par ? slab1 : slab0, par ? slab0 : slab1,
-                                         insts[it.inst], it, mo, status, 0, h))
-      return;
+    const InstParams& P = insts[it.inst];
+    float* fin = par ? slab1 : slab0;
+    float* fout = par ? slab0 : slab1;
+    constexpr int body = KIND == PERSIST_MIXED ? 2 : KIND == PERSIST_FULL ? 1 : 0;
+    if (sweep2_item<NT, MODE_STEP, body>(fin, fout, P, it, mo, status, 0, h)) return;
     __syncthreads();  // every thread's stores of the item precede its release
     if (threadIdx.x == 0) ps.release = links2[par * n_items + k].chunk;
   }

@@ -61,16 +61,17 @@ cudaError_t launch_pressure(const S* rho, const InstParams& P, double sigma, dou
                             double* pyy, double* pxy, cudaStream_t st);
 
 // FP32 pair kernel in its persistent form (sweep2_persist_kernel): `steps` time steps of
-// one launch group, from slab0 (step 0 reads it) and slab1, with `grid` CTAs.  items2 and
-// links2 hold 2 n_items entries (the even steps' list, then the odd steps'); queue (one int)
-// and done (one int per chunk) must be zero at launch; dep_limit bounds each dependency
-// wait (DEP_WAIT_LIMIT).
-cudaError_t launch_persist(int nt, int full, float* slab0, float* slab1,
+// one work list, from slab0 (step 0 reads it) and slab1, with `grid` CTAs.  kind is
+// PERSIST_STRIP or PERSIST_FULL (every item of that kind of strip) or PERSIST_MIXED (each
+// item's kind from its instance's width).  items2 and links2 hold 2 n_items entries (the
+// even steps' list, then the odd steps'); queue (one int) and done (one int per chunk)
+// must be zero at launch; dep_limit bounds each dependency wait (DEP_WAIT_LIMIT).
+cudaError_t launch_persist(int nt, int kind, float* slab0, float* slab1,
                            const InstParams* d_inst, const WorkItem* items2,
                            const ItemLink* links2, int n_items, int steps, int* queue,
                            int* done, int* d_status, int grid, int dep_limit, cudaStream_t st);
-// Resident CTAs per SM of the persistent pair kernel of width nt (at least 1).
-int persist_occupancy(int nt, int full);
+// Resident CTAs per SM of the persistent pair kernel of width nt and that kind (at least 1).
+int persist_occupancy(int nt, int kind);
 
 // Status bit of an asynchronous initialisation whose fields failed the validity check
 // (host-side status only; distinct from the kernels' STATUS_* bits).

@@ -17,32 +17,39 @@ cudaError_t launch_sweep<float>(int nt, int vec, int mode, int full, const float
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_persist(int nt, int full, float* slab0, float* slab1,
+cudaError_t launch_persist(int nt, int kind, float* slab0, float* slab1,
                            const InstParams* d_inst, const WorkItem* items2,
                            const ItemLink* links2, int n_items, int steps, int* queue,
                            int* done, int* d_status, int grid, int dep_limit,
                            cudaStream_t st) {
-#define LBM_PERSIST(T)                                                                       \
-  if (nt == T)                                                                               \
-    return full ? launch_persist2_cfg<T, true>(slab0, slab1, d_inst, items2, links2, n_items, \
-                                               steps, queue, done, d_status, grid, dep_limit, \
-                                               st)                                           \
-                : launch_persist2_cfg<T, false>(slab0, slab1, d_inst, items2, links2,        \
-                                                n_items, steps, queue, done, d_status, grid, \
-                                                dep_limit, st);
+#define LBM_PERSIST_KIND(T, K)                                                             \
+  if (nt == T && kind == K)                                                                \
+    return launch_persist2_cfg<T, K>(slab0, slab1, d_inst, items2, links2, n_items, steps, \
+                                     queue, done, d_status, grid, dep_limit, st);
+#define LBM_PERSIST(T)                  \
+  LBM_PERSIST_KIND(T, PERSIST_STRIP)    \
+  LBM_PERSIST_KIND(T, PERSIST_FULL)     \
+  LBM_PERSIST_KIND(T, PERSIST_MIXED)
   LBM_PERSIST(32)
   LBM_PERSIST(64)
   LBM_PERSIST(96)
   LBM_PERSIST(128)
 #undef LBM_PERSIST
+#undef LBM_PERSIST_KIND
   return cudaErrorInvalidValue;
 }
 
-int persist_occupancy(int nt, int full) {
-  if (nt == 32) return full ? persist_occupancy_cfg<32, true>() : persist_occupancy_cfg<32, false>();
-  if (nt == 64) return full ? persist_occupancy_cfg<64, true>() : persist_occupancy_cfg<64, false>();
-  if (nt == 96) return full ? persist_occupancy_cfg<96, true>() : persist_occupancy_cfg<96, false>();
-  if (nt == 128) return full ? persist_occupancy_cfg<128, true>() : persist_occupancy_cfg<128, false>();
+int persist_occupancy(int nt, int kind) {
+#define LBM_PERSIST_OCC(T)                                                          \
+  if (nt == T)                                                                      \
+    return kind == PERSIST_MIXED  ? persist_occupancy_cfg<T, PERSIST_MIXED>()       \
+           : kind == PERSIST_FULL ? persist_occupancy_cfg<T, PERSIST_FULL>()        \
+                                  : persist_occupancy_cfg<T, PERSIST_STRIP>();
+  LBM_PERSIST_OCC(32)
+  LBM_PERSIST_OCC(64)
+  LBM_PERSIST_OCC(96)
+  LBM_PERSIST_OCC(128)
+#undef LBM_PERSIST_OCC
   return 1;
 }
 

@@ -80,7 +80,7 @@ static cudaError_t launch_sweep2_mode(int mode, int full, const float* fin, floa
 }
 
 // Persistent pair kernel (sweep2_persist_kernel) with `grid` CTAs.
-template <int NT, bool FULL>
+template <int NT, int KIND>
 static cudaError_t launch_persist2_cfg(float* slab0, float* slab1, const InstParams* d_inst,
                                        const WorkItem* items2, const ItemLink* links2,
                                        int n_items, int steps, int* queue, int* done,
@@ -88,23 +88,23 @@ static cudaError_t launch_persist2_cfg(float* slab0, float* slab1, const InstPar
                                        cudaStream_t st) {
   constexpr size_t smem = Sweep2Cfg<NT>::BYTES;
   static std::atomic<unsigned long long> flag{0};
-  cudaError_t e = ensure_smem_attr(sweep2_persist_kernel<NT, FULL>, smem, flag);
+  cudaError_t e = ensure_smem_attr(sweep2_persist_kernel<NT, KIND>, smem, flag);
   if (e != cudaSuccess) return e;
   if (n_items <= 0 || steps <= 0 || grid <= 0) return cudaSuccess;
-  sweep2_persist_kernel<NT, FULL><<<grid, NT, smem, st>>>(slab0, slab1, d_inst, items2, links2,
+  sweep2_persist_kernel<NT, KIND><<<grid, NT, smem, st>>>(slab0, slab1, d_inst, items2, links2,
                                                           n_items, steps, queue, done,
                                                           d_status, dep_limit);
   return cudaGetLastError();
 }
 
-template <int NT, bool FULL>
+template <int NT, int KIND>
 static int persist_occupancy_cfg() {
   constexpr size_t smem = Sweep2Cfg<NT>::BYTES;
-  cudaFuncSetAttribute(sweep2_persist_kernel<NT, FULL>,
+  cudaFuncSetAttribute(sweep2_persist_kernel<NT, KIND>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int occ = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &occ, sweep2_persist_kernel<NT, FULL>, NT, smem);
+      &occ, sweep2_persist_kernel<NT, KIND>, NT, smem);
   return (e == cudaSuccess && occ > 0) ? occ : 1;
 }
 

@@ -296,3 +296,43 @@ def test_autotune_keeps_state_and_uses_cache(tmp_path):
         t2, v2, r2, ms2 = L2.autotune(steps=6, cache=cache)
         assert (t2, v2, r2) == (t, v, r) and abs(ms2 - ms) < 1e-5
     assert len(open(cache).read().strip().splitlines()) == 1
+
+
+def test_autotune_chooses_between_persistent_and_per_step_stepping(tmp_path):
+    """A tiling that steps persistently is timed that way and with one launch per step; the
+    faster is kept and cached (a sixth field, 1 if persistent stepping is allowed), a cache
+    hit restores it, an entry recording one launch per step as faster turns persistent
+    stepping off for its tiling, and an explicit tiling returns to the default rule."""
+    import os
+    c = pairs.case(600, 250, tr=0.7, sigma=0.114)
+    f = pairs.droplet_state(c, vel=0.01)
+    cache = os.path.join(tmp_path, "tiles.txt")
+    old = os.environ.get("LBM_PERSISTENT")
+    os.environ["LBM_PERSISTENT"] = "2"  # persistent wherever the dependency rule allows
+    try:
+        with pairs.gpu_lattice(c, "fp32") as L:
+            L.set_populations(f)
+            t, v, r, ms = L.autotune(steps=6, cache=cache)
+            key, *vals = open(cache).read().split()
+            assert len(vals) == 5 and vals[4] in ("0", "1")
+            if vals[4] == "0":
+                assert not L.persistent
+            assert L.tiling == (t, v, r)
+        out = []
+        for allow in ("1", "0"):
+            with open(cache, "a") as fh:
+                fh.write("%s 128 2 16 0.1 %s\n" % (key, allow))
+            with pairs.gpu_lattice(c, "fp32") as L2:
+                L2.set_populations(f)
+                assert L2.autotune(steps=6, cache=cache)[:3] == (128, 2, 16)
+                assert L2.persistent == (allow == "1")
+                L2.step(70)
+                out.append(L2.get_populations())
+                L2.set_tiling(128, 2, 16)
+                assert L2.persistent
+        assert np.array_equal(out[0], out[1])
+    finally:
+        if old is None:
+            del os.environ["LBM_PERSISTENT"]
+        else:
+            os.environ["LBM_PERSISTENT"] = old

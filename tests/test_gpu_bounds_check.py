@@ -77,7 +77,7 @@ SCRIPT = textwrap.dedent('''
 @pytest.mark.parametrize("persistent", ["0", "2"])
 def test_bounds_check_build_runs_clean(persistent):
     """Once with one launch per step, once with persistent stepping wherever the
-    dependency rule allows (LBM_PERSISTENT=2: every single-group FP32 pair tiling)."""
+    dependency rule allows (LBM_PERSISTENT=2: every FP32 pair tiling of one kernel width)."""
     from paper_1211_6932_gb300 import build
     build.build(check=True)
     env = dict(os.environ, LBM_LIBRARY="check", LBM_PERSISTENT=persistent)

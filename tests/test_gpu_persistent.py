@@ -3,8 +3,9 @@ launch group, CTAs taking (step, chunk row, strip) items from a queue and waitin
 the chunk rows of the previous step they depend on) gives the populations of one launch
 per step and group bit for bit: periodic and wall boundaries, strips and full-width
 strips, odd widths, ragged last chunks (down to one row), two-row chunks, graph replays
-and shorter runs, and a batch of one launch group (batches of several groups keep one
-launch per step and group)."""
+and shorter runs, batches of one launch group and of strips and full-width strips in one
+launch, and the 256-instance batch (per-instance widths keep one launch per step and
+group)."""
 import os
 
 import numpy as np
@@ -77,29 +78,73 @@ def test_default_rule_steps_large_lattices_persistently():
 
 
 def test_persistent_batch_equals_per_step_launches():
-    """A batch whose instances form one launch group (every instance swept in one
-    full-width 128-thread strip per row) steps persistently; a batch of several groups
-    (strips and full-width strips) keeps one launch per step and group.  Both give the
-    per-step populations bit for bit."""
+    """Batches whose instances share one kernel width step persistently: one launch group
+    (every instance swept in one full-width 128-thread strip per row), and strips and
+    full-width strips together (one launch, each item taking its instance's sweep); with
+    per-instance widths they keep one launch per step and group.  All give the per-step
+    populations bit for bit."""
     from paper_1211_6932_gb300 import Batch
+    from paper_1211_6932_gb300.lattice import TILE_PER_INSTANCE
     from tests.test_gpu_batch import CASES, instance, start_fields
-    for cs, single in ((CASES[:1] + CASES[2:3] + [pairs.case(200, 90, tr=0.75, sigma=0.114),
-                                                 pairs.case(130, 67, tr=0.8, sigma=0.11,
-                                                            walls=True)], True),
-                       (CASES + [pairs.case(400, 40, tr=0.75, sigma=0.114)], False)):
+    single = CASES[:1] + CASES[2:3] + [pairs.case(200, 90, tr=0.75, sigma=0.114),
+                                      pairs.case(130, 67, tr=0.8, sigma=0.11, walls=True)]
+    mixed = CASES + [pairs.case(400, 40, tr=0.75, sigma=0.114)]
+    for cs, threads, persistent in ((single, 0, True), (mixed, 0, True),
+                                    (mixed, TILE_PER_INSTANCE, False)):
         fields = [start_fields(c, 60 + i) for i, c in enumerate(cs)]
 
         def make():
-            b = Batch([instance(c) for c in cs], precision="fp32")
+            b = Batch([instance(c) for c in cs], precision="fp32", tile_threads=threads)
             for i, fl in enumerate(fields):
                 b.init_fields(i, *fl)
+            if b.persistent:
+                assert b.launches_per_step == 1
             return b
         mp, a = _run(make, True)
         mq, b = _run(make, False)
-        assert mp == single and not mq
+        assert mp == persistent and not mq
         for x, y in zip(a, b):
             for i in range(len(cs)):
                 assert np.array_equal(x[i], y[i]), i
+
+
+def test_batch_of_256_persistent_equals_per_step_launches():
+    """The 256-instance batch of ragged instances (sides 64 to 512; the instances that turn
+    non-finite within 10^4 steps screened out, as timed; strips and full-width strips in one
+    persistent launch at the default tiling) stepped 640 steps persistently and with one
+    launch per step and group ends in the same populations bit for bit."""
+    from paper_1211_6932_gb300 import Batch, batched
+    insts, fields, _ = batched.instances(256, seed=4)
+    bad = batched.screen(insts, fields, steps=10000)
+    insts = [x for i, x in enumerate(insts) if i not in bad]
+    fields = [x for i, x in enumerate(fields) if i not in bad]
+
+    def make(persistent):
+        old = os.environ.get("LBM_PERSISTENT")
+        os.environ["LBM_PERSISTENT"] = "1" if persistent else "0"
+        try:
+            b = Batch(insts, precision="fp32")
+        finally:
+            if old is None:
+                del os.environ["LBM_PERSISTENT"]
+            else:
+                os.environ["LBM_PERSISTENT"] = old
+        assert b.persistent == persistent
+        assert b.launches_per_step == (1 if persistent else 2)
+        for i, rho in enumerate(fields):
+            b.init_fields(i, rho)
+        b.step(640)
+        return b
+    bp = make(True)
+    try:
+        bq = make(False)
+        try:
+            for i in range(len(insts)):
+                assert np.array_equal(bp.get_populations(i), bq.get_populations(i)), i
+        finally:
+            bq.close()
+    finally:
+        bp.close()
 
 
 def test_long_persistent_run_on_the_field_equals_per_step_launches():
