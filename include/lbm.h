@@ -208,15 +208,16 @@ int lbm_persistent(const lbm_handle* h);
 /*
  * The persistent work lists, for tests of the schedule (host code only; no device is
  * used): the step items of n_inst periodic (walls[i] == 0 or walls NULL) or walled
- * instances of nx[i] x ny[i] nodes, swept as one launch group with `threads` (32, 64, 96
- * or 128) threads of two columns and chunks of `rows` rows, as lbm_step would list them
- * (strips of 2 threads - 4 columns, or one full-width strip per row where nx <= 2 threads,
- * ignoring that the kinds would be separate groups).  *n_items receives the items per
+ * instances of nx[i] x ny[i] nodes, swept with `threads` (32, 64, 96 or 128) threads of
+ * two columns and chunks of `rows` rows as one persistent work list (strips of
+ * 2 threads - 4 columns, or one full-width strip per row where nx <= 2 threads, both kinds
+ * in one list as in a batch's persistent launch; the library lists the strip instances
+ * first, this call keeps the given order).  *n_items receives the items per
  * step; items_out (may be NULL) receives 2 n_items items, the even steps' list then the
  * odd steps', as (instance, x0, y0, y1, sweep direction), and links_out (may be NULL)
  * 2 n_items dependency links as (chunk, strips of its chunk row, four dependency chunks).
- * Returns LBM_OK, 1 if an item would depend on more than four chunks (the group would not
- * step persistently; nothing is written), or LBM_EINVAL.
+ * Returns LBM_OK, 1 if an item would depend on more than four chunks (the instances would
+ * not step persistently; nothing is written), or LBM_EINVAL.
  */
 int lbm_debug_persist_plan(int n_inst, const int* nx, const int* ny, const int* walls,
                            int threads, int rows, int* n_items, int* items_out,

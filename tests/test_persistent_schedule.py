@@ -52,6 +52,8 @@ CASES = [
     ([(200, 64, 0)], 128, 2),             # full width, two-row chunks
     ([(40, 3, 0)], 128, 8),               # one chunk
     ([(200, 64, 0), (400, 40, 0), (130, 67, 1)], 128, 8),  # several instances
+    # strip instances, then full-width ones: one list, as a batch's persistent launch
+    ([(400, 40, 0), (300, 97, 1), (200, 64, 0), (64, 200, 0), (5, 3, 0)], 128, 12),
 ]
 
 
