@@ -320,11 +320,10 @@ int lbm_diagnostics(lbm_handle* h, lbm_diag* out);
  *            is neither read nor updated), count of non-finite nodes.
  * Queued on the handle's stream and not synchronised; nothing is allocated, neither on
  * the device nor on the host.  The first call on a device (and the first call after a
- * device reset, in the new context) looks up the array's device address, so make that
- * first call before any stream capture.  All calls in the process share the one array and
- * each call overwrites it (the part it uses is cleared first): calls whose work can
- * overlap on the GPU (other streams, other handles) race and must be serialised by the
- * caller.  Returns LBM_EINVAL, with nothing queued, if the lattice needs more work items
+ * device reset, in the new context) looks up the array's device address.  All calls in
+ * the process share the one array and each call overwrites it (the part it uses is
+ * cleared first): calls whose work can overlap on the GPU (other streams, other handles)
+ * race and must be serialised by the caller.  Returns LBM_EINVAL, with nothing queued, if the lattice needs more work items
  * than the array holds (see lbm_get_tiling; larger tiles need fewer items).
  */
 #define LBM_NOALLOC_MAX_ITEMS 16384
