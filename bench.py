@@ -357,7 +357,7 @@ def run_batch(args):
     for i, rho in enumerate(fields):
         b.init_fields(i, rho)
     nt, vec, rows, tuned_ms = b.autotune(steps=64)
-    per_step = b.launches_per_step  # one per kernel width under per-instance tiling
+    per_step = b.launches_per_step  # launch groups, or 1 stepping persistently
     for _ in range(args.warmup):
         b.step(1)
     b.step(64)

@@ -604,5 +604,7 @@ class Batch:
 
     @property
     def launches_per_step(self):
-        """Step-kernel launches per step (one per pair-kernel width in use)."""
+        """Step-kernel launches per step: one per launch group (kernel width and kind of
+        strip), or 1 when the batch steps persistently (one launch per run of up to 64
+        steps for all groups)."""
         return self._check(self._L.lbm_batch_launches_per_step(self._h))
