@@ -534,7 +534,7 @@ void make_all_items(const Batch* b, std::vector<WorkItem>& out, std::vector<int>
 // the instances of the range; *n_chunks receives their number, rowwork (may be NULL) the
 // rows its items load.  False if an item would depend on more than four chunks (chunks of
 // one row): the items then cannot step persistently.  Host code only.
-bool plan_persist_group(const std::vector<WorkItem>& items, int lo, int hi,
+bool plan_persist_list(const std::vector<WorkItem>& items, int lo, int hi,
                         const std::vector<InstParams>& inst, int rows, WorkItem* items2,
                         ItemLink* links2, int* n_chunks, double* rowwork) {
   const int ng = hi - lo;
@@ -597,7 +597,7 @@ int build_persist(Batch* b) {
   std::vector<WorkItem> items2(2 * (size_t)n);
   std::vector<ItemLink> links2(2 * (size_t)n);
   int nch = 0;
-  if (!plan_persist_group(b->items, 0, n, b->inst, b->rows, items2.data(), links2.data(), &nch,
+  if (!plan_persist_list(b->items, 0, n, b->inst, b->rows, items2.data(), links2.data(), &nch,
                           nullptr))
     return LBM_OK;  // too many dependencies: no persistent stepping
   const int sync = 1 + nch;  // the queue counter, then the chunk counters
@@ -2418,7 +2418,7 @@ int lbm_debug_persist_plan(int n_inst, const int* nx, const int* ny, const int* 
   std::vector<WorkItem> items2(2 * (size_t)n);
   std::vector<ItemLink> links2(2 * (size_t)n);
   int nch = 0;
-  if (!plan_persist_group(items, 0, n, inst, rows, items2.data(), links2.data(), &nch,
+  if (!plan_persist_list(items, 0, n, inst, rows, items2.data(), links2.data(), &nch,
                           nullptr))
     return 1;
   for (int k = 0; k < 2 * n; ++k) {
