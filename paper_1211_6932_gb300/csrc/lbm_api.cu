@@ -598,7 +598,7 @@ int build_persist(Batch* b) {
   std::vector<ItemLink> links2(2 * (size_t)n);
   int nch = 0;
   if (!plan_persist_list(b->items, 0, n, b->inst, b->rows, items2.data(), links2.data(), &nch,
-                          nullptr))
+                         nullptr))
     return LBM_OK;  // too many dependencies: no persistent stepping
   const int sync = 1 + nch;  // the queue counter, then the chunk counters
   b->persist_kind = kind;
@@ -2419,7 +2419,7 @@ int lbm_debug_persist_plan(int n_inst, const int* nx, const int* ny, const int* 
   std::vector<ItemLink> links2(2 * (size_t)n);
   int nch = 0;
   if (!plan_persist_list(items, 0, n, inst, rows, items2.data(), links2.data(), &nch,
-                          nullptr))
+                         nullptr))
     return 1;
   for (int k = 0; k < 2 * n; ++k) {
     if (items_out) {
