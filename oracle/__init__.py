@@ -14,6 +14,7 @@ Contents
 """
 import ctypes
 import dataclasses
+import os
 
 import numpy as np
 
@@ -73,10 +74,12 @@ class Params:
 
 
 def lib():
-    """Load (building first if needed) the oracle's shared object."""
+    """Load (building first if needed) the oracle's shared object.  LBM_ORACLE_LIB, when
+    set, names another build of it to load instead (the mutation check of the pins loads
+    altered copies this way)."""
     global _LIB
     if _LIB is None:
-        path = _build.build()
+        path = os.environ.get("LBM_ORACLE_LIB") or _build.build()
         L = ctypes.CDLL(path)
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int)

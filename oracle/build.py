@@ -13,15 +13,21 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbm_oracle.so")
 
 
+def compile_to(src: str, out: str) -> str:
+    """Compile one C source of the oracle into the shared object ``out``."""
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", src, "-o", out, "-lm"]
+    subprocess.run(cmd, check=True)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Build ``liblbm_oracle.so`` if it is missing or older than its source."""
     os.makedirs(OUT_DIR, exist_ok=True)
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-fno-fast-math", SRC, "-o", tmp, "-lm"]
-    subprocess.run(cmd, check=True)
+    compile_to(SRC, tmp)
     os.replace(tmp, LIB)
     return LIB
 
