@@ -1,11 +1,14 @@
 """Mutation check of the oracle's pins: each plausible mistake below (a dropped term, a
-wrong sign, a wrong weight or index, a transposed operand), written into a copy of the C
-oracle, must make the committed pins (tests/test_oracle_pins.py) fail.  Each altered copy
-is compiled into a temporary directory and loaded by a child pytest through
-LBM_ORACLE_LIB; the oracle's own source is never touched.  A control copy without any
-change must pass the same pins, so that a failure means the mistake was caught, not that
-the harness broke.  The two slowest pins (the Table II droplet run and Laplace's law) are
-left out of these runs to keep them short; every mistake is caught without them."""
+wrong sign, a wrong weight or index, a transposed operand), written into a copy of the
+oracle, must make the committed pins fail.  The C step (lbm_oracle.c) is altered in a
+copy compiled into a temporary directory and loaded by a child pytest through
+LBM_ORACLE_LIB; a Python module of the oracle (the pressure tensor of Eq. 18, the
+thermodynamics) is altered in a copy whose definitions a child process puts in place of
+the module's before it runs the pins.  The oracle's own sources are never touched.
+Control copies without any change must pass the same pins, so that a failure means the
+mistake was caught, not that the harness broke.  The two slowest pins (the Table II
+droplet run and Laplace's law) are left out of these runs to keep them short; every
+mistake is caught without them."""
 import os
 import subprocess
 import sys
@@ -60,11 +63,42 @@ MUTATIONS = [
 ]
 
 
+PIN_FILES = [os.path.join(ROOT, "tests", f) for f in ("test_oracle_pins.py",
+                                                     "test_pressure_oracle.py")]
+PYTEST_ARGS = PIN_FILES + ["-x", "-q", "-p", "no:cacheprovider", "-k", FAST]
+
+
 def _pins(lib_path):
     env = dict(os.environ, LBM_ORACLE_LIB=lib_path)
-    cmd = [sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-           "-x", "-q", "-p", "no:cacheprovider", "-k", FAST]
+    cmd = [sys.executable, "-m", "pytest"] + PYTEST_ARGS
     return subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True)
+
+
+# Child process for a Python module of the oracle: execute the altered copy as that module
+# (same package, so its relative imports resolve), put its definitions in place of the
+# module's, then run the pins in the same interpreter.
+RUNNER = """
+import importlib, sys, types
+import pytest
+name, path = sys.argv[1], sys.argv[2]
+real = importlib.import_module(name)
+alt = types.ModuleType(name)
+alt.__package__ = name.rpartition(".")[0]
+alt.__file__ = path
+with open(path) as fh:
+    exec(compile(fh.read(), path, "exec"), alt.__dict__)
+for k, v in list(alt.__dict__.items()):
+    if not k.startswith("__"):
+        setattr(real, k, v)
+sys.exit(pytest.main(sys.argv[3:]))
+"""
+
+
+def _pins_with_module(name, path):
+    # the module's own pins first, so that a caught mistake ends the run early
+    files = PIN_FILES[::-1] if name == "oracle.pressure" else PIN_FILES
+    cmd = [sys.executable, "-c", RUNNER, name, path] + files + PYTEST_ARGS[len(PIN_FILES):]
+    return subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True)
 
 
 def _compile(tmp_path, name, text):
@@ -72,6 +106,50 @@ def _compile(tmp_path, name, text):
     with open(src, "w") as fh:
         fh.write(text)
     return obuild.compile_to(src, os.path.join(tmp_path, name + ".so"))
+
+
+# (what the mistake is, the passage it breaks, module, text in its source, replacement)
+PY_MUTATIONS = [
+    ("pressure tensor with the diagonal weight 1/6", "Eqs. 7, 18", "oracle.pressure",
+     "_W = {1: 1.0 / 3.0, 2: 1.0 / 12.0}", "_W = {1: 1.0 / 3.0, 2: 1.0 / 6.0}"),
+    ("pressure tensor without the factor 1/2 of G", "Eq. 18", "oracle.pressure",
+     "half = 0.5 * G * psi", "half = G * psi"),
+    ("ideal-gas part rho/2 instead of rho c_s^2", "Eq. 18", "oracle.pressure",
+     "iso = rho / 3.0 + 2.0 * sigma", "iso = rho / 2.0 + 2.0 * sigma"),
+    ("sigma term with G instead of G^2", "Eq. 26", "oracle.pressure",
+     "2.0 * sigma * G * G * (gx * gx + gy * gy)", "2.0 * sigma * G * (gx * gx + gy * gy)"),
+    ("shear component from e_x e_x", "Eq. 18", "oracle.pressure",
+     "sxy += wp * ex * ey", "sxy += wp * ex * ex"),
+    ("surface tension over both interfaces instead of one", "Eq. 18", "oracle.pressure",
+     "return 0.5 * float(np.sum(", "return float(np.sum("),
+    ("CS compressibility factor without its cubic term", "Eq. 30", "oracle.thermo",
+     "return (1.0 + x + x * x - x ** 3) / (1.0 - x) ** 3", "return (1.0 + x + x * x) / (1.0 - x) ** 3"),
+    ("derivative of the CS numerator with a wrong coefficient", "Eq. 30", "oracle.thermo",
+     "N1 = 1.0 + 2.0 * x - 3.0 * x * x", "N1 = 1.0 + 2.0 * x - 2.0 * x * x"),
+    ("Maxwell rule weighted by 1/rho instead of 1/rho^2", "Eq. 22", "oracle.thermo",
+     "lambda r: 1.0 / (r * r)", "lambda r: 1.0 / r"),
+    ("epsilon of Eq. 29 with the wrong sign", "Eq. 29", "oracle.thermo",
+     "return -2.0 * (alpha + 24.0 * G * sigma) / beta", "return 2.0 * (alpha + 24.0 * G * sigma) / beta"),
+    ("mechanical-stability weight psi^(1 - eps) instead of psi^(1 + eps)", "Eq. 21",
+     "oracle.thermo", "** (1.0 + eps)", "** (1.0 - eps)"),
+    ("lattice sound speed squared 1/2", "Eq. 24", "oracle.thermo",
+     "CS2 = 1.0 / 3.0", "CS2 = 1.0 / 2.0"),
+    ("critical temperature without the factor 2", "Sec. IV A", "oracle.thermo",
+     "Tc = 2.0 * a / ((b / 4.0)", "Tc = a / ((b / 4.0)"),
+]
+
+
+def _module_source(name):
+    path = os.path.join(ROOT, *name.split(".")) + ".py"
+    with open(path) as fh:
+        return fh.read()
+
+
+def _write(tmp_path, name, text):
+    path = os.path.join(tmp_path, name.replace(".", "_") + ".py")
+    with open(path, "w") as fh:
+        fh.write(text)
+    return path
 
 
 @pytest.fixture(scope="module")
@@ -89,6 +167,21 @@ def test_unaltered_copy_passes_the_pins(source, tmp_path):
 def test_pins_catch_the_mistake(source, tmp_path, what, passage, old, new):
     assert source.count(old) == 1, "the text to alter must occur exactly once"
     r = _pins(_compile(str(tmp_path), "mutant", source.replace(old, new)))
+    assert r.returncode == 1, (what, passage, r.stdout[-2000:])
+
+
+@pytest.mark.parametrize("name", sorted({m[2] for m in PY_MUTATIONS}))
+def test_unaltered_module_copy_passes_the_pins(tmp_path, name):
+    r = _pins_with_module(name, _write(str(tmp_path), name, _module_source(name)))
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+
+
+@pytest.mark.parametrize("what,passage,name,old,new", PY_MUTATIONS,
+                         ids=[m[0] for m in PY_MUTATIONS])
+def test_pins_catch_the_mistake_in_a_module(tmp_path, what, passage, name, old, new):
+    text = _module_source(name)
+    assert text.count(old) == 1, "the text to alter must occur exactly once"
+    r = _pins_with_module(name, _write(str(tmp_path), name, text.replace(old, new)))
     assert r.returncode == 1, (what, passage, r.stdout[-2000:])
 
 

@@ -1,5 +1,6 @@
 """Pins of the discrete pressure tensor oracle (Eq. 18) against closed forms."""
 import numpy as np
+import pytest
 
 import oracle
 from oracle import pressure as op
@@ -73,3 +74,22 @@ def test_film_tensor_is_x_uniform_and_symmetric():
     assert np.allclose(qxx, pyy.T, rtol=1e-14) and np.allclose(qyy, pxx.T, rtol=1e-14)
     # bulk rows carry p_EOS; the interfaces carry a positive excess of P_n - P_t
     assert op.surface_tension_film(pxx, pyy) > 0
+
+
+def test_film_surface_tension_is_the_integral_over_one_interface():
+    """A constructed x-uniform film whose P_yy - P_xx is two Gaussian bumps of integral g0
+    each (one per interface; sampled at the nodes their sums equal g0 to rounding) gives
+    the per-interface tension g0; exchanging P_xx and P_yy flips its sign, and a part of
+    P_xx that varies in x with zero mean over x leaves it unchanged."""
+    import math
+    ny, nx, g0 = 64, 6, 0.0123
+    y = np.arange(ny, dtype=float)
+
+    def bump(y0, s=2.0):
+        return np.exp(-0.5 * ((y - y0) / s) ** 2) / (s * math.sqrt(2.0 * math.pi))
+    pxx = np.full((ny, nx), 0.05)
+    pyy = pxx + g0 * (bump(16.0) + bump(48.0))[:, None]
+    assert op.surface_tension_film(pxx, pyy) == pytest.approx(g0, rel=1e-12)
+    assert op.surface_tension_film(pyy, pxx) == pytest.approx(-g0, rel=1e-12)
+    wiggle = 1e-3 * np.cos(2.0 * np.pi * np.arange(nx) / nx)[None, :]
+    assert op.surface_tension_film(pxx + wiggle, pyy + wiggle) == pytest.approx(g0, rel=1e-12)
