@@ -3,8 +3,8 @@ wrong sign, a wrong weight or index, a transposed operand), written into a copy 
 oracle, must make the committed pins fail.  The C step (lbm_oracle.c) is altered in a
 copy compiled into a temporary directory and loaded by a child pytest through
 LBM_ORACLE_LIB; a Python module of the oracle (the pressure tensor of Eq. 18, the
-thermodynamics) is altered in a copy whose definitions a child process puts in place of
-the module's before it runs the pins.  The oracle's own sources are never touched.
+thermodynamics, the warm-start network and measurements) is altered in a copy whose
+definitions a child process puts in place of the module's before it runs its pins.  The oracle's own sources are never touched.
 Control copies without any change must pass the same pins, so that a failure means the
 mistake was caught, not that the harness broke.  The two slowest pins (the Table II
 droplet run and Laplace's law) are left out of these runs to keep them short; every
@@ -12,6 +12,7 @@ mistake is caught without them."""
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 import pytest
 
@@ -68,10 +69,19 @@ PIN_FILES = [os.path.join(ROOT, "tests", f) for f in ("test_oracle_pins.py",
 PYTEST_ARGS = PIN_FILES + ["-x", "-q", "-p", "no:cacheprovider", "-k", FAST]
 
 
+# The children run side by side, each with a share of the cores for the oracle's OpenMP.
+WORKERS = max(1, min(8, os.cpu_count() or 1))
+
+
+def _env(**extra):
+    threads = max(1, (os.cpu_count() or 1) // WORKERS)
+    return dict(os.environ, OMP_NUM_THREADS=str(threads), **extra)
+
+
 def _pins(lib_path):
-    env = dict(os.environ, LBM_ORACLE_LIB=lib_path)
     cmd = [sys.executable, "-m", "pytest"] + PYTEST_ARGS
-    return subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True)
+    return subprocess.run(cmd, cwd=ROOT, env=_env(LBM_ORACLE_LIB=lib_path),
+                          capture_output=True, text=True)
 
 
 # Child process for a Python module of the oracle: execute the altered copy as that module
@@ -94,11 +104,26 @@ sys.exit(pytest.main(sys.argv[3:]))
 """
 
 
+def _tests(*names):
+    return [os.path.join(ROOT, "tests", n) for n in names]
+
+
+# Each module's pins (its own first, so that a caught mistake ends the run early).  The
+# warm-start measurements' file also compares the library's host code with the oracle;
+# only the oracle's own pins (test_oracle_*) are run for them.
+MODULE_PINS = {
+    "oracle.pressure": (_tests("test_pressure_oracle.py", "test_oracle_pins.py"), FAST),
+    "oracle.thermo": (_tests("test_oracle_pins.py", "test_pressure_oracle.py"), FAST),
+    "oracle.mlp": (_tests("test_mlp_oracle.py"), None),
+    "oracle.warm": (_tests("test_warm_host.py"), "test_oracle_"),
+}
+
+
 def _pins_with_module(name, path):
-    # the module's own pins first, so that a caught mistake ends the run early
-    files = PIN_FILES[::-1] if name == "oracle.pressure" else PIN_FILES
-    cmd = [sys.executable, "-c", RUNNER, name, path] + files + PYTEST_ARGS[len(PIN_FILES):]
-    return subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True)
+    files, k = MODULE_PINS[name]
+    args = files + ["-x", "-q", "-p", "no:cacheprovider"] + (["-k", k] if k else [])
+    cmd = [sys.executable, "-c", RUNNER, name, path] + args
+    return subprocess.run(cmd, cwd=ROOT, env=_env(), capture_output=True, text=True)
 
 
 def _compile(tmp_path, name, text):
@@ -136,6 +161,40 @@ PY_MUTATIONS = [
      "CS2 = 1.0 / 3.0", "CS2 = 1.0 / 2.0"),
     ("critical temperature without the factor 2", "Sec. IV A", "oracle.thermo",
      "Tc = 2.0 * a / ((b / 4.0)", "Tc = a / ((b / 4.0)"),
+    ("GELU derivative without its z phi(z) term", "GELU", "oracle.mlp",
+     "return _phi_cdf(z) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)",
+     "return _phi_cdf(z)"),
+    ("normal CDF with the wrong sign of its argument", "GELU", "oracle.mlp",
+     "return 0.5 * _erfc(-z / math.sqrt(2.0))", "return 0.5 * _erfc(z / math.sqrt(2.0))"),
+    ("loss gradient without the factor 2", "squared error", "oracle.mlp",
+     "dy = 2.0 * (y - tn) / (n * N_OUT)", "dy = (y - tn) / (n * N_OUT)"),
+    ("gradient of the square hidden layer transposed", "chain rule", "oracle.mlp",
+     'g["W2"] = dz2.T @ c["h1"]', 'g["W2"] = (dz2.T @ c["h1"]).T'),
+    ("Adam without the bias correction of v", "Adam", "oracle.mlp",
+     "vhat = v / (1.0 - beta2 ** k)", "vhat = v"),
+    ("Adam first moment without the (1 - beta1) weight", "Adam", "oracle.mlp",
+     "m = beta1 * m + (1.0 - beta1) * g", "m = beta1 * m + g"),
+    ("bf16 rounding half up instead of to even", "bf16", "oracle.mlp",
+     "r = (b + np.uint64(0x7FFF) + lsb)", "r = (b + np.uint64(0x8000))"),
+    ("inputs multiplied by their scale instead of divided", "standardisation", "oracle.mlp",
+     '/ scaling["in_scale"]', '* scaling["in_scale"]'),
+    ("integral width with the factor 2 instead of 4", "Eq. 31", "oracle.warm",
+     "width = 4.0 * float(np.sum(g * (1.0 - g))) / 2.0",
+     "width = 2.0 * float(np.sum(g * (1.0 - g))) / 2.0"),
+    ("equimolar radius from the inner density alone", "Eq. 31", "oracle.warm",
+     "(math.pi * (ri - ro))", "(math.pi * ri)"),
+    ("Laplace coefficient divided by the radius", "Eq. 30", "oracle.warm",
+     "lap = (thermo.p_eos(ri, a, b, R, T) - thermo.p_eos(ro, a, b, R, T)) * Rg",
+     "lap = (thermo.p_eos(ri, a, b, R, T) - thermo.p_eos(ro, a, b, R, T)) / Rg"),
+    ("vapour law returning the slope without dividing by rho_v", "1/R law", "oracle.warm",
+     "return float(rv), float(s / rv)", "return float(rv), float(s)"),
+    ("liquid response taken at the vapour's compressibility", "Eq. 30", "oracle.warm",
+     'dp / thermo.dp_drho(p["rho_l"], a, b, R, T)', "dp / thermo.dp_drho(ro, a, b, R, T)"),
+    ("droplet field with the tanh profile inverted", "Eq. 31", "oracle.warm",
+     "- 0.5 * (ri - rho_v) * np.tanh(2.0 * s / width)",
+     "+ 0.5 * (ri - rho_v) * np.tanh(2.0 * s / width)"),
+    ("Gibbs surface from the whole liquid excess instead of half", "Eq. 31", "oracle.warm",
+     "yg = c + L / 2.0", "yg = c + L"),
 ]
 
 
@@ -158,34 +217,55 @@ def source():
         return fh.read()
 
 
-def test_unaltered_copy_passes_the_pins(source, tmp_path):
-    r = _pins(_compile(str(tmp_path), "control", source))
+@pytest.fixture(scope="module")
+def runs(source, tmp_path_factory):
+    """Every copy's pin run, side by side: {(kind, what): CompletedProcess}."""
+    d = str(tmp_path_factory.mktemp("mutants"))
+    jobs = {("c", "control"): (lambda: _pins(_compile(d, "c_control", source)))}
+    for i, (what, _, old, new) in enumerate(MUTATIONS):
+        if source.count(old) == 1:
+            text = source.replace(old, new)
+            jobs[("c", what)] = (lambda t=text, k="c_%d" % i: _pins(_compile(d, k, t)))
+    for name in sorted(MODULE_PINS):
+        path = _write(d, name + "_control", _module_source(name))
+        jobs[("py", name)] = (lambda n=name, p=path: _pins_with_module(n, p))
+    for i, (what, _, name, old, new) in enumerate(PY_MUTATIONS):
+        text = _module_source(name)
+        if text.count(old) == 1:
+            path = _write(d, "%s_%d" % (name, i), text.replace(old, new))
+            jobs[("py", what)] = (lambda n=name, p=path: _pins_with_module(n, p))
+    with ThreadPoolExecutor(WORKERS) as ex:
+        futures = {k: ex.submit(f) for k, f in jobs.items()}
+        return {k: f.result() for k, f in futures.items()}
+
+
+def test_unaltered_copy_passes_the_pins(runs):
+    r = runs[("c", "control")]
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
 
 
 @pytest.mark.parametrize("what,passage,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_pins_catch_the_mistake(source, tmp_path, what, passage, old, new):
+def test_pins_catch_the_mistake(runs, source, what, passage, old, new):
     assert source.count(old) == 1, "the text to alter must occur exactly once"
-    r = _pins(_compile(str(tmp_path), "mutant", source.replace(old, new)))
+    r = runs[("c", what)]
     assert r.returncode == 1, (what, passage, r.stdout[-2000:])
 
 
-@pytest.mark.parametrize("name", sorted({m[2] for m in PY_MUTATIONS}))
-def test_unaltered_module_copy_passes_the_pins(tmp_path, name):
-    r = _pins_with_module(name, _write(str(tmp_path), name, _module_source(name)))
+@pytest.mark.parametrize("name", sorted(MODULE_PINS))
+def test_unaltered_module_copy_passes_the_pins(runs, name):
+    r = runs[("py", name)]
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
 
 
 @pytest.mark.parametrize("what,passage,name,old,new", PY_MUTATIONS,
                          ids=[m[0] for m in PY_MUTATIONS])
-def test_pins_catch_the_mistake_in_a_module(tmp_path, what, passage, name, old, new):
-    text = _module_source(name)
-    assert text.count(old) == 1, "the text to alter must occur exactly once"
-    r = _pins_with_module(name, _write(str(tmp_path), name, text.replace(old, new)))
+def test_pins_catch_the_mistake_in_a_module(runs, what, passage, name, old, new):
+    assert _module_source(name).count(old) == 1, "the text to alter must occur exactly once"
+    r = runs[("py", what)]
     assert r.returncode == 1, (what, passage, r.stdout[-2000:])
 
 
-def test_the_check_loads_the_named_build(tmp_path):
+def test_the_check_loads_the_named_build():
     """LBM_ORACLE_LIB names the shared object the oracle package loads."""
     code = "import oracle; print(oracle.lib()._name)"
     path = oracle.build.build()
