@@ -58,6 +58,8 @@ MUTATIONS = [
      "fnew[OPP[a] * N + n] = fstar[a * N + n];", "fnew[a * N + n] = fstar[a * N + n];"),
     ("streaming against the lattice velocity in x", "Eq. 5",
      "int xd = wrap(x + EX[a], nx);", "int xd = wrap(x - EX[a], nx);"),
+    ("pseudopotential without the clamp of a negative argument", "Eq. 24 (reading)",
+     "if (arg < 0.0) arg = 0.0;", ""),
     ("two diagonal velocities exchanged in the velocity table", "Eq. 3",
      "static const int EX[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};",
      "static const int EX[Q] = {0, 1, 0, -1, 0, -1, 1, -1, 1};"),
@@ -159,6 +161,8 @@ PY_MUTATIONS = [
      "oracle.thermo", "** (1.0 + eps)", "** (1.0 - eps)"),
     ("lattice sound speed squared 1/2", "Eq. 24", "oracle.thermo",
      "CS2 = 1.0 / 3.0", "CS2 = 1.0 / 2.0"),
+    ("pseudopotential without the clamp of a negative argument", "Eq. 24 (reading)",
+     "oracle.thermo", "return math.sqrt(max(arg, 0.0))", "return math.sqrt(arg)"),
     ("critical temperature without the factor 2", "Sec. IV A", "oracle.thermo",
      "Tc = 2.0 * a / ((b / 4.0)", "Tc = a / ((b / 4.0)"),
     ("GELU derivative without its z phi(z) term", "GELU", "oracle.mlp",

@@ -127,6 +127,20 @@ def test_psi_reproduces_eos_through_eq11():
                                 abs_tol=1e-18)
 
 
+def test_psi_clamps_a_negative_argument_to_zero():
+    """Reading of Eq. 24 (G < 0): where p_EOS exceeds rho c_s^2, which the CS EOS does at
+    liquid densities well above coexistence (here rho >= 0.7 at T = 0.7 T_c), the square
+    root's argument is negative; psi is taken as zero there, by the C step and the Python
+    thermodynamics alike, and stays positive below that density."""
+    T = 0.7 * tc(A)
+    for rho in (0.7, 0.8, 0.95):
+        assert oracle.p_eos(rho, A, B, R, T) > rho / 3.0
+        assert oracle.psi(rho, A, B, R, T, -1.0) == 0.0
+        assert thermo.psi(rho, A, B, R, T, -1.0) == 0.0
+    for rho in (0.01, 0.3, 0.6):
+        assert oracle.psi(rho, A, B, R, T, -1.0) > 0.0
+
+
 def test_maxwell_matches_table_ii(golden):
     """Maxwell construction (Eq. 22) against the Maxwell column of Table II (a = 0.25,
     T_c = 0.0235, Sec. IV C).  Liquid within the printed digits; vapour within 0.5 %
