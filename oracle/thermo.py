@@ -48,12 +48,6 @@ def dp_drho(rho, a, b, R, T):
     return R * T * (Z + x * Z1) - 2.0 * a * rho
 
 
-def d2p_drho2(rho, a, b, R, T):
-    x = b * rho / 4.0
-    _, Z1, Z2 = _Z_derivs(x)
-    return R * T * (b / 4.0) * (2.0 * Z1 + x * Z2) - 2.0 * a
-
-
 def psi(rho, a, b, R, T, G=-1.0):
     """Eq. 24 with c = 1; a negative argument is clamped to zero."""
     arg = 2.0 * (p_eos(rho, a, b, R, T) - rho * CS2) / G

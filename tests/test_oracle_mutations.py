@@ -147,6 +147,9 @@ PY_MUTATIONS = [
      "2.0 * sigma * G * G * (gx * gx + gy * gy)", "2.0 * sigma * G * (gx * gx + gy * gy)"),
     ("shear component from e_x e_x", "Eq. 18", "oracle.pressure",
      "sxy += wp * ex * ey", "sxy += wp * ex * ex"),
+    ("pressure tensor at walls reading the wrapped row", "Eq. 18 (reading)",
+     "oracle.pressure", "idx = np.clip(np.arange(ny) + ey, 0, ny - 1)",
+     "idx = (np.arange(ny) + ey) % ny"),
     ("surface tension over both interfaces instead of one", "Eq. 18", "oracle.pressure",
      "return 0.5 * float(np.sum(", "return float(np.sum("),
     ("CS compressibility factor without its cubic term", "Eq. 30", "oracle.thermo",

@@ -60,6 +60,21 @@ def test_sigma_term_is_two_sigma_force_over_psi_squared():
     assert np.array_equal(a1[2], a0[2])
 
 
+def test_walls_tensor_equals_the_mirrored_periodic_tensor():
+    """With walls, psi at a ghost row equals psi of the adjacent fluid row (the halfway
+    wall of the step), so the walled tensor equals, on the original rows, the periodic
+    tensor of the field extended by its mirror image in y."""
+    T = 0.7 * wl.t_crit(A)
+    rng = np.random.default_rng(3)
+    rho = 0.05 + 0.3 * rng.uniform(size=(9, 7))
+    psi = np.vectorize(lambda r: thermo.psi(r, A, B, R, T))(rho)
+    walled = op.pressure_tensor_from_psi(rho, psi, -1.0, walls=True, sigma=0.114)
+    ext = lambda a: np.concatenate([a, a[::-1]], axis=0)  # noqa: E731
+    periodic = op.pressure_tensor_from_psi(ext(rho), ext(psi), -1.0, sigma=0.114)
+    for w, q in zip(walled, periodic):
+        assert np.allclose(w, q[:9], rtol=1e-14, atol=1e-17)
+
+
 def test_film_tensor_is_x_uniform_and_symmetric():
     """An x-uniform film has no shear and x-uniform components; rotating the film by 90
     degrees swaps pxx and pyy."""
