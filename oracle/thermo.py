@@ -158,8 +158,3 @@ def mechanical_stability(a, b, R, T, G=-1.0, eps=0.0):
 def lamb_period(gamma, rho_l, R0, n=2):
     """Eq. 32: T_a = 2 pi [n (n^2 - 1) gamma / (rho_l R0^3)]^(-1/2)."""
     return 2.0 * math.pi / math.sqrt(n * (n * n - 1) * gamma / (rho_l * R0 ** 3))
-
-
-def tc_of(a, b=4.0, R=1.0, k=0.3773):
-    """Critical temperature in the rounded form k a / (b R) used by the workloads."""
-    return k * a / (b * R)
