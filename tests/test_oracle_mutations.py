@@ -60,6 +60,17 @@ MUTATIONS = [
      "int xd = wrap(x + EX[a], nx);", "int xd = wrap(x - EX[a], nx);"),
     ("pseudopotential without the clamp of a negative argument", "Eq. 24 (reading)",
      "if (arg < 0.0) arg = 0.0;", ""),
+    ("force reported without its psi(x) factor", "Eq. 7",
+     "if (Fx_out) Fx_out[n] = psi[n] * fpx[n];", "if (Fx_out) Fx_out[n] = fpx[n];"),
+    ("bounce-back at the bottom wall only", "Sec. IV C",
+     "if (p->walls && (yd < 0 || yd >= ny)) {", "if (p->walls && (yd < 0)) {"),
+    ("psi above the top wall read from the bottom row", "Sec. IV C",
+     "if (y >= p->ny) y = p->ny - 1;", "if (y >= p->ny) y = 0;"),
+    ("equilibrium populations through M instead of M^-1", "Eq. 3",
+     "for (int i = 0; i < Q; ++i) acc += Minv[a][i] * meq[i];",
+     "for (int i = 0; i < Q; ++i) acc += M[i][a] * meq[i] / 9.0;"),
+    ("collision relaxing away from the equilibrium", "Eq. 4",
+     "ms[i] = m[i] - lam[i] * (m[i] - meq[i])", "ms[i] = m[i] - lam[i] * (meq[i] - m[i])"),
     ("two diagonal velocities exchanged in the velocity table", "Eq. 3",
      "static const int EX[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};",
      "static const int EX[Q] = {0, 1, 0, -1, 0, -1, 1, -1, 1};"),
